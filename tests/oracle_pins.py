@@ -1,0 +1,525 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each ``pin_*`` function takes an ``oracle.Oracle`` instance and raises
+AssertionError when the oracle disagrees with:
+  * closed forms of a single Gaussian (projection, EWA Jacobian, rotation
+    conventions, blended value, Eq. 10 threshold and the adjusted radius),
+  * adaptive quadrature of the annulus integral behind Eq. 8-9 and the pixel
+    (Riemann) sum it replaces,
+  * the textbook table of real spherical harmonics (Condon-Shortley phase) and
+    their orthonormality on the sphere,
+  * brute-force enumeration (pixel coverage of the tile rectangle, untiled
+    rendering, and an ideal render with no footprint at all),
+  * invariants stated by the paper (Th >= tau, Th > sigma culls, larger K drops
+    pairs, the blend always uses the unscaled covariance),
+  * FP64 central finite differences of the forward (backward pin).
+
+The same functions run against deliberately broken oracle builds in
+``test_oracle_mutants.py`` to show that plausible mistakes are caught.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+from paper_2604_18980_gb300 import synth
+
+TAU = oracle.TAU
+C0 = 0.5 / math.sqrt(math.pi)     # Y_0^0
+
+
+def axis_camera(W, H, f, R=None, campos=(0.0, 0.0, 0.0)):
+    R = np.eye(3) if R is None else np.asarray(R, dtype=np.float64)
+    c = np.asarray(campos, dtype=np.float64)
+    vm = np.concatenate([R, (-R @ c)[:, None]], 1)
+    return dict(width=W, height=H, fx=f, fy=f, cx=(W - 1) / 2.0, cy=(H - 1) / 2.0, viewmat=vm,
+                campos=c, near=0.2)
+
+
+def one_gaussian(pos, scales, quat=(1.0, 0.0, 0.0, 0.0), opacity=0.7, dc=(0.2, -0.3, 0.4), extra_sh=None):
+    sh = np.zeros((16, 3, 1))
+    sh[0, :, 0] = dc
+    if extra_sh is not None:
+        sh[:, :, 0] += extra_sh
+    return dict(mean=np.asarray(pos, dtype=np.float64).reshape(3, 1),
+                log_scale=np.log(np.asarray(scales, dtype=np.float64)).reshape(3, 1),
+                quat=np.asarray(quat, dtype=np.float64).reshape(4, 1),
+                opacity_logit=np.array([math.log(opacity / (1.0 - opacity))]), sh=sh)
+
+
+def concat(*scenes):
+    out = {}
+    for k in scenes[0]:
+        out[k] = np.concatenate([s[k] for s in scenes], axis=-1)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Closed form 1: isotropic Gaussian on the optical axis, mean at a pixel centre
+# --------------------------------------------------------------------------
+def pin_isotropic_on_axis(orc):
+    W = H = 65
+    f, d, s, sig = 80.0, 2.0, 0.05, 0.7
+    cam = axis_camera(W, H, f)
+    sc = one_gaussian((0.0, 0.0, d), (s, s, s), quat=(0.3, -0.5, 0.2, 0.7), opacity=sig)
+    lam = (f * s / d) ** 2 + 0.3
+    rgb = np.array([0.2, -0.3, 0.4]) * C0 + 0.5
+    par = oracle.params(cam, scale_mode=0)
+    out = orc.render(sc, cam, par)
+    g = out["dbl"][0]
+    np.testing.assert_allclose([g[oracle.F_U], g[oracle.F_V]], [32.0, 32.0], atol=1e-12)
+    np.testing.assert_allclose(g[oracle.F_DEPTH], d, rtol=1e-14)
+    np.testing.assert_allclose([g[oracle.F_COVA], g[oracle.F_COVB], g[oracle.F_COVC]], [lam, 0.0, lam],
+                               rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose([g[oracle.F_A], g[oracle.F_B], g[oracle.F_C]], [1 / lam, 0.0, 1 / lam],
+                               rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g[oracle.F_DET], lam * lam, rtol=1e-12)
+    np.testing.assert_allclose(g[oracle.F_OPAC], sig, rtol=1e-12)
+    np.testing.assert_allclose(g[oracle.F_R:oracle.F_BL + 1], rgb, rtol=1e-12)
+    r = math.ceil(3 * math.sqrt(lam))
+    ir = out["irec"][0]
+    assert ir[oracle.I_RADIUS] == r
+    # pixel centres 32-r .. 32+r -> tiles
+    assert (ir[oracle.I_X0], ir[oracle.I_X1]) == ((32 - r) // 16, (32 + r) // 16 + 1)
+    img = out["image"]
+    np.testing.assert_allclose(img[:, 32, 32], min(0.99, sig) * rgb, rtol=1e-12)
+    for k in range(1, 9):
+        a = sig * math.exp(-k * k / (2 * lam))
+        exp = a * rgb if a >= TAU else np.zeros(3)
+        np.testing.assert_allclose(img[:, 32, 32 + k], exp, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(img[:, 32 - k, 32], exp, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(out["final_T"][32, 32], 1 - sig, rtol=1e-12)
+
+    # AdaGScale with T_up = 1: Th = K / (2 pi lambda) + tau (sqrt(det) = lambda)
+    for K in (0.05, 0.5, 2.0):
+        par = oracle.params(cam, scale_mode=1, K=K)
+        o2 = orc.render(sc, cam, par)
+        th = K / (2 * math.pi * lam) + TAU
+        np.testing.assert_allclose(o2["dbl"][0][oracle.F_TH], th, rtol=1e-12)
+        ra = math.ceil(math.sqrt(lam) * min(3.0, math.sqrt(2 * math.log(sig / th))))
+        assert o2["irec"][0][oracle.I_RADIUS] == ra
+        assert (o2["irec"][0][oracle.I_X0], o2["irec"][0][oracle.I_X1]) == ((32 - ra) // 16, (32 + ra) // 16 + 1)
+        assert len(o2["ids"]) == ((32 + ra) // 16 + 1 - (32 - ra) // 16) ** 2
+        # dual size: the blend is unchanged where the pair survives
+        np.testing.assert_array_equal(o2["image"][:, 32, 32], img[:, 32, 32])
+    # K large enough that Th > sigma: culled
+    Kc = (sig - TAU) * 2 * math.pi * lam * 1.001
+    o3 = orc.render(sc, cam, oracle.params(cam, scale_mode=1, K=Kc))
+    assert o3["irec"][0][oracle.I_CULL] == oracle.CULL_TH and len(o3["ids"]) == 0
+    # LUT: depth 2 falls in bin floor(2 / 5) = 0 of 20 bins over [0, 100]
+    lut = np.ones(20)
+    lut[0] = 0.25
+    o4 = orc.render(sc, cam, oracle.params(cam, scale_mode=1, K=0.5, lut=lut))
+    np.testing.assert_allclose(o4["dbl"][0][oracle.F_TH], 0.5 / (0.25 * 2 * math.pi * lam) + TAU, rtol=1e-12)
+    lut = np.ones(20)
+    lut[1] = 0.25   # bin 1 must not be used at depth 2
+    o5 = orc.render(sc, cam, oracle.params(cam, scale_mode=1, K=0.5, lut=lut))
+    np.testing.assert_allclose(o5["dbl"][0][oracle.F_TH], 0.5 / (2 * math.pi * lam) + TAU, rtol=1e-12)
+    # T_up = 0 for the bin: Th infinite -> culled
+    lut[0] = 0.0
+    o6 = orc.render(sc, cam, oracle.params(cam, scale_mode=1, K=0.5, lut=lut))
+    assert o6["irec"][0][oracle.I_CULL] == oracle.CULL_TUP
+
+
+# --------------------------------------------------------------------------
+# Closed form 2: off-axis isotropic Gaussian (the off-diagonal Jacobian terms)
+# and the 1.3 tan(fov/2) frustum clamp
+# --------------------------------------------------------------------------
+def pin_off_axis_jacobian(orc):
+    W, H, f = 200, 120, 150.0
+    cam = axis_camera(W, H, f)
+    for (x, y, d, s) in ((0.3, -0.2, 2.0, 0.02), (-0.5, 0.25, 3.0, 0.04)):
+        sc = one_gaussian((x, y, d), (s, s, s), quat=(0.1, 0.9, -0.3, 0.2))
+        g = orc.preprocess(sc, cam, oracle.params(cam))[0][0]
+        JJ = np.array([[f * f / d ** 2 * (1 + x * x / d ** 2), f * f * x * y / d ** 4],
+                       [f * f * x * y / d ** 4, f * f / d ** 2 * (1 + y * y / d ** 2)]])
+        S = s * s * JJ + 0.3 * np.eye(2)
+        np.testing.assert_allclose([g[oracle.F_COVA], g[oracle.F_COVB], g[oracle.F_COVC]],
+                                   [S[0, 0], S[0, 1], S[1, 1]], rtol=1e-12)
+        np.testing.assert_allclose([g[oracle.F_U], g[oracle.F_V]], [f * x / d + (W - 1) / 2, f * y / d + (H - 1) / 2],
+                                   rtol=1e-13)
+        Si = np.linalg.inv(S)
+        np.testing.assert_allclose([g[oracle.F_A], g[oracle.F_B], g[oracle.F_C]], [Si[0, 0], Si[0, 1], Si[1, 1]],
+                                   rtol=1e-11)
+        lam = 0.5 * (S[0, 0] + S[1, 1]) + math.sqrt(max(0.1, (0.5 * (S[0, 0] + S[1, 1])) ** 2 - np.linalg.det(S)))
+        np.testing.assert_allclose(g[oracle.F_LAMBDA], lam, rtol=1e-12)
+    # clamp: x/z beyond 1.3 * (W/2)/f -> the Jacobian uses the clamped x, the mean does not
+    d, s = 2.0, 0.05
+    lim = 1.3 * (0.5 * W / f)
+    x = 1.6 * lim * d
+    sc = one_gaussian((x, 0.0, d), (s, s, s))
+    g = orc.preprocess(sc, cam, oracle.params(cam))[0][0]
+    xc = lim * d
+    np.testing.assert_allclose(g[oracle.F_COVA], s * s * f * f / d ** 2 * (1 + xc * xc / d ** 2) + 0.3, rtol=1e-12)
+    np.testing.assert_allclose(g[oracle.F_U], f * x / d + (W - 1) / 2, rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Closed form 3: quaternion convention (w, x, y, z) and the camera rotation W
+# --------------------------------------------------------------------------
+def pin_rotation_conventions(orc):
+    W = H = 101
+    f, d = 120.0, 2.5
+    cam = axis_camera(W, H, f)
+    th = math.radians(30.0)
+    s1, s2, s3 = 0.06, 0.02, 0.01
+    sc = one_gaussian((0.0, 0.0, d), (s1, s2, s3), quat=(math.cos(th / 2), 0.0, 0.0, math.sin(th / 2)))
+    g = orc.preprocess(sc, cam, oracle.params(cam))[0][0]
+    c, s = math.cos(th), math.sin(th)
+    Sxy = np.array([[c * c * s1 ** 2 + s * s * s2 ** 2, c * s * (s1 ** 2 - s2 ** 2)],
+                    [c * s * (s1 ** 2 - s2 ** 2), s * s * s1 ** 2 + c * c * s2 ** 2]])
+    S = (f / d) ** 2 * Sxy + 0.3 * np.eye(2)
+    np.testing.assert_allclose([g[oracle.F_COVA], g[oracle.F_COVB], g[oracle.F_COVC]],
+                               [S[0, 0], S[0, 1], S[1, 1]], rtol=1e-12)
+    # an un-normalised quaternion describes the same rotation
+    sc2 = one_gaussian((0.0, 0.0, d), (s1, s2, s3), quat=(3 * math.cos(th / 2), 0.0, 0.0, 3 * math.sin(th / 2)))
+    g2 = orc.preprocess(sc2, cam, oracle.params(cam))[0][0]
+    np.testing.assert_allclose(g2[oracle.F_COVA:oracle.F_COVC + 1], g[oracle.F_COVA:oracle.F_COVC + 1], rtol=1e-12)
+    # camera looking along world +x with z up: camera x = -world y, camera y = -world z
+    Rc = np.array([[0.0, -1.0, 0.0], [0.0, 0.0, -1.0], [1.0, 0.0, 0.0]])
+    cam2 = axis_camera(W, H, f, R=Rc)
+    sx, sy, sz = 0.03, 0.05, 0.02
+    sc3 = one_gaussian((d, 0.0, 0.0), (sx, sy, sz))
+    g3 = orc.preprocess(sc3, cam2, oracle.params(cam2))[0][0]
+    np.testing.assert_allclose([g3[oracle.F_COVA], g3[oracle.F_COVB], g3[oracle.F_COVC]],
+                               [(f / d) ** 2 * sy ** 2 + 0.3, 0.0, (f / d) ** 2 * sz ** 2 + 0.3], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g3[oracle.F_DEPTH], d, rtol=1e-14)
+    # a point at world (d, 0.1, 0.05) lands left of and above the centre
+    sc4 = one_gaussian((d, 0.1, 0.05), (sx, sy, sz))
+    g4 = orc.preprocess(sc4, cam2, oracle.params(cam2))[0][0]
+    np.testing.assert_allclose([g4[oracle.F_U], g4[oracle.F_V]], [50.0 - f * 0.1 / d, 50.0 - f * 0.05 / d], rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Eq. 8-10: the annulus integral, by adaptive quadrature and by pixel sums
+# --------------------------------------------------------------------------
+def _annulus_integral(A, B, C, sig, lo, hi):
+    """Integral of sig*exp(-Q/2) over tau_lo <= alpha < hi, Q = A dx^2 + 2B dx dy + C dy^2."""
+    from scipy import integrate
+
+    def radial(phi):
+        rho = A * math.cos(phi) ** 2 + 2 * B * math.cos(phi) * math.sin(phi) + C * math.sin(phi) ** 2
+        r_out = math.sqrt(2 * math.log(sig / lo) / rho)
+        r_in = math.sqrt(2 * math.log(sig / hi) / rho) if hi < sig else 0.0
+        val, _ = integrate.quad(lambda r: sig * math.exp(-0.5 * r * r * rho) * r, r_in, r_out,
+                                epsabs=1e-13, epsrel=1e-11)
+        return val
+
+    val, _ = integrate.quad(radial, 0.0, 2 * math.pi, epsabs=1e-12, epsrel=1e-10, limit=200)
+    return val
+
+
+def pin_eq9_quadrature(orc):
+    W = H = 257
+    f, d = 300.0, 2.0
+    cam = axis_camera(W, H, f)
+    sig = 0.8
+    sc = one_gaussian((0.0, 0.0, d), (0.07, 0.03, 0.02), quat=(0.9, 0.1, 0.2, 0.35), opacity=sig)
+    for K in (0.5, 5.0):
+        lut = np.full(20, 0.6)
+        g = orc.preprocess(sc, cam, oracle.params(cam, scale_mode=1, K=K, lut=lut))[0][0]
+        A, B, C = g[oracle.F_A], g[oracle.F_B], g[oracle.F_C]
+        th = g[oracle.F_TH]
+        assert TAU <= th < sig
+        # Eq. 5 with the integral form (Eq. 8): T_up * integral_{tau <= alpha < Th} alpha = K
+        ps = 0.6 * _annulus_integral(A, B, C, sig, TAU, th)
+        np.testing.assert_allclose(ps, K, rtol=1e-7)
+        # Eq. 9 at other levels x
+        for x in (0.01, 0.1, 0.5, sig):
+            np.testing.assert_allclose(_annulus_integral(A, B, C, sig, TAU, x),
+                                       2 * math.pi * math.sqrt(g[oracle.F_DET]) * (x - TAU), rtol=1e-7)
+
+
+def pin_eq8_riemann_pixels(orc):
+    """Pixel sum of alpha over tau <= alpha < x is within 1% of Eq. 9 for a large Gaussian."""
+    W = H = 161
+    f, d, sig = 200.0, 2.0, 0.3          # sigma <= 0.35: the 3-sigma square covers alpha >= tau
+    cam = axis_camera(W, H, f)
+    dc = (0.5 / C0,) * 3                 # colour 1 in every channel: image = alpha
+    sc = one_gaussian((0.013, -0.007, d), (0.2, 0.11, 0.05), quat=(0.8, 0.0, 0.0, 0.6), opacity=sig, dc=dc)
+    out = orc.render(sc, cam, oracle.params(cam))
+    g = out["dbl"][0]
+    lam = g[oracle.F_LAMBDA]
+    assert 300 < lam < 500
+    a = out["image"][0]
+    np.testing.assert_allclose(out["image"][1], a, rtol=1e-13)
+    for x in (0.02, 0.1, 0.2, sig + 1e-9):
+        sel = (a >= TAU) & (a < x)
+        approx = 2 * math.pi * math.sqrt(g[oracle.F_DET]) * (min(x, sig) - TAU)
+        np.testing.assert_allclose(a[sel].sum(), approx, rtol=1e-2)
+
+
+# --------------------------------------------------------------------------
+# Spherical harmonics: textbook table (Condon-Shortley phase) + orthonormality
+# --------------------------------------------------------------------------
+def sh_table(x, y, z):
+    p = math.pi
+    return np.array([
+        0.5 / math.sqrt(p),
+        -math.sqrt(3 / (4 * p)) * y, math.sqrt(3 / (4 * p)) * z, -math.sqrt(3 / (4 * p)) * x,
+        0.5 * math.sqrt(15 / p) * x * y, -0.5 * math.sqrt(15 / p) * y * z,
+        0.25 * math.sqrt(5 / p) * (3 * z * z - 1), -0.5 * math.sqrt(15 / p) * x * z,
+        0.25 * math.sqrt(15 / p) * (x * x - y * y),
+        -0.25 * math.sqrt(35 / (2 * p)) * y * (3 * x * x - y * y), 0.5 * math.sqrt(105 / p) * x * y * z,
+        -0.25 * math.sqrt(21 / (2 * p)) * y * (5 * z * z - 1), 0.25 * math.sqrt(7 / p) * (5 * z ** 3 - 3 * z),
+        -0.25 * math.sqrt(21 / (2 * p)) * x * (5 * z * z - 1), 0.25 * math.sqrt(105 / p) * z * (x * x - y * y),
+        -0.25 * math.sqrt(35 / (2 * p)) * x * (x * x - 3 * y * y),
+    ])
+
+
+def pin_sh_basis(orc):
+    rng = np.random.default_rng(7)
+    dirs = rng.standard_normal((40, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    dirs = np.concatenate([dirs, np.eye(3), -np.eye(3)])
+    Y = orc.sh_basis(3, dirs)
+    for i, d in enumerate(dirs):
+        np.testing.assert_allclose(Y[i], sh_table(*d), rtol=1e-12, atol=1e-14)
+    # orthonormality: Gauss-Legendre in z times uniform phi (exact for these degrees)
+    zs, wz = np.polynomial.legendre.leggauss(16)
+    phis = np.arange(32) * (2 * math.pi / 32)
+    pts, wts = [], []
+    for z, w in zip(zs, wz):
+        r = math.sqrt(1 - z * z)
+        for ph in phis:
+            pts.append((r * math.cos(ph), r * math.sin(ph), z))
+            wts.append(w * 2 * math.pi / 32)
+    Yq = orc.sh_basis(3, np.array(pts))
+    G = (Yq * np.array(wts)[:, None]).T @ Yq
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def pin_sh_colour(orc):
+    """Colour = sum_k sh_k Y_k(dir) + 0.5, clamped at zero, with dir from the camera centre."""
+    W = H = 33
+    cam = axis_camera(W, H, 40.0, campos=(0.1, -0.2, -1.0))
+    rng = np.random.default_rng(3)
+    extra = rng.normal(0, 0.3, size=(16, 3))
+    extra[0] = 0.0
+    pos = np.array([0.2, 0.1, 1.5])
+    sc = one_gaussian(pos, (0.01, 0.01, 0.01), dc=(0.1, -2.5, 0.3), extra_sh=extra)
+    dbl, irec = orc.preprocess(sc, cam, oracle.params(cam))
+    d = pos - np.array([0.1, -0.2, -1.0])
+    d /= np.linalg.norm(d)
+    sh = sc["sh"][:, :, 0]
+    rgb = sh_table(*d) @ sh + 0.5
+    clamped = rgb < 0
+    rgb = np.maximum(rgb, 0.0)
+    np.testing.assert_allclose(dbl[0, oracle.F_R:oracle.F_BL + 1], rgb, rtol=1e-12, atol=1e-14)
+    assert (irec[0, oracle.I_CLAMP] & 7) == sum(1 << c for c in range(3) if clamped[c])
+    assert clamped[1]
+
+
+# --------------------------------------------------------------------------
+# Brute force: tile rectangles by pixel enumeration; untiled and ideal renders
+# --------------------------------------------------------------------------
+def tiny_scene(n, seed, opacity_max=None, W=64, H=48):
+    scene = synth.scene_uniform_cube(n, seed)
+    scene["mean"] *= 0.6
+    scene["log_scale"] += 1.0
+    if opacity_max is not None:
+        sig = 1.0 / (1.0 + np.exp(-scene["opacity_logit"].astype(np.float64)))
+        sig = np.minimum(sig, opacity_max)
+        scene["opacity_logit"] = np.log(sig / (1 - sig)).astype(np.float32)
+    cam = synth.cams_sphere(1, seed + 1, 3.0, W, H)[0]
+    return scene, cam
+
+
+def pin_rect_enumeration(orc):
+    for mode, K in ((0, 0.0), (1, 0.2)):
+        scene, cam = tiny_scene(300, 11)
+        W, H = cam["width"], cam["height"]
+        dbl, irec = orc.preprocess(scene, cam, oracle.params(cam, scale_mode=mode, K=K))
+        px, py = np.meshgrid(np.arange(W), np.arange(H))
+        for i in range(len(irec)):
+            r = irec[i, oracle.I_RADIUS]
+            if irec[i, oracle.I_CULL] not in (oracle.CULL_NONE, oracle.CULL_EMPTY):
+                continue
+            u, v = dbl[i, oracle.F_U], dbl[i, oracle.F_V]
+            inside = (np.abs(px - u) <= r) & (np.abs(py - v) <= r) if r > 0 else np.zeros_like(px, bool)
+            tiles = set(zip((px[inside] // 16).tolist(), (py[inside] // 16).tolist()))
+            x0, y0, x1, y1 = (irec[i, k] for k in (oracle.I_X0, oracle.I_Y0, oracle.I_X1, oracle.I_Y1))
+            got = {(tx, ty) for tx in range(x0, x1) for ty in range(y0, y1)} if irec[i, oracle.I_TOUCHED] else set()
+            assert got == tiles, (i, got, tiles)
+
+
+def _ideal_render(dbl, irec, W, H, cull_ok):
+    """Blend every Gaussian at every pixel in (fp32 depth, id) order; no footprint test."""
+    order = sorted([i for i in range(len(dbl)) if cull_ok(irec[i])],
+                   key=lambda i: (np.float32(dbl[i, oracle.F_DEPTH]), i))
+    img = np.zeros((3, H, W))
+    for y in range(H):
+        for x in range(W):
+            T, col = 1.0, np.zeros(3)
+            for i in order:
+                g = dbl[i]
+                dx, dy = g[oracle.F_U] - x, g[oracle.F_V] - y
+                p = -0.5 * (g[oracle.F_A] * dx * dx + g[oracle.F_C] * dy * dy) - g[oracle.F_B] * dx * dy
+                if p > 0:
+                    continue
+                a = min(0.99, g[oracle.F_OPAC] * math.exp(p))
+                if a < TAU:
+                    continue
+                tT = T * (1 - a)
+                if tT < 1e-4:
+                    break
+                col += g[oracle.F_R:oracle.F_BL + 1] * a * T
+                T = tT
+            img[:, y, x] = col
+    return img
+
+
+def pin_bruteforce(orc):
+    scene, cam = tiny_scene(160, 21)
+    par = oracle.params(cam, bg=(0.1, 0.2, 0.3))
+    tiled = orc.render(scene, cam, par)["image"]
+    brute = orc.render_bruteforce(scene, cam, par)
+    np.testing.assert_array_equal(tiled, brute)
+    par = oracle.params(cam, scale_mode=1, K=0.05)
+    np.testing.assert_array_equal(orc.render(scene, cam, par)["image"], orc.render_bruteforce(scene, cam, par))
+
+
+def pin_ideal_render(orc):
+    """With opacities <= 0.35 the 3-sigma square covers all alpha >= tau: tiling loses nothing."""
+    scene, cam = tiny_scene(120, 31, opacity_max=0.35, W=48, H=40)
+    par = oracle.params(cam)
+    out = orc.render(scene, cam, par)
+    ideal = _ideal_render(out["dbl"], out["irec"], cam["width"], cam["height"],
+                          lambda r: r[oracle.I_CULL] in (oracle.CULL_NONE, oracle.CULL_EMPTY))
+    np.testing.assert_allclose(out["image"], ideal, rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Invariants
+# --------------------------------------------------------------------------
+def _pairs(out, W):
+    ts, ids = out["tile_start"], out["ids"]
+    tile = np.repeat(np.arange(len(ts) - 1), np.diff(ts))
+    return set(zip(tile.tolist(), ids.tolist()))
+
+
+def pin_invariants(orc):
+    scene, cams, _ = synth.workload("c1_cube16k_256", n=3000, width=96, height=80)
+    cam = cams[0]
+    plain = orc.render(scene, cam, oracle.params(cam))
+    P = _pairs(plain, cam["width"])
+    prev = None
+    for K in (0.0, 0.1, 0.3, 1.0, 3.0, 10.0):
+        par = oracle.params(cam, scale_mode=1, K=K)
+        ada = orc.render(scene, cam, par)
+        A = _pairs(ada, cam["width"])
+        assert A <= P, "AdaGScale added a pair"
+        if prev is not None:
+            assert A <= prev, "pair set not monotone in K"
+        prev = A
+        live = ada["irec"][:, oracle.I_CULL] != oracle.CULL_NONFINITE
+        th = ada["dbl"][live, oracle.F_TH]
+        assert np.all(th[np.isfinite(th)] >= TAU)                       # Th >= tau (Sec. 3.3)
+        culled = ada["irec"][:, oracle.I_CULL] == oracle.CULL_TH
+        np.testing.assert_array_equal(culled, ada["dbl"][:, oracle.F_TH] > ada["dbl"][:, oracle.F_OPAC])
+        # dual size: features of surviving Gaussians identical to plain mode
+        surv = ada["irec"][:, oracle.I_CULL] == oracle.CULL_NONE
+        np.testing.assert_array_equal(ada["dbl"][surv, :oracle.F_DEPTH + 1], plain["dbl"][surv, :oracle.F_DEPTH + 1])
+        # the blend of a given list does not depend on K or the mode
+        r1 = orc.rasterize(plain["dbl"], ada["tile_start"], ada["ids"], cam["width"], cam["height"],
+                           oracle.params(cam))
+        np.testing.assert_array_equal(r1["image"], ada["image"])
+        if K == 0.0:
+            # K = 0: Th = tau, dropped tiles held only alpha < tau pixels
+            np.testing.assert_array_equal(ada["image"], plain["image"])
+            sig = plain["dbl"][:, oracle.F_OPAC]
+            assert np.all(ada["irec"][sig < TAU, oracle.I_CULL] == oracle.CULL_TH)
+    assert len(prev) < len(P)
+
+
+def pin_low_opacity_invisible(orc):
+    """Gaussians with opacity < tau never change the image (and AdaGScale culls them)."""
+    scene, cam = tiny_scene(150, 41)
+    faint, _ = tiny_scene(60, 42)
+    faint["opacity_logit"][:] = math.log((TAU * 0.9) / (1 - TAU * 0.9))
+    both = concat(scene, faint)
+    par = oracle.params(cam)
+    np.testing.assert_array_equal(orc.render(both, cam, par)["image"], orc.render(scene, cam, par)["image"])
+    ada = orc.render(both, cam, oracle.params(cam, scale_mode=1, K=0.0))
+    assert np.all(ada["irec"][150:, oracle.I_CULL] == oracle.CULL_TH)
+
+
+def pin_max_T(orc):
+    """Calibration statistic: max T before blending over the pixels where a Gaussian blends."""
+    W = H = 65
+    f = 80.0
+    cam = axis_camera(W, H, f)
+    lam_f = (f * 0.3 / 2.0) ** 2 + 0.3       # front: wide, depth 2
+    s_b = 0.02                                # back: small, depth 3
+    lam_b = (f * s_b / 3.0) ** 2 + 0.3
+    sc = concat(one_gaussian((0, 0, 2.0), (0.3, 0.3, 0.3), opacity=0.5),
+                one_gaussian((0, 0, 3.0), (s_b, s_b, s_b), opacity=0.9))
+    out = orc.render(sc, cam, oracle.params(cam), want_max_T=True)
+    k = np.arange(-32, 33)
+    dx, dy = np.meshgrid(k, k)
+    r2 = dx * dx + dy * dy
+    blended = 0.9 * np.exp(-r2 / (2 * lam_b)) >= TAU
+    exp_back = (1 - 0.5 * np.exp(-r2[blended] / (2 * lam_f))).max()
+    np.testing.assert_allclose(out["max_T"], [1.0, exp_back], rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Backward: FP64 central differences of the forward with frozen lists
+# --------------------------------------------------------------------------
+def pin_backward_fd(orc, n_check=None, seed=5):
+    scene, cam = synth.fd_subscene()
+    scene = {k: v.astype(np.float64) for k, v in scene.items()}
+    scene["opacity_logit"][:4] = 5.5        # opacity 0.996: alpha hits the 0.99 clamp near the centre
+    W, H = cam["width"], cam["height"]
+    par = oracle.params(cam, bg=(0.05, 0.1, 0.15))
+    base = orc.render(scene, cam, par, want_state=True)
+    ts, ids = base["tile_start"], base["ids"]
+    rng = np.random.default_rng(seed)
+    w = rng.normal(size=(3, H, W))
+    grads = orc.backward(scene, cam, par, ts, ids, w)
+
+    def loss_and_state(sc):
+        dbl, irec = orc.preprocess(sc, cam, par)
+        r = orc.rasterize(dbl, ts, ids, W, H, par, want_state=True)
+        return float((w * r["image"]).sum()), (r["state"].tobytes(), irec[:, oracle.I_CLAMP].tobytes(),
+                                               irec[:, oracle.I_CULL].tobytes())
+
+    n = scene["opacity_logit"].shape[0]
+    coords = []
+    for key, rows in (("mean", 3), ("log_scale", 3), ("quat", 4), ("opacity_logit", 1)):
+        for r in range(rows):
+            for i in range(n):
+                coords.append((key, r, i))
+    for _ in range(96):
+        coords.append(("sh", (int(rng.integers(0, 16)), int(rng.integers(0, 3))), int(rng.integers(0, n))))
+    if n_check is not None:
+        keep = [c for c in coords if c[2] < 4 and c[0] != "sh"]
+        coords = keep + [coords[j] for j in rng.choice(len(coords), n_check, replace=False)]
+    gmax = max(np.abs(grads[k]).max() for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"))
+    checked = skipped = 0
+    for key, r, i in coords:
+        arr = scene[key]
+        idx = (i,) if arr.ndim == 1 else ((r, i) if arr.ndim == 2 else (r[0], r[1], i))
+        th = arr[idx]
+        h = 1e-6 * max(1.0, abs(th))
+        arr[idx] = th + h
+        lp, sp = loss_and_state(scene)
+        arr[idx] = th - h
+        lm, sm = loss_and_state(scene)
+        arr[idx] = th
+        if sp != sm:
+            skipped += 1
+            continue
+        fd = (lp - lm) / (2 * h)
+        g = grads[key][idx]
+        assert abs(fd - g) <= 1e-5 * abs(g) + 1e-7 * gmax, (key, r, i, fd, g)
+        checked += 1
+    assert checked > 0.9 * len(coords), (checked, skipped)
+    return checked, skipped
+
+
+ALL_PINS = [pin_isotropic_on_axis, pin_off_axis_jacobian, pin_rotation_conventions, pin_eq9_quadrature,
+            pin_eq8_riemann_pixels, pin_sh_basis, pin_sh_colour, pin_rect_enumeration, pin_bruteforce,
+            pin_ideal_render, pin_invariants, pin_low_opacity_invisible, pin_max_T, pin_backward_fd]

@@ -1,0 +1,77 @@
+"""Plant plausible mistakes in copies of the oracle source and check that the
+pins catch every one of them (CPU only; nothing is planted in the real oracle)."""
+import os
+import tempfile
+
+import pytest
+
+import oracle
+import oracle_pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "ags_oracle.c")
+
+# (name, original text, planted text, pins expected to catch it)
+MUTANTS = [
+    ("dropped_lowpass", "cc = jaddc(S2[3], 0.3);", "cc = S2[3];",
+     ["pin_isotropic_on_axis"]),
+    ("quat_sign", "Rq[1] = jscale(jsub(jmul(x, y), jmul(w, z)), 2.0);",
+     "Rq[1] = jscale(jadd(jmul(x, y), jmul(w, z)), 2.0);", ["pin_rotation_conventions"]),
+    ("camera_rotation_transposed", "acc = jadd(acc, jscale(J[a * 3 + k], cam->R[k * 3 + b]));",
+     "acc = jadd(acc, jscale(J[a * 3 + k], cam->R[b * 3 + k]));", ["pin_rotation_conventions"]),
+    ("dropped_offaxis_jacobian", "J[2] = jscale(jmul(tx, iz2), -cam->fx);", "J[2] = jc(0.0);",
+     ["pin_off_axis_jacobian"]),
+    ("no_frustum_clamp", "if (txtz.v > limx) { tx = jscale(t[2], limx); fclamp |= 8; }",
+     "if (0) { tx = jscale(t[2], limx); fclamp |= 8; }", ["pin_off_axis_jacobian"]),
+    ("eq10_det_not_sqrt", "double sd = sqrt(det.v);", "double sd = det.v;",
+     ["pin_isotropic_on_axis", "pin_eq9_quadrature"]),
+    ("eq10_missing_2pi", "th = par->K / (tup * 2.0 * M_PI * sd) + par->tau;",
+     "th = par->K / (tup * sd) + par->tau;", ["pin_isotropic_on_axis", "pin_eq9_quadrature"]),
+    ("radius_not_clamped_at_3", "rarg = sqrt(lam1) * fmin(3.0, sqrt(2.0 * log(opac.v / th)));",
+     "rarg = sqrt(lam1) * sqrt(2.0 * log(opac.v / th));", ["pin_invariants"]),
+    ("th_cull_inverted", "if (th > opac.v) { irec[I_EDGE] = edge; irec[I_CULL] = CULL_TH; return CULL_TH; }",
+     "if (th < opac.v) { irec[I_EDGE] = edge; irec[I_CULL] = CULL_TH; return CULL_TH; }",
+     ["pin_isotropic_on_axis"]),
+    ("lut_bin_off_by_one", "int bin = (int)floor(fb);", "int bin = (int)floor(fb) + 1;",
+     ["pin_isotropic_on_axis"]),
+    ("colour_after_transmittance_update", "col[0] += g[F_R] * alpha * T;", "col[0] += g[F_R] * alpha * test_T;",
+     ["pin_isotropic_on_axis"]),
+    ("no_condon_shortley", "double s = sqrt(2.0) * K * ((m & 1) ? -1.0 : 1.0);", "double s = sqrt(2.0) * K;",
+     ["pin_sh_basis"]),
+    ("sh_cos_sin_swapped", "Y[l * l + l + m] = jscale(jmul(pz, re), s);", "Y[l * l + l + m] = jscale(jmul(pz, im), s);",
+     ["pin_sh_basis"]),
+    ("colour_no_offset", "jet acc = jc(0.5);", "jet acc = jc(0.0);", ["pin_isotropic_on_axis", "pin_sh_colour"]),
+    ("depth_sort_descending", "if (x->depth < y->depth) return -1;", "if (x->depth < y->depth) return 1;",
+     ["pin_ideal_render", "pin_max_T"]),
+    ("rect_floor_not_ceil", "double plo = ceil(lo), phi = floor(hi);", "double plo = floor(lo), phi = floor(hi);",
+     ["pin_rect_enumeration"]),
+    ("max_T_after_update", "T = test_T;\n    last = (int32_t)(k + 1);",
+     "T = test_T;\n    if (maxT) maxT[list[k]] = T;\n    last = (int32_t)(k + 1);", ["pin_max_T"]),
+    ("backward_missing_behind_colour", "dLda += g[ch] * Ti[j] * (c[ch] - R[ch]);",
+     "dLda += g[ch] * Ti[j] * c[ch];", ["pin_backward_fd"]),
+    ("backward_mean_sign", "atomic_add_double(&G[who[j] * 9 + 0], dLdp * (-(f[F_A] * dx + f[F_B] * dy)));",
+     "atomic_add_double(&G[who[j] * 9 + 0], dLdp * (f[F_A] * dx + f[F_B] * dy));", ["pin_backward_fd"]),
+    ("backward_ignores_alpha_clamp", "if (clampa[j]) continue;", "", ["pin_backward_fd"]),
+]
+
+
+@pytest.mark.parametrize("mut", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(mut):
+    name, old, new, pins = mut
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, name + ".c")
+        open(path, "w").write(src.replace(old, new))
+        lib = oracle.compile_library(path, os.path.join(d, "lib" + name + ".so"))
+        orc = oracle.Oracle(lib)
+        caught = []
+        for pname in pins:
+            pin = getattr(oracle_pins, pname)
+            try:
+                if pname == "pin_backward_fd":
+                    pin(orc, n_check=120)
+                else:
+                    pin(orc)
+            except AssertionError:
+                caught.append(pname)
+        assert caught, "planted mistake %s passed every pin" % name
