@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the AdaGScale 3D-GS rendering hot path on GB300.
+
+Workload (seeded, synthetic, resident in HBM): 1,048,576 Gaussians drawn from
+64 surface-like clusters, rendered at 1920x1080 from 10 fixed orbit poses, all
+10 views in one launch per stage.  A step is one pass of the whole forward
+path (preprocess with the AdaGScale threshold, pair emission, key sort, tile
+ranges, blending) over the 10-view batch; `value` is frames per second in
+AdaGScale mode at the calibrated K (Sec. 3.4).  Reported beside it: plain
+3-sigma FPS on the same GPU, pairs per frame in both modes, PSNR of AdaGScale
+against plain, forward+backward ms (pose 0, L2 loss, pair selection fixed),
+per-stage times, the roofline of the dominant kernel, an end-to-end number
+through host buffers, and the CPU oracle as a baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 it runs under torchrun, one rank per GPU, each rank rendering its
+own copy of the 10-view batch (weak scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2_clusters1m_1080p"
+METRIC = "FPS (AdaGScale, 1M Gaussians, 1920x1080, 10 poses)"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP32 work per pixel-pair evaluation of Eq. 1-2 counted as the FP32-pipe
+# operations the blend needs: dx, dy (2); the quadratic form (5); exp scale
+# and opacity product (2); alpha clamp and the two threshold compares (3);
+# 1 - alpha and the transmittance product (2); the three colour FMAs and
+# alpha*T (4) = 18.  The exponential itself runs on the SFU.
+RASTER_OPS_PER_EVAL = 18
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/backward legs")
+    ap.add_argument("--views", type=int, default=10, help="views per step (profiling cases use fewer)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.strip()]
+        if self.uuid:
+            mine = [r for r in rows if len(r) > 1 and self.uuid.lower() in r[1].lower()]
+            rows = mine or rows
+        sm = [float(r[2]) for r in rows if len(r) >= 10 and r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if len(r) >= 10 and r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) >= 10:
+                for k, nm in enumerate(names):
+                    if r[6 + k].strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    try:
+        return json.load(open(MEASURED_PEAKS)), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def device_uuid():
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(scene, cam, par_kwargs, frames: int = 1) -> dict:
+    """The FP64 oracle on the host cores: `frames` full frames of the workload."""
+    import oracle
+    par = oracle.params(cam, **par_kwargs)
+    t0 = time.perf_counter()
+    for _ in range(frames):
+        oracle.render(scene, cam, par)
+    dt = time.perf_counter() - t0
+    return {"value": frames / dt, "unit": "FPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d full frame(s) (pose 0, 1920x1080, 1,048,576 Gaussians), FP64, OpenMP over tiles" % frames,
+            "seconds": dt}
+
+
+def oracle_kwargs(wp):
+    import numpy as np
+    return dict(scale_mode=1, K=float(np.float32(wp["K"])), lut=np.asarray(wp["lut"], np.float32).astype(np.float64),
+                tau=float(np.float32(1 / 255)), t_min=float(np.float32(1e-4)), alpha_max=float(np.float32(0.99)))
+
+
+def workload_params(sc, calib):
+    from paper_2604_18980_gb300 import calibrate as C
+    wp = C.load_params(WORKLOAD)
+    if wp is None:
+        lut = C.calibrate_lut(sc, calib)
+        K, p = C.search_K(sc, calib, lut, C.TARGET_PSNR["c2"])
+        wp = dict(K=float(K), lut=[float(x) for x in lut], target_psnr=C.TARGET_PSNR["c2"], calib_psnr=p,
+                  source="calibrated in this run")
+    else:
+        wp = dict(wp, source="workload_params.json")
+    return wp
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step renders one frame of the workload on the host cores."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    from paper_2604_18980_gb300 import calibrate as C
+    from paper_2604_18980_gb300 import synth
+    import oracle
+    wp = C.load_params(WORKLOAD)
+    if wp is None:
+        print(json.dumps({"impl": "reference", "unavailable": "workload_params.json (K, T_up) not present"}))
+        return 0
+    scene, cams, _ = synth.workload(WORKLOAD)
+    kw = oracle_kwargs(wp)
+    times = []
+    for s in range(args.warmup + args.steps):
+        cam = cams[s % len(cams)]
+        par = oracle.params(cam, **kw)
+        t0 = time.perf_counter()
+        oracle.render(scene, cam, par)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    fps = len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "FPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": 1048576, "width": 1920, "height": 1080,
+                       "views": 10, "scale_mode": "adagscale", "K": wp["K"], "step": "one frame per step"},
+            "cpu_baseline": {"value": fps, "unit": "FPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "one full 1920x1080 frame per step, poses cycled"},
+            "e2e": {"value": fps, "unit": "FPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_18980_gb300 import binding as B
+    from paper_2604_18980_gb300 import build as cuda_build
+    from paper_2604_18980_gb300 import calibrate as C
+    from paper_2604_18980_gb300 import render as R
+    from paper_2604_18980_gb300 import synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cuda_build.build()
+    scene_np, cams, calib = synth.workload(WORKLOAD)
+    cams = cams[:args.views]
+    sc = R.scene_to_device(scene_np)
+    wp = workload_params(sc, calib)
+    V = len(cams)
+    ada = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_stats=True)
+    plain = R.Renderer(sc, cams, B.AGS_SCALE_PLAIN)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # evaluation counts of the blend (separate, untimed pass)
+    ada.stats.zero_()
+    ada.forward()
+    ada.check()
+    evals_per_step = int(ada.stats[0].item())
+    ada_pairs = ada.pairs()
+    passes = math.ceil(ada.end_bit / ada.digit_bits)
+    launches_per_step = 1 + 1 + (2 + passes + 1) + 1   # preprocess, emit, hist+scan+passes+ranges, blend
+
+    # warm-up
+    for _ in range(args.warmup):
+        ada.forward()
+    ada.stats = None      # the timed region runs without the counters
+    barrier()
+
+    # timed region: events between stages on the launching stream
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clocks = ClockSampler(device_uuid())
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        e = ev[s]
+        e[0].record(stream)
+        ada.preprocess()
+        e[1].record(stream)
+        ada.emit()
+        e[2].record(stream)
+        ada.sort()
+        e[3].record(stream)
+        ada.rasterize()
+        e[4].record(stream)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end))
+    ada.check()
+    stage_names = ["preprocess", "emit", "sort", "raster"]
+    stage_ms = {nm: sum(ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(args.steps)) / args.steps
+                for k, nm in enumerate(stage_names)}
+    ms_step = ms_total / args.steps
+    fps = world * V * args.steps / (ms_total / 1000.0)
+
+    extras = {}
+    if not args.no_extras:
+        # plain 3-sigma on the same GPU
+        for _ in range(args.warmup):
+            plain.forward()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            plain.forward()
+        b.record(stream)
+        barrier()
+        plain.check()
+        plain_ms = max_over_ranks(a.elapsed_time(b)) / args.steps
+        extras["plain"] = {"fps": world * V * 1000.0 / plain_ms, "ms_per_step": plain_ms,
+                           "pairs_per_frame": plain.pairs() / V}
+        img_a = ada.forward().clone()
+        img_p = plain.forward().clone()
+        extras["psnr_adagscale_vs_plain_db"] = C.psnr(img_a, img_p)
+        del img_a, img_p
+
+        # end to end through host buffers: params H2D, render, images D2H, every step
+        host = {k: v.cpu().pin_memory() for k, v in sc.items()}
+        out_host = torch.empty(ada.image.shape, dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = out_host.numel() * out_host.element_size()
+        for _ in range(2):
+            for k in host:
+                sc[k].copy_(host[k], non_blocking=True)
+            ada.forward()
+            out_host.copy_(ada.image, non_blocking=True)
+        barrier()
+        a.record(stream)
+        for _ in range(args.steps):
+            for k in host:
+                sc[k].copy_(host[k], non_blocking=True)
+            ada.forward()
+            out_host.copy_(ada.image, non_blocking=True)
+        b.record(stream)
+        barrier()
+        e2e_ms = max_over_ranks(a.elapsed_time(b)) / args.steps
+        extras["e2e"] = {"value": world * V * 1000.0 / e2e_ms, "unit": "FPS", "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+        del host, out_host
+
+        # forward + backward: pose 0, L2 loss against the plain render of a perturbed scene
+        pert = R.scene_to_device(synth.perturb_scene(scene_np, 5005))
+        tgt_r = R.Renderer(pert, cams[:1], B.AGS_SCALE_PLAIN)
+        target = tgt_r.forward().clone()
+        del tgt_r, pert
+        fb = R.Renderer(sc, cams[:1], B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_backward=True)
+        grads = {k: torch.empty_like(v) for k, v in sc.items()}
+        inv = 2.0 / target.numel()
+
+        def fwd_bwd():
+            img = fb.forward()
+            fb.backward((img - target) * inv, grads)
+
+        for _ in range(args.warmup):
+            fwd_bwd()
+        barrier()
+        a.record(stream)
+        for _ in range(args.steps):
+            fwd_bwd()
+        b.record(stream)
+        barrier()
+        fb.check()
+        extras["fwd_bwd_ms"] = max_over_ranks(a.elapsed_time(b)) / args.steps
+        del fb, grads, target
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant stage
+    pk, pk_src = peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    roof = roofline(dom, stage_ms[dom], ada, evals_per_step, pk, pk_src, passes, clk)
+    line = {
+        "metric": METRIC, "value": fps, "unit": "FPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; stands in for the paper's trained scenes)",
+        "config": {"workload": WORKLOAD, "gaussians": ada.n, "width": ada.W, "height": ada.H, "views_per_step": V,
+                   "scale_mode": "adagscale", "K": wp["K"], "lut_source": wp.get("source"),
+                   "pairs_per_frame": ada_pairs / V, "sort_passes": passes,
+                   "l2": "inputs larger than L2 (params 236 MB, pairs %.1f GB per step)" % (ada_pairs * 24 / 1e9),
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "stage_ms": stage_ms,
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    line.update({k: v for k, v in extras.items() if k != "e2e"})
+    if "e2e" in extras:
+        line["e2e"] = extras["e2e"]
+    if not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(scene_np, cams[0], oracle_kwargs(wp))
+        except Exception as exc:   # report, never fail the benchmark line
+            line["cpu_baseline"] = {"value": None, "unit": "FPS", "kind": "oracle", "error": str(exc)}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):
+    V, n = r.V, r.n
+    P = r.pairs()
+    if stage == "raster":
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        import torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12           # FP32 lanes x clock, Tops/s
+        achieved = evals * RASTER_OPS_PER_EVAL / (ms / 1e3) / 1e12
+        return {"kernel": "raster_kernel", "bound": "alu", "achieved": achieved, "peak": peak_ops,
+                "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                "work": "%d pixel-pair evaluations x %d FP32 ops" % (evals, RASTER_OPS_PER_EVAL),
+                "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (%s)" % (sms, sm_mhz, pk_src)}
+    hbm = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
+    if stage == "sort":
+        byts = P * 8 + passes * P * 24 + P * 8 + V * r.T * 8
+        kern = "onesweep_kernel (+hist, ranges)"
+    elif stage == "emit":
+        byts = V * n * 12 + P * 12
+        kern = "emit_kernel"
+    else:
+        byts = V * n * (44 + 4) + V * n * 192 + V * n * 65
+        kern = "preprocess_kernel"
+    achieved = byts / (ms / 1e3) / 1e9
+    return {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": pk_src}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,237 @@
+/*
+ * ags.h -- C ABI of the AdaGScale 3D Gaussian Splatting hot path for one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The rendering pipeline (AdaGScale, arXiv 2604.18980, Sec. 2.1 and Fig. 1) has
+ * four stages, one entry point each, plus the hand-written backward:
+ *
+ *   ags_preprocess          cull, EWA projection, SH colour, depth, and the
+ *                           AdaGScale threshold Th (Eq. 10), opacity cull and
+ *                           adjusted footprint (Sec. 3.3)
+ *   ags_emit_pairs          Gaussian-tile pairs with 64-bit (tile | depth) keys
+ *                           (Sec. 2.1, Sec. 3.3 "Gaussian-tile pair generation")
+ *   ags_sort                stable LSD radix sort of the pairs (Sec. 2.1) and the
+ *                           per-tile [start, end) ranges
+ *   ags_rasterize           per-16x16-tile front-to-back alpha blending, Eq. 1
+ *                           and Eq. 2, always with the original covariance and
+ *                           tau (Sec. 3.3 "dual-size strategy")
+ *   ags_rasterize_backward  adjoint of the blend and of the preprocess (not in
+ *                           the paper; the pair selection is held fixed)
+ *   ags_calibrate_lut       T_up(depth) look-up table from per-Gaussian maximum
+ *                           transmittance (Sec. 3.4)
+ *
+ * Conventions (all entry points):
+ *  - Every pointer is a DEVICE pointer owned by the caller unless it is marked
+ *    "host".  The library allocates no memory and keeps no mutable global
+ *    state; scratch memory ("workspace") is passed in by the caller, sized by
+ *    the matching *_workspace_bytes() call.
+ *  - `stream` is a cudaStream_t passed as void*.  Every call only enqueues
+ *    work on that stream and returns without synchronising, so a sequence of
+ *    calls can be captured in a CUDA graph.
+ *  - The return value reports what the host can detect: invalid arguments
+ *    (AGS_ERR_INVALID_ARG, nothing is launched) and launch failures
+ *    (AGS_ERR_CUDA).  What only the device can detect -- pair capacity
+ *    overflow, a bounded wait that gave up, non-finite inputs -- is written to
+ *    the caller's device status block `d_status` (int64_t[4], zeroed with
+ *    ags_status_reset) and read back by ags_check.  No kernel ever traps.
+ *  - Arrays are structure-of-arrays fp32 unless stated; `n` Gaussians, `views`
+ *    cameras of one common width and height rendered in one launch per stage.
+ *  - Tiles are 16x16 pixels; pixel centres sit at integer coordinates.
+ *  - Gaussian-tile pair counts are limited to AGS_MAX_PAIRS per sort call.
+ */
+#ifndef AGS_H
+#define AGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AGS_TILE 16
+#define AGS_MAX_VIEWS 32
+#define AGS_MAX_LUT_BINS 32
+#define AGS_MAX_PAIRS ((int64_t)1 << 30)
+
+typedef enum {
+  AGS_OK = 0,
+  AGS_ERR_INVALID_ARG = 1,
+  AGS_ERR_CAPACITY = 2,     /* more pairs than `capacity`; detail = pairs needed */
+  AGS_ERR_TIMEOUT = 3,      /* a bounded device wait gave up; detail = stage id */
+  AGS_ERR_CUDA = 4,         /* a CUDA launch or runtime call failed */
+  AGS_ERR_NUMERIC = 5       /* non-finite Gaussian parameters were culled; detail = count */
+} ags_status;
+
+typedef enum { AGS_SCALE_PLAIN = 0, AGS_SCALE_ADAGSCALE = 1 } ags_scale_mode;
+
+/* Pinhole camera (host struct).  viewmat is the row-major 3x4 world->camera
+ * transform (+x right, +y down, +z forward): t = R m + t_cam.  The EWA
+ * frustum clamp uses tan(fov/2) = 0.5*width/fx and 0.5*height/fy. */
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float viewmat[12];
+  float campos[3];
+  float near_z;             /* 0.2 in 3D-GS */
+} ags_camera;
+
+/* Render parameters (host struct). */
+typedef struct {
+  int32_t scale_mode;       /* ags_scale_mode */
+  int32_t sh_degree;        /* 0..3 */
+  int32_t lut_bins;         /* 1..AGS_MAX_LUT_BINS; 20 in the paper (Sec. 3.4) */
+  float K;                  /* peripheral-loss budget K >= 0 (Eq. 5, Eq. 10) */
+  float tau;                /* alpha threshold, 1/255 (Sec. 2.1) */
+  float t_min;              /* transmittance stop, 1e-4 (Sec. 2.1) */
+  float alpha_max;          /* alpha clamp, 0.99 (3D-GS) */
+  float lut_depth_max;      /* depth range [0, lut_depth_max] of the LUT; 100 (Sec. 3.4) */
+  float lut[AGS_MAX_LUT_BINS]; /* T_up per depth bin (Sec. 3.2 Eq. 7, Sec. 3.4) */
+  float bg[3];              /* background colour added with the final transmittance */
+} ags_params;
+
+/* Gaussian parameters (pointers to device memory, SoA fp32). */
+typedef struct {
+  const float* mean;          /* [3][n] world position */
+  const float* log_scale;     /* [3][n] log standard deviations */
+  const float* quat;          /* [4][n] rotation (w,x,y,z), any non-zero norm */
+  const float* opacity_logit; /* [n]    opacity = sigmoid(logit) */
+  const float* sh;            /* [(sh_degree+1)^2][3][n] real SH, index l*l+l+m */
+  int64_t n;
+} ags_gaussians;
+
+/* Per-view preprocess results (device memory, index e = view*n + i). */
+typedef struct {
+  float* splat;             /* [views*n][12], 16-byte aligned:
+                               u v A B | C opacity r g | b Th 0 0
+                               (u,v) 2D mean in pixels, (A,B,C) conic of the
+                               ORIGINAL dilated 2D covariance */
+  float* depth;             /* [views*n] view-space z */
+  uint16_t* rect;           /* [views*n][4] tile rectangle x0 y0 x1 y1 (end
+                               exclusive); all zero for culled Gaussians */
+  uint32_t* tiles_touched;  /* [views*n] (x1-x0)*(y1-y0), nullable */
+  uint8_t* flags;           /* [views*n] bit0-2 colour clamped at 0, bit3/bit4
+                               EWA x/y frustum clamp, bit7 culled */
+} ags_projected;
+
+/* Device status block: int64_t[4] = {status code, detail, non-finite count, reserved}. */
+
+/* ---------------------------------------------------------------------- */
+
+/* Zero a device status block (int64_t[4]) on `stream`. */
+ags_status ags_status_reset(int64_t* d_status, void* stream);
+
+/* Synchronise `stream`, read the device status block and return its code;
+ * *detail (host, nullable) receives its detail word. */
+ags_status ags_check(const int64_t* d_status, void* stream, int64_t* detail);
+
+/* Human-readable name of a status code (static string). */
+const char* ags_status_string(ags_status s);
+
+/* Preprocess (Sec. 2.1 preprocessing; Eq. 10 and Sec. 3.3 in AdaGScale mode).
+ * For every view v and Gaussian i: frustum (near-plane) cull, EWA projection
+ * of the 3D covariance R S S^T R^T to the dilated 2D covariance (+0.3 I), its
+ * conic, 2D mean, depth, opacity = sigmoid(logit), colour = SH + 0.5 clamped
+ * at 0, and the footprint radius: ceil(3 sqrt(lambda_max)) in plain mode; in
+ * AdaGScale mode Th = K / (T_up(depth) 2 pi sqrt(det)) + tau (Eq. 10), culled
+ * when Th > opacity, else radius ceil(sqrt(lambda_max) min(3, sqrt(2 ln(opacity/Th)))).
+ * The rectangle holds every tile containing a pixel centre within the square
+ * [u-r, u+r] x [v-r, v+r].  cams (host) has `views` entries of equal size.
+ * Non-finite parameters are culled and counted in d_status[2]. */
+ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* cams, int32_t views,
+                          const ags_params* params, const ags_projected* out,
+                          int64_t* d_status, void* stream);
+
+/* Scratch bytes needed by ags_emit_pairs for views*n Gaussians. */
+size_t ags_emit_workspace_bytes(int64_t n, int32_t views);
+
+/* Pair emission (Sec. 2.1, Sec. 3.3).  Exclusive prefix sum of the rectangle
+ * areas (single pass, decoupled look-back) and one pair per covered tile, in
+ * Gaussian order and row-major within a rectangle:
+ *   key = ((view * tiles_per_view + tile) << 32) | float_bits(depth),
+ *   val = view * n + i.
+ * `order` (nullable, [views*n]) visits the Gaussians in that order instead
+ * (a permutation of 0..views*n-1).  *d_num_pairs (device int64) receives the
+ * total.  Pairs beyond `capacity` are not written; the status block then
+ * holds AGS_ERR_CAPACITY and the total needed. */
+ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32_t views,
+                          const ags_camera* cams, const uint32_t* order,
+                          uint64_t* keys, uint32_t* vals, int64_t capacity,
+                          int64_t* d_num_pairs, int64_t* d_status,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* Scratch bytes needed by ags_sort for up to `capacity` pairs. */
+size_t ags_sort_workspace_bytes(int64_t capacity);
+
+/* Stable LSD radix sort of (keys, vals) by key bits [begin_bit, end_bit)
+ * (Sec. 2.1 sorting stage): one global-histogram pass, then one single-pass
+ * ("onesweep") scatter per digit of `digit_bits` (4..8) bits, with warp-level
+ * match/ballot ranking and decoupled look-back between blocks.  The count is
+ * read on the device from *d_num_pairs (<= capacity <= AGS_MAX_PAIRS).
+ * The sorted result lands in (keys, vals) when the number of digit passes is
+ * even and in (keys_alt, vals_alt) when it is odd; *result_in_alt (host)
+ * reports which.  If `ranges` is non-null it then receives, for each of
+ * `num_ranges` tiles, [start, end) of that tile's pairs (uint32[num_ranges][2],
+ * zero for empty tiles), the tile being key >> 32. */
+ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                    const int64_t* d_num_pairs, int64_t capacity, int32_t begin_bit,
+                    int32_t end_bit, int32_t digit_bits, uint32_t* ranges, int64_t num_ranges,
+                    int32_t* result_in_alt, int64_t* d_status, void* ws, size_t ws_bytes,
+                    void* stream);
+
+/* Blending (Eq. 1, Eq. 2; Sec. 3.3 dual size).  One CTA per 16x16 tile of
+ * each view; per pixel, front to back over the tile's sorted pairs:
+ *   p = -(A dx^2 + C dy^2)/2 - B dx dy, skip if p > 0,
+ *   alpha = min(alpha_max, opacity e^p), skip if alpha < tau,
+ *   stop (without blending) when T (1 - alpha) < t_min,
+ *   C += alpha T rgb, T *= 1 - alpha.
+ * Always the original conic and tau, whatever the scale mode.
+ * Outputs: image [views][3][H][W] = C + T bg; final_T [views][H][W] and
+ * n_contrib [views][H][W] (1-based position in the tile list of the last
+ * blended pair), both nullable (the backward needs them); max_T [views*n]
+ * (nullable; zeroed by the caller) receives, per Gaussian, the largest T seen
+ * before blending it (calibration, Sec. 3.4); stats (nullable uint64[2])
+ * accumulates {pixel-pair evaluations, blended pairs}. */
+ags_status ags_rasterize(const ags_projected* proj, int64_t n, const uint32_t* sorted_vals,
+                         const uint32_t* ranges, const ags_camera* cams, int32_t views,
+                         const ags_params* params, float* image, float* final_T,
+                         uint32_t* n_contrib, float* max_T, uint64_t* stats,
+                         int64_t* d_status, void* stream);
+
+/* T_up look-up table (Sec. 3.4): for every Gaussian and view with
+ * max_T > 0, bin its depth into lut_bins uniform intervals of
+ * [0, lut_depth_max] (depths beyond go to the last bin) and take the maximum.
+ * lut_out [lut_bins] fp32; bins no Gaussian reached are set to 1.0. */
+ags_status ags_calibrate_lut(const float* max_T, const float* depth, int64_t count,
+                             int32_t lut_bins, float lut_depth_max, float* lut_out,
+                             void* stream);
+
+/* Scratch bytes needed by ags_rasterize_backward. */
+size_t ags_backward_workspace_bytes(int64_t n, int32_t views);
+
+/* Backward of ags_rasterize and ags_preprocess with the pair lists held
+ * fixed (not in the paper).  dL_dimage [views][3][H][W].  The blend adjoint
+ * replays each pixel from its last blended pair backwards, recovering T by
+ * division by (1 - alpha); the preprocess adjoint chains through the EWA
+ * projection, the covariance, the quaternion normalisation, the sigmoid and
+ * the SH basis, summing over views.  Clamped quantities (alpha at
+ * alpha_max, colour at 0, the EWA frustum clamp) pass no gradient; Th and
+ * the footprint pass none either.  Outputs are overwritten:
+ * g_mean [3][n], g_log_scale [3][n], g_quat [4][n], g_opacity_logit [n],
+ * g_sh [(sh_degree+1)^2][3][n]. */
+ags_status ags_rasterize_backward(const ags_gaussians* g, const ags_camera* cams, int32_t views,
+                                  const ags_params* params, const ags_projected* proj,
+                                  const uint32_t* sorted_vals, const uint32_t* ranges,
+                                  const float* final_T, const uint32_t* n_contrib,
+                                  const float* dL_dimage, float* g_mean, float* g_log_scale,
+                                  float* g_quat, float* g_opacity_logit, float* g_sh,
+                                  int64_t* d_status, void* ws, size_t ws_bytes, void* stream);
+
+/* Library version string (static). */
+const char* ags_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AGS_H */

@@ -1,0 +1,155 @@
+// preprocess.cu -- per-Gaussian preprocess with the AdaGScale threshold.
+//
+// Paper: AdaGScale (arXiv 2604.18980).  Sec. 2.1 (preprocessing: cull,
+// projected 2D mean and covariance, colour, depth), Eq. 10 (Th), Sec. 3.3
+// (cull when Th > opacity; Th shrinks only the footprint used by the tile
+// test), Sec. 3.4 (T_up from a depth look-up table).
+//
+// One thread per (view, Gaussian).  The structure-of-arrays inputs are read
+// with coalesced loads; the 48 SH floats are read only for Gaussians that
+// survive and touch at least one tile.  Outputs per survivor: a 48-byte splat
+// record (three 16-byte stores), depth, the tile rectangle (one 8-byte store),
+// the tile count and a flag byte.
+#include "project.cuh"
+
+namespace ags {
+
+struct PreIn {
+  const float* mean;
+  const float* ls;
+  const float* quat;
+  const float* logit;
+  const float* sh;
+};
+
+struct PreOut {
+  float* splat;
+  float* depth;
+  uint16_t* rect;
+  uint32_t* touched;
+  uint8_t* flags;
+};
+
+__device__ __forceinline__ void write_culled(const PreOut& o, int64_t e) {
+  reinterpret_cast<uint2*>(o.rect)[e] = make_uint2(0u, 0u);
+  if (o.touched) o.touched[e] = 0u;
+  o.flags[e] = kFlagCulled;
+}
+
+// Tiles [t0, t1) holding a pixel centre in [lo, hi] on an axis of `len` pixels.
+__device__ __forceinline__ void tile_span(float lo, float hi, int len, int& t0, int& t1) {
+  float plo = fmaxf(ceilf(lo), 0.f);
+  float phi = fminf(floorf(hi), (float)(len - 1));
+  if (!(plo <= phi)) { t0 = t1 = 0; return; }
+  t0 = (int)plo >> 4;
+  t1 = ((int)phi >> 4) + 1;
+}
+
+__global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, const __grid_constant__ CamBatch cams,
+                                                         const __grid_constant__ DevParams P, PreOut out,
+                                                         int64_t* status) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int view = blockIdx.y;
+  const DevCam& C = cams.c[view];
+  const int64_t e = (int64_t)view * n + i;
+
+  float m[3], ls[3], q[4];
+#pragma unroll
+  for (int k = 0; k < 3; k++) m[k] = __ldg(in.mean + k * n + i);
+#pragma unroll
+  for (int k = 0; k < 3; k++) ls[k] = __ldg(in.ls + k * n + i);
+#pragma unroll
+  for (int k = 0; k < 4; k++) q[k] = __ldg(in.quat + k * n + i);
+  float logit = __ldg(in.logit + i);
+  bool finite = isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && isfinite(ls[0]) && isfinite(ls[1]) &&
+                isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]) &&
+                isfinite(logit);
+  if (!finite) {
+    if (view == 0) atomicAdd(reinterpret_cast<unsigned long long*>(status + 2), 1ull);
+    write_culled(out, e);
+    return;
+  }
+  Proj pj;
+  if (!project_geometry(C, m, ls, q, logit, pj)) {
+    write_culled(out, e);
+    return;
+  }
+  // footprint radius: plain 3-sigma, or AdaGScale (Eq. 10, Sec. 3.3)
+  float th = P.tau;
+  float rf;
+  if (P.scale_mode == AGS_SCALE_ADAGSCALE) {
+    int bin = (int)fminf(pj.t[2] * P.lut_scale, (float)(P.lut_bins - 1));   // depth > 0: truncation = floor
+    float tup = P.lut[bin];
+    if (!(tup > 0.f)) { write_culled(out, e); return; }
+    th = P.K / (tup * 6.2831853f * sqrtf(pj.det)) + P.tau;
+    if (th > pj.opac) { write_culled(out, e); return; }
+    rf = ceilf(sqrtf(pj.lam1) * fminf(3.f, sqrtf(2.f * logf(pj.opac / th))));
+  } else {
+    rf = ceilf(3.f * sqrtf(pj.lam1));
+  }
+  int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+  if (rf > 0.f) {
+    tile_span(pj.u - rf, pj.u + rf, C.W, x0, x1);
+    tile_span(pj.v - rf, pj.v + rf, C.H, y0, y1);
+  }
+  uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+  if (touched == 0u) { write_culled(out, e); return; }
+
+  // colour: SH at the world-space direction from the camera centre
+  float dx = m[0] - C.campos[0], dy = m[1] - C.campos[1], dz = m[2] - C.campos[2];
+  float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+  float Y[16];
+  sh_basis(P.sh_degree, dx * il, dy * il, dz * il, Y);
+  const int nc = (P.sh_degree + 1) * (P.sh_degree + 1);
+  float rgb[3] = {0.5f, 0.5f, 0.5f};
+  for (int k = 0; k < nc; k++) {
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(__ldg(in.sh + (int64_t)(k * 3 + ch) * n + i), Y[k], rgb[ch]);
+  }
+  uint8_t flags = (uint8_t)pj.fclamp;
+#pragma unroll
+  for (int ch = 0; ch < 3; ch++) {
+    if (!isfinite(rgb[ch])) {
+      if (view == 0) atomicAdd(reinterpret_cast<unsigned long long*>(status + 2), 1ull);
+      write_culled(out, e);
+      return;
+    }
+    if (rgb[ch] < 0.f) { rgb[ch] = 0.f; flags |= (uint8_t)(1 << ch); }
+  }
+  float4* sp = reinterpret_cast<float4*>(out.splat + e * kSplatFloats);
+  sp[0] = make_float4(pj.u, pj.v, pj.A, pj.B);
+  sp[1] = make_float4(pj.C, pj.opac, rgb[0], rgb[1]);
+  sp[2] = make_float4(rgb[2], th, 0.f, 0.f);
+  out.depth[e] = pj.t[2];
+  reinterpret_cast<uint2*>(out.rect)[e] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16),
+                                                     (uint32_t)x1 | ((uint32_t)y1 << 16));
+  if (out.touched) out.touched[e] = touched;
+  out.flags[e] = flags;
+}
+
+}  // namespace ags
+
+extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* cams, int32_t views,
+                                     const ags_params* params, const ags_projected* out, int64_t* d_status,
+                                     void* stream) {
+  using namespace ags;
+  if (!g || !out || !d_status) return AGS_ERR_INVALID_ARG;
+  if (g->n < 0 || g->n > (int64_t)1 << 31) return AGS_ERR_INVALID_ARG;
+  CamBatch cb;
+  DevParams dp;
+  ags_status s = build_cams(cams, views, &cb);
+  if (s != AGS_OK) return s;
+  s = build_params(params, &dp);
+  if (s != AGS_OK) return s;
+  if ((int64_t)views * g->n >= ((int64_t)1 << 32)) return AGS_ERR_INVALID_ARG;
+  if (g->n == 0) return AGS_OK;
+  if (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->sh) return AGS_ERR_INVALID_ARG;
+  if (!out->splat || !out->depth || !out->rect || !out->flags) return AGS_ERR_INVALID_ARG;
+  if (((uintptr_t)out->splat & 15u) || ((uintptr_t)out->rect & 7u)) return AGS_ERR_INVALID_ARG;
+  PreIn in{g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
+  PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags};
+  dim3 grid((unsigned)((g->n + 255) / 256), (unsigned)views);
+  preprocess_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(in, g->n, cb, dp, po, d_status);
+  return launch_status(cudaGetLastError());
+}

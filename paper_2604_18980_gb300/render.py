@@ -1,0 +1,169 @@
+"""Frame pipeline over libags with PyTorch-managed device memory.
+
+``Renderer`` owns the device buffers of one batch of views and enqueues the
+four stages (preprocess, pair emission, sort, blend) on the current CUDA
+stream -- one launch sequence per stage for all views, no host
+synchronisation, so a whole frame can be captured in a CUDA graph.  PyTorch
+only provides memory, streams and graphs; every step runs in libags kernels.
+``AgsRender`` wraps forward and backward as a ``torch.autograd.Function``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+SCENE_KEYS = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+
+
+def scene_to_device(scene: dict, device="cuda") -> dict:
+    return {k: torch.as_tensor(np.ascontiguousarray(scene[k]), dtype=torch.float32).to(device).contiguous()
+            for k in SCENE_KEYS}
+
+
+def tiles_per_view(cam: dict) -> int:
+    return ((cam["width"] + B.AGS_TILE - 1) // B.AGS_TILE) * ((cam["height"] + B.AGS_TILE - 1) // B.AGS_TILE)
+
+
+def key_end_bit(views: int, tiles: int) -> int:
+    """Highest key bit + 1: 32 depth bits plus the bits of the largest tile id."""
+    return 32 + max(1, int(views * tiles - 1).bit_length())
+
+
+class Renderer:
+    """Buffers and launch sequence for rendering `scene` into `cams` (one batch)."""
+
+    def __init__(self, scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_PLAIN, K: float = 0.0, lut=None,
+                 sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 8,
+                 headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False):
+        self.scene = scene
+        self.cams = list(cams)
+        self.V = len(self.cams)
+        self.n = int(scene["opacity_logit"].shape[0])
+        self.W, self.H = self.cams[0]["width"], self.cams[0]["height"]
+        self.T = tiles_per_view(self.cams[0])
+        self.device = scene["mean"].device
+        self.digit_bits = digit_bits
+        self.set_params(scale_mode, K, lut, sh_degree, bg)
+        dev, V, n = self.device, self.V, self.n
+        self.proj = dict(splat=torch.empty(V * n * 12, dtype=torch.float32, device=dev),
+                         depth=torch.empty(V * n, dtype=torch.float32, device=dev),
+                         rect=torch.empty(V * n * 4, dtype=torch.int16, device=dev),
+                         tiles_touched=torch.empty(V * n, dtype=torch.int32, device=dev),
+                         flags=torch.empty(V * n, dtype=torch.uint8, device=dev))
+        self.status = torch.zeros(4, dtype=torch.int64, device=dev)
+        self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.ws_emit = torch.empty(max(B.ags_emit_workspace_bytes(n, V), 16), dtype=torch.uint8, device=dev)
+        self.ranges = torch.empty(V * self.T * 2, dtype=torch.int32, device=dev)
+        self.image = torch.empty(V, 3, self.H, self.W, dtype=torch.float32, device=dev)
+        self.final_T = torch.empty(V, self.H, self.W, dtype=torch.float32, device=dev)
+        self.n_contrib = torch.empty(V, self.H, self.W, dtype=torch.int32, device=dev)
+        self.stats = torch.zeros(2, dtype=torch.int64, device=dev) if want_stats else None
+        if capacity is None:
+            capacity = max(1024, int(math.ceil(self.count_pairs() * headroom)))
+        self.alloc_pairs(capacity)
+        self.ws_bwd = None
+        if want_backward:
+            self.ws_bwd = torch.empty(B.ags_backward_workspace_bytes(n, V), dtype=torch.uint8, device=dev)
+
+    # -- configuration -------------------------------------------------------
+    def set_params(self, scale_mode=None, K=None, lut=None, sh_degree=None, bg=None):
+        prev = getattr(self, "_pargs", dict(scale_mode=B.AGS_SCALE_PLAIN, K=0.0, lut=None, sh_degree=3,
+                                            bg=(0.0, 0.0, 0.0)))
+        args = dict(scale_mode=prev["scale_mode"] if scale_mode is None else scale_mode,
+                    K=prev["K"] if K is None else K, lut=prev["lut"] if lut is None else lut,
+                    sh_degree=prev["sh_degree"] if sh_degree is None else sh_degree,
+                    bg=prev["bg"] if bg is None else bg)
+        self._pargs = args
+        self.params = B.params(**args)
+
+    def alloc_pairs(self, capacity: int):
+        if capacity >= B.AGS_MAX_PAIRS:
+            raise ValueError("more than %d pairs in one batch; render fewer views at once" % B.AGS_MAX_PAIRS)
+        dev = self.device
+        self.capacity = int(capacity)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=dev)
+        self.keys_alt = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+        self.vals_alt = torch.empty(self.capacity, dtype=torch.int32, device=dev)
+        self.ws_sort = torch.empty(B.ags_sort_workspace_bytes(self.capacity), dtype=torch.uint8, device=dev)
+
+    def count_pairs(self) -> int:
+        """Preprocess + emission with zero capacity; returns the pair count (synchronises)."""
+        B.ags_status_reset(self.status)
+        B.ags_preprocess(self.scene, self.cams, self.params, self.proj, self.status)
+        B.ags_emit_pairs(self.proj, self.n, self.cams, None, None, 0, self.num_pairs, self.status, self.ws_emit)
+        B.ags_status_reset(self.status)
+        return int(self.num_pairs.item())
+
+    @property
+    def end_bit(self) -> int:
+        return key_end_bit(self.V, self.T)
+
+    # -- stages ---------------------------------------------------------------
+    def preprocess(self):
+        B.ags_preprocess(self.scene, self.cams, self.params, self.proj, self.status)
+
+    def emit(self):
+        B.ags_emit_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity, self.num_pairs,
+                         self.status, self.ws_emit)
+
+    def sort(self):
+        alt = B.ags_sort(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity, 0,
+                         self.end_bit, self.digit_bits, self.ranges, self.V * self.T, self.status, self.ws_sort)
+        self.sorted_keys = self.keys_alt if alt else self.keys
+        self.sorted_vals = self.vals_alt if alt else self.vals
+
+    def rasterize(self, max_T=None):
+        B.ags_rasterize(self.proj, self.n, self.sorted_vals, self.ranges, self.cams, self.params, self.image,
+                        self.final_T, self.n_contrib, self.status, max_T=max_T, stats=self.stats)
+
+    def forward(self, max_T=None):
+        """Enqueue the whole frame on the current stream; returns the image tensor."""
+        self.preprocess()
+        self.emit()
+        self.sort()
+        self.rasterize(max_T)
+        return self.image
+
+    def backward(self, dL_dimage: torch.Tensor, grads: dict | None = None) -> dict:
+        if self.ws_bwd is None:
+            self.ws_bwd = torch.empty(B.ags_backward_workspace_bytes(self.n, self.V), dtype=torch.uint8,
+                                      device=self.device)
+        if grads is None:
+            grads = {k: torch.empty_like(self.scene[k]) for k in SCENE_KEYS}
+        B.ags_rasterize_backward(self.scene, self.cams, self.params, self.proj, self.sorted_vals, self.ranges,
+                                 self.final_T, self.n_contrib, dL_dimage.contiguous(), grads, self.status,
+                                 self.ws_bwd)
+        return grads
+
+    def check(self):
+        """Synchronise and raise on a device-side error (capacity, timeout)."""
+        code, detail = B.ags_check(self.status, raise_on_error=False)
+        if code not in (B.AGS_OK, B.AGS_ERR_NUMERIC):
+            raise B.AgsError(code, "render", detail)
+        return code, detail
+
+    def pairs(self) -> int:
+        return int(self.num_pairs.item())
+
+
+class AgsRender(torch.autograd.Function):
+    """image = render(params); backward through libags with the pair lists of the forward held fixed."""
+
+    @staticmethod
+    def forward(ctx, mean, log_scale, quat, opacity_logit, sh, renderer: Renderer):
+        renderer.scene = dict(mean=mean.detach().contiguous(), log_scale=log_scale.detach().contiguous(),
+                              quat=quat.detach().contiguous(), opacity_logit=opacity_logit.detach().contiguous(),
+                              sh=sh.detach().contiguous())
+        img = renderer.forward()
+        ctx.renderer = renderer
+        return img.clone()
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        g = ctx.renderer.backward(grad_image)
+        return g["mean"], g["log_scale"], g["quat"], g["opacity_logit"], g["sh"], None

@@ -1,0 +1,156 @@
+"""Comparison helpers between the CUDA path (through the C ABI) and the oracle."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2604_18980_gb300 import binding as B
+from paper_2604_18980_gb300 import render as R
+
+IMG_TOL = 2e-3          # max-abs per channel outside edge-flagged pixels
+PSNR_MIN = 60.0         # dB, over all pixels
+
+
+def gpu_render(scene_np, cams, scale_mode=0, K=0.0, lut=None, bg=(0.0, 0.0, 0.0), sh_degree=3, capacity=None,
+               digit_bits=8, want_stats=False):
+    scene = R.scene_to_device(scene_np)
+    r = R.Renderer(scene, cams, scale_mode, K, lut, sh_degree, bg, capacity=capacity, digit_bits=digit_bits,
+                   want_stats=want_stats)
+    r.forward()
+    r.check()
+    return r
+
+
+def oracle_params(cam, scale_mode=0, K=0.0, lut=None, bg=(0.0, 0.0, 0.0), sh_degree=3):
+    lut32 = None if lut is None else np.asarray(lut, dtype=np.float32).astype(np.float64)
+    return oracle.params(cam, scale_mode=scale_mode, K=float(np.float32(K)), lut=lut32, sh_degree=sh_degree,
+                         bg=tuple(float(np.float32(b)) for b in bg), tau=float(np.float32(1.0 / 255.0)),
+                         t_min=float(np.float32(1e-4)), alpha_max=float(np.float32(0.99)))
+
+
+def gpu_features(r, view=0):
+    n = r.n
+    sp = r.proj["splat"].view(r.V, n, 12)[view].cpu().numpy()
+    rect = r.proj["rect"].view(r.V, n, 4)[view].cpu().numpy().view(np.uint16).astype(np.int64)
+    flags = r.proj["flags"].view(r.V, n)[view].cpu().numpy()
+    depth = r.proj["depth"].view(r.V, n)[view].cpu().numpy()
+    return sp, rect, flags, depth
+
+
+def compare_features(r, orc_out, view=0):
+    """Per-Gaussian parity: survivors, rectangles and features.  Returns counts."""
+    sp, rect, flags, depth = gpu_features(r, view)
+    dbl, irec = orc_out["dbl"], orc_out["irec"]
+    edge = irec[:, oracle.I_EDGE] != 0
+    o_live = irec[:, oracle.I_TOUCHED] > 0
+    g_live = (flags & 0x80) == 0
+    mism = (o_live != g_live) & ~edge
+    assert not mism.any(), "survivor mismatch outside edge classes: %s" % np.nonzero(mism)[0][:10]
+    both = o_live & g_live & ~edge
+    o_rect = irec[:, [oracle.I_X0, oracle.I_Y0, oracle.I_X1, oracle.I_Y1]].astype(np.int64)
+    bad = both & np.any(o_rect != rect, axis=1)
+    assert not bad.any(), "rect mismatch: %s" % np.nonzero(bad)[0][:10]
+    W = r.W
+    du = np.abs(sp[both, 0] - dbl[both, oracle.F_U])
+    dv = np.abs(sp[both, 1] - dbl[both, oracle.F_V])
+    assert np.all(du <= 1e-5 * (np.abs(dbl[both, oracle.F_U]) + W)), du.max()
+    assert np.all(dv <= 1e-5 * (np.abs(dbl[both, oracle.F_V]) + W)), dv.max()
+    for gi, oi in ((2, oracle.F_A), (3, oracle.F_B), (4, oracle.F_C)):
+        scale = np.abs(dbl[both, oracle.F_A]) + np.abs(dbl[both, oracle.F_C])
+        err = np.abs(sp[both, gi] - dbl[both, oi])
+        assert np.all(err <= 2e-5 * scale), (gi, (err / scale).max())
+    np.testing.assert_allclose(sp[both, 5], dbl[both, oracle.F_OPAC], rtol=2e-6, atol=1e-7)
+    for gi, oi in ((6, oracle.F_R), (7, oracle.F_G), (8, oracle.F_BL)):
+        np.testing.assert_allclose(sp[both, gi], dbl[both, oi], rtol=1e-5, atol=2e-6)
+    np.testing.assert_allclose(depth[both], dbl[both, oracle.F_DEPTH], rtol=1e-6)
+    th = dbl[both, oracle.F_TH]
+    np.testing.assert_allclose(sp[both, 9], th, rtol=1e-4)
+    return dict(live=int(o_live.sum()), edge=int(edge.sum()), compared=int(both.sum()))
+
+
+def gpu_pairs(r):
+    npairs = r.pairs()
+    keys = r.sorted_keys[:npairs].cpu().numpy().view(np.uint64)
+    vals = r.sorted_vals[:npairs].cpu().numpy().view(np.uint32).astype(np.int64)
+    return keys, vals
+
+
+def compare_lists(r, orc_outs):
+    """Per-tile sorted id lists: bit-exact outside edge-flagged Gaussians and depth near-ties.
+
+    orc_outs: one oracle render dict per view.  Returns the number of tiles whose
+    order differs only by near-ties."""
+    keys, vals = gpu_pairs(r)
+    n, T = r.n, r.T
+    g_tile = (keys >> np.uint64(32)).astype(np.int64)
+    assert np.all(keys[1:] >= keys[:-1]), "keys not sorted"
+    assert np.all(vals // n == g_tile // T), "view of pair and of tile disagree"
+    g_depth_bits = (keys & np.uint64(0xffffffff)).astype(np.uint32)
+    tie_tiles = 0
+    edge_tiles = []
+    for v, oo in enumerate(orc_outs):
+        edge = oo["irec"][:, oracle.I_EDGE] != 0
+        ts, ids = oo["tile_start"], oo["ids"]
+        o_tile = np.repeat(np.arange(T), np.diff(ts))
+        sel = (g_tile // T) == v
+        gt, gi, gd = g_tile[sel] - v * T, vals[sel] - v * n, g_depth_bits[sel]
+        # tiles whose lists differ only through edge-class Gaussians (excluded from image parity)
+        eo = set(zip(o_tile[edge[ids]].tolist(), ids[edge[ids]].tolist()))
+        eg = set(zip(gt[edge[gi]].tolist(), gi[edge[gi]].tolist()))
+        edge_tiles.append(sorted({t for t, _ in eo ^ eg}))
+        keep_o = ~edge[ids]
+        o_tile, o_ids = o_tile[keep_o], ids[keep_o].astype(np.int64)
+        keep_g = ~edge[gi]
+        gt, gi, gd = gt[keep_g], gi[keep_g], gd[keep_g]
+        assert len(gt) == len(o_tile), "pair count differs outside edge classes: gpu %d oracle %d" % (
+            len(gt), len(o_tile))
+        np.testing.assert_array_equal(gt, o_tile)
+        # depth keys: exactly the fp32 depth (within 1 ulp of the oracle's rounding)
+        od = oo["dbl"][gi, oracle.F_DEPTH].astype(np.float32).view(np.uint32).astype(np.int64)
+        assert np.all(np.abs(gd.astype(np.int64) - od) <= 1), "depth key off by more than 1 ulp"
+        if not np.array_equal(gi, o_ids):
+            # allowed only between near-ties: same multiset per tile and oracle depths within 4 ulps
+            diff_tiles = np.unique(gt[gi != o_ids])
+            for t in diff_tiles:
+                a = gi[gt == t]
+                b = o_ids[o_tile == t]
+                assert np.array_equal(np.sort(a), np.sort(b)), "tile %d holds different Gaussians" % t
+                da = oo["dbl"][a, oracle.F_DEPTH].astype(np.float32).view(np.int32).astype(np.int64)
+                bad = np.nonzero(a != b)[0]
+                for k in bad:
+                    j = np.nonzero(b == a[k])[0][0]
+                    lo, hi = min(k, j), max(k, j)
+                    span = da[lo:hi + 1]
+                    assert span.max() - span.min() <= 4, "order differs beyond a depth near-tie in tile %d" % t
+                tie_tiles += 1
+    return tie_tiles, edge_tiles
+
+
+def compare_image(img_gpu, oo, tol=IMG_TOL, edge_tiles=()):
+    """Image parity: max-abs <= tol outside edge-flagged pixels; PSNR over all pixels.
+
+    Edge pixels: a near-threshold alpha decision (oracle flip budget > 0), or a
+    tile whose pair list differs through an edge-class Gaussian."""
+    o = oo["image"]
+    g = np.asarray(img_gpu, dtype=np.float64)
+    H, W = o.shape[1:]
+    flagged = oo["budget"] > 0
+    tile_px = np.zeros((H, W), dtype=bool)
+    gx = (W + 15) // 16
+    for t in edge_tiles:
+        ty, tx = divmod(int(t), gx)
+        tile_px[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    flagged_budget = flagged & ~tile_px
+    flagged = flagged | tile_px
+    err = np.abs(g - o).max(axis=0)
+    ok = err[~flagged]
+    assert ok.size == 0 or ok.max() <= tol, "max abs error %.3g outside edge pixels" % ok.max()
+    assert np.all(err[flagged_budget] <= tol + oo["budget"][flagged_budget]), "edge pixel beyond its flip bound"
+    mse = float(np.mean((g - o) ** 2))
+    psnr = math.inf if mse == 0 else 10 * math.log10(1.0 / mse)
+    assert psnr >= PSNR_MIN, psnr
+    return dict(max_err=float(ok.max()) if ok.size else 0.0, flagged=int(flagged.sum()),
+                edge_tile_px=int(tile_px.sum()), psnr=psnr)

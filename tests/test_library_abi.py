@@ -1,0 +1,108 @@
+"""The C-ABI library loads and exports every entry point include/ags.h declares,
+and rejects invalid arguments on the host (no GPU needed: these paths return
+before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2604_18980_gb300 import binding as B
+from paper_2604_18980_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ags.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return B.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ags_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_pipeline():
+    names = declared_functions()
+    for n in ("ags_preprocess", "ags_emit_pairs", "ags_sort", "ags_rasterize", "ags_rasterize_backward",
+              "ags_calibrate_lut", "ags_check", "ags_status_reset"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in B.EXPORTS, "binding lacks %s" % name
+
+
+def test_struct_layouts_match_header(lib):
+    # sizes implied by the header's field lists (all 4- or 8-byte fields)
+    assert ctypes.sizeof(B.AgsCamera) == 4 * (2 + 4 + 12 + 3 + 1)
+    assert ctypes.sizeof(B.AgsParams) == 4 * (3 + 5 + 32 + 3)
+    assert ctypes.sizeof(B.AgsGaussians) == 8 * 6
+    assert ctypes.sizeof(B.AgsProjected) == 8 * 5
+
+
+def test_status_strings_and_version(lib):
+    assert B.ags_status_string(0) == "ok"
+    assert "capacity" in B.ags_status_string(2)
+    assert "sm_103a" in B.ags_version()
+
+
+def test_workspace_sizes(lib):
+    assert B.ags_emit_workspace_bytes(0, 1) == 256
+    assert B.ags_emit_workspace_bytes(2048, 1) == 256 + 8
+    assert B.ags_emit_workspace_bytes(2049, 1) == 256 + 16
+    assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 256 * 4 + 256 * 4
+    assert B.ags_backward_workspace_bytes(10, 2) == 10 * 2 * 9 * 4
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    L = lib
+    cam = B.cameras([dict(width=64, height=48, fx=50.0, fy=50.0, cx=31.5, cy=23.5,
+                          viewmat=[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], campos=[0, 0, 0])])
+    par = B.params()
+    g = B.AgsGaussians()
+    g.n = -1
+    pr = B.AgsProjected()
+    st = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    # negative n
+    assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(par), ctypes.byref(pr), st, None) == 1
+    # zero / too many views
+    g.n = 10
+    assert L.ags_preprocess(ctypes.byref(g), cam, 0, ctypes.byref(par), ctypes.byref(pr), st, None) == 1
+    assert L.ags_preprocess(ctypes.byref(g), cam, B.AGS_MAX_VIEWS + 1, ctypes.byref(par), ctypes.byref(pr), st,
+                            None) == 1
+    # bad parameters
+    bad = B.params(sh_degree=4)
+    assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
+    bad = B.params(K=-1.0)
+    assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
+    bad = B.params(scale_mode=2)
+    assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
+    # null outputs
+    assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(par), ctypes.byref(pr), st, None) == 1
+    # sort: bad digit width, capacity beyond the limit, missing workspace
+    npairs = ctypes.c_void_p(16)
+    alt = ctypes.c_int32(0)
+    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 9, None, 0, ctypes.byref(alt), st, None, 0,
+                      None) == 1
+    assert L.ags_sort(None, None, None, None, npairs, B.AGS_MAX_PAIRS, 0, 40, 8, None, 0, ctypes.byref(alt), st,
+                      None, 0, None) == 1
+    assert L.ags_sort(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
+                      10, 0, 40, 8, None, 0, ctypes.byref(alt), st, None, 0, None) == 1
+    # emit: workspace too small
+    assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, None, 0, None) == 1
+    # mismatched view sizes
+    cams2 = B.cameras([dict(width=64, height=48, fx=50.0, fy=50.0, cx=31.5, cy=23.5,
+                            viewmat=[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], campos=[0, 0, 0]),
+                       dict(width=65, height=48, fx=50.0, fy=50.0, cx=31.5, cy=23.5,
+                            viewmat=[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], campos=[0, 0, 0])])
+    assert L.ags_rasterize(ctypes.byref(pr), 10, None, ctypes.c_void_p(16), cams2, 2, ctypes.byref(par),
+                           ctypes.c_void_p(16), None, None, None, None, st, None) == 1
+    # LUT: too many bins
+    assert L.ags_calibrate_lut(None, None, 0, 33, 100.0, ctypes.c_void_p(16), None) == 1
