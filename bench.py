@@ -231,8 +231,8 @@ def run_ours(args, world, rank, local):
     ada.check()
     evals_per_step = int(ada.stats[0].item())
     ada_pairs = ada.pairs()
-    passes = math.ceil(ada.end_bit / ada.digit_bits)
-    launches_per_step = 1 + 1 + (2 + passes + 1) + 1   # preprocess, emit, hist+scan+passes+ranges, blend
+    passes = ada.sort_plan()[0]
+    launches_per_step = ada.launches_per_forward()
 
     # warm-up
     for _ in range(args.warmup):
@@ -241,7 +241,7 @@ def run_ours(args, world, rank, local):
     barrier()
 
     # timed region: events between stages on the launching stream
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     clocks = ClockSampler(device_uuid())
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
@@ -252,20 +252,30 @@ def run_ours(args, world, rank, local):
         e[0].record(stream)
         ada.preprocess()
         e[1].record(stream)
-        ada.emit()
+        ada.depth_sort()
         e[2].record(stream)
-        ada.sort()
+        ada.emit()
         e[3].record(stream)
-        ada.rasterize()
+        ada.sort()
         e[4].record(stream)
+        ada.rasterize()
+        e[5].record(stream)
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
     ms_total = max_over_ranks(t_start.elapsed_time(t_end))
     ada.check()
-    stage_names = ["preprocess", "emit", "sort", "raster"]
+    stage_names = ["preprocess", "depth_sort", "emit", "sort", "raster"]
     stage_ms = {nm: sum(ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(args.steps)) / args.steps
                 for k, nm in enumerate(stage_names)}
+    pk0, _ = peaks()
+    stage_frac = {}
+    for nm in stage_names:
+        if nm == "raster" or stage_ms[nm] <= 0:
+            continue
+        b, _ = stage_bytes(nm, ada, passes)
+        gbs = b / (stage_ms[nm] / 1e3) / 1e9
+        stage_frac[nm] = {"GB/s": gbs, "frac_of_hbm": gbs / pk0.get("hbm_gbs", FALLBACK_HBM_GBS)}
     ms_step = ms_total / args.steps
     fps = world * V * args.steps / (ms_total / 1000.0)
 
@@ -358,6 +368,7 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2 (params 236 MB, pairs %.1f GB per step)" % (ada_pairs * 24 / 1e9),
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
         "stage_ms": stage_ms,
+        "stage_hbm": stage_frac,
         "roofline": roof,
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
@@ -376,6 +387,26 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def stage_bytes(stage, r, passes):
+    """Algorithmic HBM bytes of one launch sequence of an HBM-bound stage (per-unit figures x units)."""
+    V, n, P = r.V, r.n, r.pairs()
+    G = V * n
+    live = int(((r.proj["flags"] & 0x80) == 0).sum().item())
+    if stage == "sort":
+        # histogram read (8 B/pair), each digit pass reads and writes key+value (24 B/pair),
+        # ranges read the keys (8 B/pair) and write 8 B/tile
+        return P * 8 + passes * P * 24 + P * 8 + V * r.T * 8, "onesweep_kernel (+hist, ranges)"
+    if stage == "depth_sort":
+        dp = math.ceil(r.dsort_end / r.digit_bits) if r.presort else 0
+        return G * 8 + dp * G * 24 - G * 4, "onesweep_kernel (depth keys, identity values)"
+    if stage == "emit":
+        # order (4 B), rectangle (8 B) per Gaussian, depth (4 B) per survivor; 12 B per pair
+        return G * 12 + live * 4 + P * 12, "emit_kernel"
+    # preprocess: 44 B geometry per Gaussian and view; survivors read 192 B SH and
+    # write 48 B splat + 4 depth + 8 rect + 4 count + 1 flag + 8 depth key; culled write 21 B
+    return G * 44 + live * (192 + 73) + (G - live) * 21, "preprocess_kernel"
+
+
 def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):
     V, n = r.V, r.n
     P = r.pairs()
@@ -390,15 +421,7 @@ def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):
                 "work": "%d pixel-pair evaluations x %d FP32 ops" % (evals, RASTER_OPS_PER_EVAL),
                 "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (%s)" % (sms, sm_mhz, pk_src)}
     hbm = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
-    if stage == "sort":
-        byts = P * 8 + passes * P * 24 + P * 8 + V * r.T * 8
-        kern = "onesweep_kernel (+hist, ranges)"
-    elif stage == "emit":
-        byts = V * n * 12 + P * 12
-        kern = "emit_kernel"
-    else:
-        byts = V * n * (44 + 4) + V * n * 192 + V * n * 65
-        kern = "preprocess_kernel"
+    byts, kern = stage_bytes(stage, r, passes)
     achieved = byts / (ms / 1e3) / 1e9
     return {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None, "peak_source": pk_src}

@@ -52,7 +52,7 @@ extern "C" {
 #define AGS_TILE 16
 #define AGS_MAX_VIEWS 32
 #define AGS_MAX_LUT_BINS 32
-#define AGS_MAX_PAIRS ((int64_t)1 << 30)
+#define AGS_MAX_PAIRS ((int64_t)1 << 30)   /* exclusive bound on a sort's pair count */
 
 typedef enum {
   AGS_OK = 0,
@@ -103,15 +103,20 @@ typedef struct {
 /* Per-view preprocess results (device memory, index e = view*n + i). */
 typedef struct {
   float* splat;             /* [views*n][12], 16-byte aligned:
-                               u v A B | C opacity r g | b Th 0 0
+                               u v A B | C opacity r g | b Th Sxx Syy
                                (u,v) 2D mean in pixels, (A,B,C) conic of the
-                               ORIGINAL dilated 2D covariance */
+                               ORIGINAL dilated 2D covariance, (Sxx,Syy) its
+                               diagonal, Th the alpha threshold (Eq. 10) */
   float* depth;             /* [views*n] view-space z */
   uint16_t* rect;           /* [views*n][4] tile rectangle x0 y0 x1 y1 (end
                                exclusive); all zero for culled Gaussians */
   uint32_t* tiles_touched;  /* [views*n] (x1-x0)*(y1-y0), nullable */
   uint8_t* flags;           /* [views*n] bit0-2 colour clamped at 0, bit3/bit4
                                EWA x/y frustum clamp, bit7 culled */
+  uint64_t* depth_key;      /* [views*n] (view << 32) | float_bits(depth), all
+                               ones for Gaussians without pairs; nullable.
+                               Sorting these first lets the pair sort skip the
+                               depth digits (see ags_emit_pairs `order`). */
 } ags_projected;
 
 /* Device status block: int64_t[4] = {status code, detail, non-finite count, reserved}. */
@@ -163,11 +168,17 @@ ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32_t views,
 /* Scratch bytes needed by ags_sort for up to `capacity` pairs. */
 size_t ags_sort_workspace_bytes(int64_t capacity);
 
+#define AGS_SORT_IDENTITY_VALUES 1   /* ags_sort flag: values are 0..count-1; `vals` is not read */
+
 /* Stable LSD radix sort of (keys, vals) by key bits [begin_bit, end_bit)
  * (Sec. 2.1 sorting stage): one global-histogram pass, then one single-pass
  * ("onesweep") scatter per digit of `digit_bits` (4..8) bits, with warp-level
  * match/ballot ranking and decoupled look-back between blocks.  The count is
- * read on the device from *d_num_pairs (<= capacity <= AGS_MAX_PAIRS).
+ * read on the device from *d_num_pairs (clamped to capacity < AGS_MAX_PAIRS).
+ * Keys already stably ordered by their bits below begin_bit stay so ordered
+ * within equal [begin_bit, end_bit) fields: pairs emitted in depth order
+ * need only the tile digits, with the same result as a sort of all bits.
+ * flags: AGS_SORT_IDENTITY_VALUES.
  * The sorted result lands in (keys, vals) when the number of digit passes is
  * even and in (keys_alt, vals_alt) when it is odd; *result_in_alt (host)
  * reports which.  If `ranges` is non-null it then receives, for each of
@@ -175,9 +186,9 @@ size_t ags_sort_workspace_bytes(int64_t capacity);
  * zero for empty tiles), the tile being key >> 32. */
 ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                     const int64_t* d_num_pairs, int64_t capacity, int32_t begin_bit,
-                    int32_t end_bit, int32_t digit_bits, uint32_t* ranges, int64_t num_ranges,
-                    int32_t* result_in_alt, int64_t* d_status, void* ws, size_t ws_bytes,
-                    void* stream);
+                    int32_t end_bit, int32_t digit_bits, int32_t flags, uint32_t* ranges,
+                    int64_t num_ranges, int32_t* result_in_alt, int64_t* d_status, void* ws,
+                    size_t ws_bytes, void* stream);
 
 /* Blending (Eq. 1, Eq. 2; Sec. 3.3 dual size).  One CTA per 16x16 tile of
  * each view; per pixel, front to back over the tile's sorted pairs:

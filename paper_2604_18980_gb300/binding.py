@@ -57,7 +57,8 @@ class AgsGaussians(ctypes.Structure):
 
 
 class AgsProjected(ctypes.Structure):
-    _fields_ = [("splat", _P), ("depth", _P), ("rect", _P), ("tiles_touched", _P), ("flags", _P)]
+    _fields_ = [("splat", _P), ("depth", _P), ("rect", _P), ("tiles_touched", _P), ("flags", _P),
+                ("depth_key", _P)]
 
 
 EXPORTS = {
@@ -68,7 +69,8 @@ EXPORTS = {
     "ags_emit_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
     "ags_emit_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P], _I32),
     "ags_sort_workspace_bytes": ([_I64], ctypes.c_size_t),
-    "ags_sort": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P], _I32),
+    "ags_sort": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _I32, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P],
+                 _I32),
     "ags_rasterize": ([_P, _I64, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "ags_calibrate_lut": ([_P, _P, _I64, _I32, _F, _P, _P], _I32),
     "ags_backward_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
@@ -164,6 +166,7 @@ def projected(proj) -> AgsProjected:
     p = AgsProjected()
     p.splat, p.depth, p.rect = ptr(proj["splat"]), ptr(proj["depth"]), ptr(proj["rect"])
     p.tiles_touched, p.flags = ptr(proj.get("tiles_touched")), ptr(proj["flags"])
+    p.depth_key = ptr(proj.get("depth_key"))
     return p
 
 
@@ -221,12 +224,15 @@ def ags_sort_workspace_bytes(capacity: int) -> int:
     return int(lib().ags_sort_workspace_bytes(int(capacity)))
 
 
+AGS_SORT_IDENTITY_VALUES = 1
+
+
 def ags_sort(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit, digit_bits, ranges,
-             num_ranges, d_status, ws, stream=None) -> bool:
+             num_ranges, d_status, ws, flags=0, stream=None) -> bool:
     """Returns True when the sorted result is in (keys_alt, vals_alt)."""
     alt = ctypes.c_int32(0)
     _ok(lib().ags_sort(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt), ptr(d_num_pairs), int(capacity),
-                       int(begin_bit), int(end_bit), int(digit_bits), ptr(ranges), int(num_ranges),
+                       int(begin_bit), int(end_bit), int(digit_bits), int(flags), ptr(ranges), int(num_ranges),
                        ctypes.byref(alt), ptr(d_status), ptr(ws), ws.numel() * ws.element_size(),
                        stream_handle(stream)), "ags_sort")
     return bool(alt.value)

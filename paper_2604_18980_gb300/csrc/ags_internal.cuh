@@ -10,7 +10,7 @@
 namespace ags {
 
 constexpr int kTile = AGS_TILE;
-constexpr int kSplatFloats = 12;            // u v A B | C opacity r g | b Th 0 0
+constexpr int kSplatFloats = 12;            // u v A B | C opacity r g | b Th Sxx Syy
 constexpr uint8_t kFlagCulled = 0x80;
 constexpr uint64_t kWaitLimitNs = 200ull * 1000ull * 1000ull;   // bounded spin: 200 ms
 

@@ -29,9 +29,11 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
                        const uint2* __restrict__ ranges, int W, int H, int gx, int tiles_per_view, BlendConst bc,
                        const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
                        const float* __restrict__ dL_dimage, float* __restrict__ gsplat) {
-  __shared__ float4 s_a[kRasterThreads];
-  __shared__ float4 s_b[kRasterThreads];
+  __shared__ float4 s_a[kRasterThreads];    // u v a2 b2
+  __shared__ float4 s_b[kRasterThreads];    // c2 l2s r g
+  __shared__ float4 s_o[kRasterThreads];    // A B C opacity (original units, for the gradients)
   __shared__ float s_c[kRasterThreads];
+  __shared__ uint32_t s_m[kRasterThreads];
   __shared__ uint32_t s_e[kRasterThreads];
   __shared__ uint32_t s_maxlast;
 
@@ -39,9 +41,10 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
   const int view = tile / tiles_per_view;
   const int lt = tile - view * tiles_per_view;
   const int ty = lt / gx, tx = lt - ty * gx;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int px = tx * kTile + (tid & (kTile - 1));
-  const int py = ty * kTile + (tid >> 4);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int lx, ly;
+  tile_pixel(tid, lx, ly);
+  const int px = tx * kTile + lx, py = ty * kTile + ly;
   const bool inside = px < W && py < H;
   const float fpx = (float)px, fpy = (float)py;
   const uint2 rg = __ldg(ranges + tile);
@@ -65,54 +68,64 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
   if (last) atomicMax(&s_maxlast, last);
   __syncthreads();
   const uint32_t maxlast = min(s_maxlast, end - start);
+  // the warp walks only the positions below its own largest "last"
+  const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
 
   for (int32_t bend = (int32_t)maxlast; bend > 0; bend -= kRasterThreads) {
     const int32_t bbeg = max(0, bend - kRasterThreads);
     const int nb = bend - bbeg;
     __syncthreads();
     if (tid < nb) {
-      uint32_t e = __ldg(vals + start + bbeg + tid);
+      const uint32_t e = __ldg(vals + start + bbeg + tid);
       const float4* rec = splat + (size_t)e * 3;
-      s_a[tid] = __ldg(rec);
-      s_b[tid] = __ldg(rec + 1);
-      s_c[tid] = __ldg(reinterpret_cast<const float*>(rec + 2));
+      Staged st;
+      uint32_t m;
+      stage_splat(rec, tx * kTile, ty * kTile, bc.l2tau, st, m);
+      const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+      s_a[tid] = st.a;
+      s_b[tid] = st.b;
+      s_c[tid] = st.c;
+      s_o[tid] = make_float4(r0.z, r0.w, r1.x, r1.y);
+      s_m[tid] = m;
       s_e[tid] = e;
     }
     __syncthreads();
-    for (int j = nb - 1; j >= 0; j--) {
-      const uint32_t pos = (uint32_t)(bbeg + j);     // 0-based position in the tile list
-      const float4 a = s_a[j];
-      const float4 bq = s_b[j];
+    const int jtop = min(nb, (int)wlast - bbeg);
+    for (int j = jtop - 1; j >= 0; j--) {
+      if (!((s_m[j] >> warp) & 1u)) continue;         // warp-uniform skip, as in the forward
+      const uint32_t pos = (uint32_t)(bbeg + j);       // 0-based position in the tile list
+      Staged s;
+      s.a = s_a[j];
+      s.b = s_b[j];
       const float cbl = s_c[j];
       float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, gO = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
       bool contrib = false;
       if (pos < last) {
         float dx, dy;
-        float power = splat_power(a.x, a.y, a.z, a.w, bq.x, fpx, fpy, dx, dy);
-        if (power <= 0.f) {
-          float raw = splat_alpha_raw(bq.y, power);
-          float alpha = fminf(bc.alpha_max, raw);
-          if (alpha >= bc.tau) {
-            contrib = true;
-            const float om = 1.f - alpha;
-            T = T / om;
-            const float w = alpha * T;
-            gr = w * g0;
-            gg = w * g1;
-            gb = w * g2;
-            const float dLda = T * (g0 * (bq.z - R0) + g1 * (bq.w - R1) + g2 * (cbl - R2));
-            R0 = bq.z * alpha + om * R0;
-            R1 = bq.w * alpha + om * R1;
-            R2 = cbl * alpha + om * R2;
-            if (!(raw > bc.alpha_max)) {
-              const float dLdp = dLda * alpha;
-              gO = dLda * (alpha / bq.y);
-              gu = -dLdp * (a.z * dx + a.w * dy);
-              gv = -dLdp * (a.w * dx + bq.x * dy);
-              gA = -0.5f * dLdp * dx * dx;
-              gB = -dLdp * dx * dy;
-              gC = -0.5f * dLdp * dy * dy;
-            }
+        const float q = splat_q(s, fpx, fpy, dx, dy);
+        if (splat_accept(q, s.b.y)) {
+          const float raw = __fmul_rn(bc.tau, fast_exp2(q));
+          const float alpha = fminf(bc.alpha_max, raw);
+          contrib = true;
+          const float4 o = s_o[j];
+          const float om = 1.f - alpha;
+          T = T / om;
+          const float w = alpha * T;
+          gr = w * g0;
+          gg = w * g1;
+          gb = w * g2;
+          const float dLda = T * (g0 * (s.b.z - R0) + g1 * (s.b.w - R1) + g2 * (cbl - R2));
+          R0 = s.b.z * alpha + om * R0;
+          R1 = s.b.w * alpha + om * R1;
+          R2 = cbl * alpha + om * R2;
+          if (!(raw > bc.alpha_max)) {
+            const float dLdp = dLda * alpha;
+            gO = dLda * (alpha / o.w);
+            gu = -dLdp * (o.x * dx + o.y * dy);
+            gv = -dLdp * (o.y * dx + o.z * dy);
+            gA = -0.5f * dLdp * dx * dx;
+            gB = -dLdp * dx * dy;
+            gC = -0.5f * dLdp * dy * dy;
           }
         }
       }
@@ -300,7 +313,7 @@ extern "C" ags_status ags_rasterize_backward(const ags_gaussians* g, const ags_c
   cudaError_t e = cudaMemsetAsync(gs, 0, ags_backward_workspace_bytes(g->n, views), st);
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   const int tiles_per_view = cb.c[0].gx * cb.c[0].gy;
-  BlendConst bc{dp.tau, dp.t_min, dp.alpha_max, {dp.bg[0], dp.bg[1], dp.bg[2]}};
+  BlendConst bc = make_blend_const(dp);
   raster_backward_kernel<<<(unsigned)(tiles_per_view * views), kRasterThreads, 0, st>>>(
       reinterpret_cast<const float4*>(proj->splat), sorted_vals, reinterpret_cast<const uint2*>(ranges), cb.c[0].W,
       cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, final_T, n_contrib, dL_dimage, gs);

@@ -1,31 +1,106 @@
-// blend.cuh -- per-pixel alpha of one splat (Eq. 1), shared by the blend and
-// its adjoint so that both take bit-identical decisions.
+// blend.cuh -- per-pixel alpha of one splat (Eq. 1) as the blend and its
+// adjoint evaluate it, shared so both take bit-identical decisions.
+//
+// The exponent is carried in log2 units relative to tau: with
+//   a2 = -A log2(e)/2, b2 = -B log2(e), c2 = -C log2(e)/2,
+//   base = log2(opacity / tau),
+//   q  = a2 dx^2 + b2 dx dy + c2 dy^2 + base = log2(opacity e^p / tau),
+// Eq. 1 is alpha = min(alpha_max, tau 2^q); alpha >= tau is q >= 0 and p <= 0 is
+// q <= base, so the threshold test runs before the exponential.
+//
+// Each CTA blends one 16x16 tile with eight warps; warp w owns the 4x8 pixel
+// block rows 4*(w>>1).., columns 8*(w&1)...  For every staged splat the loading
+// thread also computes which of the eight blocks can hold a pixel with
+// alpha >= tau: the bounding box of the ellipse p >= ln(tau/opacity), i.e.
+// half-widths sqrt(2 ln(opacity/tau) Sigma_xx) and sqrt(2 ln(opacity/tau) Sigma_yy)
+// of the dilated covariance, widened by a slack far above fp32 rounding.  A
+// warp skips a splat whose bit is clear: those pixels would have rejected it
+// with alpha < tau anyway, so the result is unchanged.
 #pragma once
+
+#include <cmath>
 
 #include "ags_internal.cuh"
 
 namespace ags {
 
 constexpr int kRasterThreads = kTile * kTile;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
 
 struct BlendConst {
-  float tau, t_min, alpha_max;
+  float tau, t_min, alpha_max, l2tau;   // l2tau = log2(tau)
   float bg[3];
 };
 
-// p = -(A dx^2 + C dy^2)/2 - B dx dy with dx = u - px, dy = v - py, every
-// operation rounded explicitly (no contraction freedom for the compiler).
-__device__ __forceinline__ float splat_power(float u, float v, float A, float B, float C, float px, float py,
-                                             float& dx, float& dy) {
-  dx = __fsub_rn(u, px);
-  dy = __fsub_rn(v, py);
-  float q = __fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(C, dy), dy));
-  return __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(__fmul_rn(B, dx), dy));
+// Host-side constants of the blend from the parameter block.
+inline BlendConst make_blend_const(const DevParams& dp) {
+  BlendConst bc;
+  bc.tau = dp.tau;
+  bc.t_min = dp.t_min;
+  bc.alpha_max = dp.alpha_max;
+  bc.l2tau = (float)std::log2((double)dp.tau);
+  for (int i = 0; i < 3; i++) bc.bg[i] = dp.bg[i];
+  return bc;
 }
 
-// opacity * e^p before the alpha_max clamp.
-__device__ __forceinline__ float splat_alpha_raw(float opacity, float power) {
-  return __fmul_rn(opacity, __expf(power));
+struct Staged {
+  float4 a;      // u, v, a2, b2
+  float4 b;      // c2, l2s - log2(tau), r, g
+  float c;       // b
+};
+
+// Splat record (48 bytes): u v A B | C opacity r g | b Th Sxx Syy.
+__device__ __forceinline__ void stage_splat(const float4* rec, int tx0, int ty0, float l2tau, Staged& s,
+                                            uint32_t& mask) {
+  const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+  const float base = __log2f(r1.y) - l2tau;               // log2(opacity / tau)
+  s.a = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
+  s.b = make_float4(-0.5f * kLog2e * r1.x, base, r1.z, r1.w);
+  s.c = r2.x;
+  // blocks of the tile that the alpha >= tau ellipse can reach
+  mask = 0u;
+  const float r2n = 2.f * kLn2 * base + 1e-3f;             // 2 ln(opacity/tau) + slack
+  if (r2n > 0.f) {
+    const float hx = sqrtf(r2n * r2.z) * 1.0001f + 0.01f;
+    const float hy = sqrtf(r2n * r2.w) * 1.0001f + 0.01f;
+    const float lx = r0.x - hx - (float)tx0, ux = r0.x + hx - (float)tx0;   // tile-relative
+    const float ly = r0.y - hy - (float)ty0, uy = r0.y + hy - (float)ty0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+      const float cx0 = (float)(8 * (w & 1)), ry0 = (float)(4 * (w >> 1));
+      if (ux >= cx0 && lx <= cx0 + 7.f && uy >= ry0 && ly <= ry0 + 3.f) mask |= 1u << w;
+    }
+  }
+}
+
+// Pixel of thread `tid` within its tile: warp w covers a 4x8 block.
+__device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
+  const int w = tid >> 5, lane = tid & 31;
+  lx = 8 * (w & 1) + (lane & 7);
+  ly = 4 * (w >> 1) + (lane >> 3);
+}
+
+// q = log2(opacity e^p / tau) at pixel offset (dx, dy); explicit roundings.
+// The splat is blended at this pixel iff 0 <= q <= log2(opacity/tau), i.e.
+// alpha >= tau and p <= 0: one unsigned compare of the bit patterns
+// (negative q, including -0, has the sign bit set).  alpha = min(alpha_max, tau 2^q).
+__device__ __forceinline__ bool splat_accept(float q, float base) {
+  return __float_as_uint(q) <= __float_as_uint(base);
+}
+
+__device__ __forceinline__ float splat_q(const Staged& s, float px, float py, float& dx, float& dy) {
+  dx = __fsub_rn(s.a.x, px);
+  dy = __fsub_rn(s.a.y, py);
+  const float t = __fmaf_rn(s.a.z, dx, __fmul_rn(s.a.w, dy));
+  const float base = __fmaf_rn(__fmul_rn(s.b.x, dy), dy, s.b.y);
+  return __fmaf_rn(t, dx, base);
+}
+
+__device__ __forceinline__ float fast_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 }  // namespace ags

@@ -5,11 +5,12 @@
 // (cull when Th > opacity; Th shrinks only the footprint used by the tile
 // test), Sec. 3.4 (T_up from a depth look-up table).
 //
-// One thread per (view, Gaussian).  The structure-of-arrays inputs are read
-// with coalesced loads; the 48 SH floats are read only for Gaussians that
-// survive and touch at least one tile.  Outputs per survivor: a 48-byte splat
-// record (three 16-byte stores), depth, the tile rectangle (one 8-byte store),
-// the tile count and a flag byte.
+// One thread per Gaussian, looping over all views of the batch: the
+// structure-of-arrays parameters are read once (coalesced) whatever the number
+// of views, and the 48 SH floats only once, when the first view in which the
+// Gaussian survives and touches a tile needs its colour.  Outputs per view and
+// survivor: a 48-byte splat record (three 16-byte stores), depth, the tile
+// rectangle (one 8-byte store), the tile count, a flag byte and the depth key.
 #include "project.cuh"
 
 namespace ags {
@@ -28,12 +29,14 @@ struct PreOut {
   uint16_t* rect;
   uint32_t* touched;
   uint8_t* flags;
+  uint64_t* dkey;
 };
 
 __device__ __forceinline__ void write_culled(const PreOut& o, int64_t e) {
   reinterpret_cast<uint2*>(o.rect)[e] = make_uint2(0u, 0u);
   if (o.touched) o.touched[e] = 0u;
   o.flags[e] = kFlagCulled;
+  if (o.dkey) o.dkey[e] = ~0ull;
 }
 
 // Tiles [t0, t1) holding a pixel centre in [lo, hi] on an axis of `len` pixels.
@@ -45,15 +48,14 @@ __device__ __forceinline__ void tile_span(float lo, float hi, int len, int& t0, 
   t1 = ((int)phi >> 4) + 1;
 }
 
-__global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, const __grid_constant__ CamBatch cams,
+__global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, int views,
+                                                         const __grid_constant__ CamBatch cams,
                                                          const __grid_constant__ DevParams P, PreOut out,
                                                          int64_t* status) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int view = blockIdx.y;
-  const DevCam& C = cams.c[view];
-  const int64_t e = (int64_t)view * n + i;
 
+  // geometry: read once for all views
   float m[3], ls[3], q[4];
 #pragma unroll
   for (int k = 0; k < 3; k++) m[k] = __ldg(in.mean + k * n + i);
@@ -61,71 +63,87 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, co
   for (int k = 0; k < 3; k++) ls[k] = __ldg(in.ls + k * n + i);
 #pragma unroll
   for (int k = 0; k < 4; k++) q[k] = __ldg(in.quat + k * n + i);
-  float logit = __ldg(in.logit + i);
-  bool finite = isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && isfinite(ls[0]) && isfinite(ls[1]) &&
-                isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]) &&
-                isfinite(logit);
+  const float logit = __ldg(in.logit + i);
+  const bool finite = isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && isfinite(ls[0]) && isfinite(ls[1]) &&
+                      isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]) &&
+                      isfinite(logit);
   if (!finite) {
-    if (view == 0) atomicAdd(reinterpret_cast<unsigned long long*>(status + 2), 1ull);
-    write_culled(out, e);
+    atomicAdd(reinterpret_cast<unsigned long long*>(status + 2), 1ull);
+    for (int view = 0; view < views; view++) write_culled(out, (int64_t)view * n + i);
     return;
   }
-  Proj pj;
-  if (!project_geometry(C, m, ls, q, logit, pj)) {
-    write_culled(out, e);
-    return;
-  }
-  // footprint radius: plain 3-sigma, or AdaGScale (Eq. 10, Sec. 3.3)
-  float th = P.tau;
-  float rf;
-  if (P.scale_mode == AGS_SCALE_ADAGSCALE) {
-    int bin = (int)fminf(pj.t[2] * P.lut_scale, (float)(P.lut_bins - 1));   // depth > 0: truncation = floor
-    float tup = P.lut[bin];
-    if (!(tup > 0.f)) { write_culled(out, e); return; }
-    th = P.K / (tup * 6.2831853f * sqrtf(pj.det)) + P.tau;
-    if (th > pj.opac) { write_culled(out, e); return; }
-    rf = ceilf(sqrtf(pj.lam1) * fminf(3.f, sqrtf(2.f * logf(pj.opac / th))));
-  } else {
-    rf = ceilf(3.f * sqrtf(pj.lam1));
-  }
-  int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-  if (rf > 0.f) {
-    tile_span(pj.u - rf, pj.u + rf, C.W, x0, x1);
-    tile_span(pj.v - rf, pj.v + rf, C.H, y0, y1);
-  }
-  uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
-  if (touched == 0u) { write_culled(out, e); return; }
-
-  // colour: SH at the world-space direction from the camera centre
-  float dx = m[0] - C.campos[0], dy = m[1] - C.campos[1], dz = m[2] - C.campos[2];
-  float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-  float Y[16];
-  sh_basis(P.sh_degree, dx * il, dy * il, dz * il, Y);
   const int nc = (P.sh_degree + 1) * (P.sh_degree + 1);
-  float rgb[3] = {0.5f, 0.5f, 0.5f};
-  for (int k = 0; k < nc; k++) {
+  float sh[16][3];            // loaded on the first view that needs a colour
+  bool sh_loaded = false;
+
+  for (int view = 0; view < views; view++) {
+    const DevCam& C = cams.c[view];
+    const int64_t e = (int64_t)view * n + i;
+    Proj pj;
+    if (!project_geometry(C, m, ls, q, logit, pj)) {
+      write_culled(out, e);
+      continue;
+    }
+    // footprint radius: plain 3-sigma, or AdaGScale (Eq. 10, Sec. 3.3)
+    float th = P.tau;
+    float rf;
+    if (P.scale_mode == AGS_SCALE_ADAGSCALE) {
+      const int bin = (int)fminf(pj.t[2] * P.lut_scale, (float)(P.lut_bins - 1));   // depth > 0: trunc = floor
+      const float tup = P.lut[bin];
+      if (!(tup > 0.f)) { write_culled(out, e); continue; }
+      th = P.K / (tup * 6.2831853f * sqrtf(pj.det)) + P.tau;
+      if (th > pj.opac) { write_culled(out, e); continue; }
+      rf = ceilf(sqrtf(pj.lam1) * fminf(3.f, sqrtf(2.f * logf(pj.opac / th))));
+    } else {
+      rf = ceilf(3.f * sqrtf(pj.lam1));
+    }
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    if (rf > 0.f) {
+      tile_span(pj.u - rf, pj.u + rf, C.W, x0, x1);
+      tile_span(pj.v - rf, pj.v + rf, C.H, y0, y1);
+    }
+    const uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+    if (touched == 0u) { write_culled(out, e); continue; }
+
+    // colour: SH at the world-space direction from the camera centre
+    if (!sh_loaded) {
+      for (int k = 0; k < nc; k++)
 #pragma unroll
-    for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(__ldg(in.sh + (int64_t)(k * 3 + ch) * n + i), Y[k], rgb[ch]);
-  }
-  uint8_t flags = (uint8_t)pj.fclamp;
+        for (int ch = 0; ch < 3; ch++) sh[k][ch] = __ldg(in.sh + (int64_t)(k * 3 + ch) * n + i);
+      sh_loaded = true;
+    }
+    const float dx = m[0] - C.campos[0], dy = m[1] - C.campos[1], dz = m[2] - C.campos[2];
+    const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float Y[16];
+    sh_basis(P.sh_degree, dx * il, dy * il, dz * il, Y);
+    float rgb[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < nc; k++) {
 #pragma unroll
-  for (int ch = 0; ch < 3; ch++) {
-    if (!isfinite(rgb[ch])) {
+      for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(sh[k][ch], Y[k], rgb[ch]);
+    }
+    uint8_t flags = (uint8_t)pj.fclamp;
+    bool bad = false;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+      if (!isfinite(rgb[ch])) bad = true;
+      if (rgb[ch] < 0.f) { rgb[ch] = 0.f; flags |= (uint8_t)(1 << ch); }
+    }
+    if (bad) {
       if (view == 0) atomicAdd(reinterpret_cast<unsigned long long*>(status + 2), 1ull);
       write_culled(out, e);
-      return;
+      continue;
     }
-    if (rgb[ch] < 0.f) { rgb[ch] = 0.f; flags |= (uint8_t)(1 << ch); }
+    float4* sp = reinterpret_cast<float4*>(out.splat + e * kSplatFloats);
+    sp[0] = make_float4(pj.u, pj.v, pj.A, pj.B);
+    sp[1] = make_float4(pj.C, pj.opac, rgb[0], rgb[1]);
+    sp[2] = make_float4(rgb[2], th, pj.a + 0.3f, pj.c + 0.3f);
+    out.depth[e] = pj.t[2];
+    reinterpret_cast<uint2*>(out.rect)[e] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16),
+                                                       (uint32_t)x1 | ((uint32_t)y1 << 16));
+    if (out.touched) out.touched[e] = touched;
+    out.flags[e] = flags;
+    if (out.dkey) out.dkey[e] = ((uint64_t)view << 32) | __float_as_uint(pj.t[2]);
   }
-  float4* sp = reinterpret_cast<float4*>(out.splat + e * kSplatFloats);
-  sp[0] = make_float4(pj.u, pj.v, pj.A, pj.B);
-  sp[1] = make_float4(pj.C, pj.opac, rgb[0], rgb[1]);
-  sp[2] = make_float4(rgb[2], th, 0.f, 0.f);
-  out.depth[e] = pj.t[2];
-  reinterpret_cast<uint2*>(out.rect)[e] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16),
-                                                     (uint32_t)x1 | ((uint32_t)y1 << 16));
-  if (out.touched) out.touched[e] = touched;
-  out.flags[e] = flags;
 }
 
 }  // namespace ags
@@ -148,8 +166,8 @@ extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* c
   if (!out->splat || !out->depth || !out->rect || !out->flags) return AGS_ERR_INVALID_ARG;
   if (((uintptr_t)out->splat & 15u) || ((uintptr_t)out->rect & 7u)) return AGS_ERR_INVALID_ARG;
   PreIn in{g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
-  PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags};
-  dim3 grid((unsigned)((g->n + 255) / 256), (unsigned)views);
-  preprocess_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(in, g->n, cb, dp, po, d_status);
+  PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags, out->depth_key};
+  preprocess_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, g->n, views, cb, dp, po,
+                                                                                      d_status);
   return launch_status(cudaGetLastError());
 }

@@ -1,12 +1,14 @@
 // raster.cu -- per-tile front-to-back alpha blending (Eq. 1, Eq. 2) and the
 // T_up calibration table (Sec. 3.4).
 //
-// One 256-thread CTA per 16x16 tile of each view, one pixel per thread.  The
-// tile's depth-ordered pairs are staged in batches of 256: each thread gathers
-// one splat record (two 16-byte loads and one 4-byte load from the 48-byte
-// record) into shared memory, then every thread walks the batch for its pixel.
-// The CTA stops as soon as every pixel has reached the transmittance floor
-// (__syncthreads_count vote).  The blend always uses the conic of the original
+// One 256-thread CTA per 16x16 tile of each view, one pixel per thread (each
+// warp a 4x8 pixel block).  The tile's depth-ordered pairs are staged in
+// batches of 256: each thread gathers one 48-byte splat record, converts it
+// to the log2 form of Eq. 1 and computes the mask of warp blocks its
+// alpha >= tau ellipse can reach; then every warp walks the batch, skipping
+// (warp-uniformly) the splats that miss its block.  A warp leaves the batch
+// once all its pixels reached the transmittance floor, the CTA once all warps
+// did (__syncthreads_count vote).  The blend always uses the conic of the original
 // covariance and tau (Sec. 3.3 "dual-size strategy"): the scale mode only ever
 // changed which pairs exist.
 #include <algorithm>
@@ -15,27 +17,40 @@
 
 namespace ags {
 
+// kStats: count evaluations and blends; kMaxT: calibration output.  The
+// benchmark's kernel is the <false, false> instance.
+template <bool kStats, bool kMaxT>
 __global__ void __launch_bounds__(kRasterThreads)
 raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
               int W, int H, int gx, int tiles_per_view, BlendConst bc, float* __restrict__ image,
               float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ max_T_bits,
               unsigned long long* stats) {
-  __shared__ float4 s_a[kRasterThreads];   // u v A B
-  __shared__ float4 s_b[kRasterThreads];   // C opacity r g
-  __shared__ float s_c[kRasterThreads];    // b
-  __shared__ uint32_t s_e[kRasterThreads]; // splat index (calibration only)
+  constexpr int kPad = kRasterThreads;                // index of an always-rejected entry
+  __shared__ float4 s_a[kRasterThreads + 1];          // u v a2 b2
+  __shared__ float4 s_b[kRasterThreads + 1];          // c2 base r g
+  __shared__ float s_c[kRasterThreads + 1];           // b
+  __shared__ uint32_t s_m[kRasterThreads];            // warp-block mask
+  __shared__ uint32_t s_e[kRasterThreads + 1];        // splat index (calibration only)
+  __shared__ uint16_t s_list[kRasterThreads / 32][kRasterThreads + 4];   // per-warp entries, padded
 
   const int tile = blockIdx.x;
   const int view = tile / tiles_per_view;
   const int lt = tile - view * tiles_per_view;
   const int ty = lt / gx, tx = lt - ty * gx;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int px = tx * kTile + (tid & (kTile - 1));
-  const int py = ty * kTile + (tid >> 4);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int lx, ly;
+  tile_pixel(tid, lx, ly);
+  const int px = tx * kTile + lx, py = ty * kTile + ly;
   const bool inside = px < W && py < H;
   const float fpx = (float)px, fpy = (float)py;
   const uint2 rg = __ldg(ranges + tile);
   const uint32_t start = rg.x, end = rg.y;
+  if (tid == 0) {   // the pad entry: far away and steep, q = -inf rejects every pixel
+    s_a[kPad] = make_float4(1e30f, 1e30f, -1.f, 0.f);
+    s_b[kPad] = make_float4(-1.f, -1.f, 0.f, 0.f);
+    s_c[kPad] = 0.f;
+    s_e[kPad] = 0u;
+  }
 
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
   bool done = !inside;
@@ -43,49 +58,69 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
 
   for (uint32_t b0 = start; b0 < end; b0 += kRasterThreads) {
     if (__syncthreads_count(done) == kRasterThreads) break;
-    uint32_t idx = b0 + tid;
+    const uint32_t idx = b0 + tid;
     if (idx < end) {
-      uint32_t e = __ldg(vals + idx);
-      const float4* rec = splat + (size_t)e * 3;
-      s_a[tid] = __ldg(rec);
-      s_b[tid] = __ldg(rec + 1);
-      s_c[tid] = __ldg(reinterpret_cast<const float*>(rec + 2));
-      s_e[tid] = e;
+      const uint32_t e = __ldg(vals + idx);
+      Staged st;
+      uint32_t m;
+      stage_splat(splat + (size_t)e * 3, tx * kTile, ty * kTile, bc.l2tau, st, m);
+      s_a[tid] = st.a;
+      s_b[tid] = st.b;
+      s_c[tid] = st.c;
+      s_m[tid] = m;
+      if (kMaxT) s_e[tid] = e;
     }
     __syncthreads();
     const int nb = (int)min((uint32_t)kRasterThreads, end - b0);
-    for (int j = 0; j < nb; j++) {
-      const float4 a = s_a[j];
-      const float4 bq = s_b[j];
-      bool blend = false;
-      float Tbefore = T;
-      if (!done) {
-        evals++;
-        float dx, dy;
-        float power = splat_power(a.x, a.y, a.z, a.w, bq.x, fpx, fpy, dx, dy);
-        if (power <= 0.f) {
-          float alpha = fminf(bc.alpha_max, splat_alpha_raw(bq.y, power));
-          if (alpha >= bc.tau) {
-            float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+    // this warp's entries of the batch, in depth order, padded to a multiple of 4
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kRasterThreads / 32; k++) {
+      const int j = k * 32 + lane;
+      const bool hit = j < nb && ((s_m[j] >> warp) & 1u);
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) s_list[warp][cnt + __popc(bal & lanemask_lt())] = (uint16_t)j;
+      cnt += __popc(bal);
+    }
+    if (lane < 4) s_list[warp][cnt + lane] = (uint16_t)kPad;
+    __syncwarp();
+    if (__all_sync(0xffffffffu, done)) continue;
+    for (int t = 0; t < cnt; t += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int j = s_list[warp][t + u];
+        Staged s;
+        s.a = s_a[j];
+        s.b = s_b[j];
+        bool blend = false;
+        const float Tbefore = T;
+        if (!done) {
+          if (kStats) evals += (j != kPad);
+          float dx, dy;
+          const float q = splat_q(s, fpx, fpy, dx, dy);
+          if (splat_accept(q, s.b.y)) {                  // alpha >= tau and p <= 0
+            const float alpha = fminf(bc.alpha_max, __fmul_rn(bc.tau, fast_exp2(q)));
+            const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
             if (test_T < bc.t_min) {
               done = true;
             } else {
-              float w = __fmul_rn(alpha, T);
-              cr = __fmaf_rn(bq.z, w, cr);
-              cg = __fmaf_rn(bq.w, w, cg);
+              const float w = __fmul_rn(alpha, T);
+              cr = __fmaf_rn(s.b.z, w, cr);
+              cg = __fmaf_rn(s.b.w, w, cg);
               cb = __fmaf_rn(s_c[j], w, cb);
               T = test_T;
               last = b0 - start + j + 1;
               blend = true;
-              blends++;
+              if (kStats) blends++;
             }
           }
         }
+        if (kMaxT) {   // calibration: per-Gaussian max T before blending (warp max, one atomic)
+          const uint32_t m = __reduce_max_sync(0xffffffffu, blend ? __float_as_uint(Tbefore) : 0u);
+          if (lane == 0 && m) atomicMax(max_T_bits + s_e[j], m);
+        }
       }
-      if (max_T_bits) {   // calibration: per-Gaussian max T before blending (warp max, one atomic)
-        uint32_t m = __reduce_max_sync(0xffffffffu, blend ? __float_as_uint(Tbefore) : 0u);
-        if (lane == 0 && m) atomicMax(max_T_bits + s_e[j], m);
-      }
+      if (__all_sync(0xffffffffu, done)) break;
     }
   }
   if (inside) {
@@ -98,7 +133,7 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
     if (final_T) final_T[op] = T;
     if (n_contrib) n_contrib[op] = last;
   }
-  if (stats) {
+  if (kStats) {
     unsigned long long e1 = warp_sum((unsigned long long)evals), e2 = warp_sum((unsigned long long)blends);
     if (lane == 0) {
       atomicAdd(stats, e1);
@@ -145,8 +180,10 @@ extern "C" ags_status ags_rasterize(const ags_projected* proj, int64_t n, const 
   if (n > 0 && (!proj->splat || !sorted_vals)) return AGS_ERR_INVALID_ARG;
   if ((uintptr_t)proj->splat & 15u) return AGS_ERR_INVALID_ARG;
   const int tiles_per_view = cb.c[0].gx * cb.c[0].gy;
-  BlendConst bc{dp.tau, dp.t_min, dp.alpha_max, {dp.bg[0], dp.bg[1], dp.bg[2]}};
-  raster_kernel<<<(unsigned)(tiles_per_view * views), kRasterThreads, 0, (cudaStream_t)stream>>>(
+  BlendConst bc = make_blend_const(dp);
+  auto kern = stats ? (max_T ? raster_kernel<true, true> : raster_kernel<true, false>)
+                    : (max_T ? raster_kernel<false, true> : raster_kernel<false, false>);
+  kern<<<(unsigned)(tiles_per_view * views), kRasterThreads, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const float4*>(proj->splat), sorted_vals, reinterpret_cast<const uint2*>(ranges),
       cb.c[0].W, cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, image, final_T, n_contrib,
       reinterpret_cast<uint32_t*>(max_T), reinterpret_cast<unsigned long long*>(stats));

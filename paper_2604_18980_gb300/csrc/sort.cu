@@ -3,7 +3,7 @@
 //
 // "Onesweep" organisation: one pass over the keys builds the histograms of
 // every digit at once; then each digit pass is a single kernel in which each
-// block (256 threads x 16 keys) ranks its keys with warp-level match/ballot
+// block (256 threads x 8 keys) ranks its keys with warp-level match/ballot
 // (per-warp digit counters in shared memory), publishes its digit counts,
 // obtains each digit's global offset by a decoupled look-back over the
 // preceding blocks (bounded spin, partition ids from an atomic counter), and
@@ -18,8 +18,8 @@
 namespace ags {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortPart = kSortThreads * kSortItems;     // 4096 keys per block
+constexpr int kSortItems = 8;
+constexpr int kSortPart = kSortThreads * kSortItems;     // 2048 keys per block
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
 constexpr int kMaxPasses = 16;
@@ -94,9 +94,10 @@ __global__ void __launch_bounds__(kRadix) hist_scan_kernel(uint32_t* ghist) {
   h[t] = pre + incl - v;
 }
 
-__global__ void __launch_bounds__(kSortThreads, 2)
+__global__ void __launch_bounds__(kSortThreads, 4)
 onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-                uint32_t* __restrict__ vout, const int64_t* count_ptr, int64_t capacity, int shift, uint32_t mask,
+                uint32_t* __restrict__ vout, const int64_t* count_ptr, int64_t capacity, int identity, int shift,
+                uint32_t mask,
                 const uint32_t* __restrict__ gprefix, uint32_t* lookback, uint32_t* counter, int64_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
@@ -115,12 +116,18 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
   uint32_t val[kSortItems];
   uint32_t rank[kSortItems];
   const unsigned lt_mask = lanemask_lt();
+  // all loads first (memory-level parallelism), then the ranking
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
     uint32_t idx = base + warp * (32 * kSortItems) + i * 32 + lane;
     bool valid = idx < count;
-    key[i] = valid ? kin[idx] : 0ull;
-    val[i] = valid ? vin[idx] : 0u;
+    key[i] = valid ? __ldcs(kin + idx) : 0ull;
+    val[i] = valid ? (identity ? idx : __ldcs(vin + idx)) : 0u;
+  }
+#pragma unroll
+  for (int i = 0; i < kSortItems; i++) {
+    uint32_t idx = base + warp * (32 * kSortItems) + i * 32 + lane;
+    bool valid = idx < count;
     uint32_t d = valid ? ((uint32_t)(key[i] >> shift) & mask) : (uint32_t)kRadix;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = valid ? S.u.warp_hist[warp][d] : 0u;
@@ -229,12 +236,14 @@ extern "C" size_t ags_sort_workspace_bytes(int64_t capacity) {
 
 extern "C" ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                                const int64_t* d_num_pairs, int64_t capacity, int32_t begin_bit, int32_t end_bit,
-                               int32_t digit_bits, uint32_t* ranges, int64_t num_ranges, int32_t* result_in_alt,
-                               int64_t* d_status, void* ws, size_t ws_bytes, void* stream) {
+                               int32_t digit_bits, int32_t flags, uint32_t* ranges, int64_t num_ranges,
+                               int32_t* result_in_alt, int64_t* d_status, void* ws, size_t ws_bytes,
+                               void* stream) {
   using namespace ags;
   if (!d_num_pairs || !d_status || capacity < 0 || capacity >= AGS_MAX_PAIRS) return AGS_ERR_INVALID_ARG;
   if (begin_bit < 0 || end_bit > 64 || begin_bit > end_bit || digit_bits < 4 || digit_bits > 8)
     return AGS_ERR_INVALID_ARG;
+  if (flags & ~AGS_SORT_IDENTITY_VALUES) return AGS_ERR_INVALID_ARG;
   const int passes = (end_bit - begin_bit + digit_bits - 1) / digit_bits;
   if (passes > kMaxPasses) return AGS_ERR_INVALID_ARG;
   if (ranges && num_ranges <= 0) return AGS_ERR_INVALID_ARG;
@@ -269,7 +278,9 @@ extern "C" ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_al
       if (e != cudaSuccess) return AGS_ERR_CUDA;
       int sh = begin_bit + p * digit_bits;
       uint32_t mask = (1u << std::min(digit_bits, end_bit - sh)) - 1u;
-      onesweep_kernel<<<(unsigned)parts, kSortThreads, smem, st>>>(kin, vin, kout, vout, d_num_pairs, capacity, sh, mask,
+      const int identity = (p == 0 && (flags & AGS_SORT_IDENTITY_VALUES)) ? 1 : 0;
+      onesweep_kernel<<<(unsigned)parts, kSortThreads, smem, st>>>(kin, vin, kout, vout, d_num_pairs, capacity,
+                                                                  identity, sh, mask,
                                                                   ghist + p * kRadix, lookback, counters + p,
                                                                   d_status);
       e = cudaGetLastError();

@@ -33,12 +33,19 @@ def key_end_bit(views: int, tiles: int) -> int:
     return 32 + max(1, int(views * tiles - 1).bit_length())
 
 
+def digit_plan(bits: int, max_digit: int = 8) -> tuple:
+    """(passes, digit_bits) covering `bits` key bits with the fewest passes."""
+    passes = max(1, -(-bits // max_digit))
+    return passes, max(4, -(-bits // passes))
+
+
 class Renderer:
     """Buffers and launch sequence for rendering `scene` into `cams` (one batch)."""
 
     def __init__(self, scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_PLAIN, K: float = 0.0, lut=None,
                  sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 8,
-                 headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False):
+                 headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
+                 presort: bool = True):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -47,6 +54,7 @@ class Renderer:
         self.T = tiles_per_view(self.cams[0])
         self.device = scene["mean"].device
         self.digit_bits = digit_bits
+        self.presort = presort
         self.set_params(scale_mode, K, lut, sh_degree, bg)
         dev, V, n = self.device, self.V, self.n
         self.proj = dict(splat=torch.empty(V * n * 12, dtype=torch.float32, device=dev),
@@ -54,6 +62,15 @@ class Renderer:
                          rect=torch.empty(V * n * 4, dtype=torch.int16, device=dev),
                          tiles_touched=torch.empty(V * n, dtype=torch.int32, device=dev),
                          flags=torch.empty(V * n, dtype=torch.uint8, device=dev))
+        if presort:
+            # depth pre-sort of the Gaussians: the pair sort then needs only the tile digits
+            self.proj["depth_key"] = torch.empty(V * n, dtype=torch.int64, device=dev)
+            self.dkey_alt = torch.empty(V * n, dtype=torch.int64, device=dev)
+            self.order = torch.empty(V * n, dtype=torch.int32, device=dev)
+            self.order_alt = torch.empty(V * n, dtype=torch.int32, device=dev)
+            self.n_total = torch.tensor([V * n], dtype=torch.int64, device=dev)
+            self.ws_dsort = torch.empty(B.ags_sort_workspace_bytes(V * n), dtype=torch.uint8, device=dev)
+            self.dsort_end = 32 + int(V - 1).bit_length()
         self.status = torch.zeros(4, dtype=torch.int64, device=dev)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
         self.ws_emit = torch.empty(max(B.ags_emit_workspace_bytes(n, V), 16), dtype=torch.uint8, device=dev)
@@ -103,17 +120,43 @@ class Renderer:
     def end_bit(self) -> int:
         return key_end_bit(self.V, self.T)
 
+    @property
+    def begin_bit(self) -> int:
+        return 32 if self.presort else 0
+
+    def sort_plan(self) -> tuple:
+        """(passes, digit_bits) of the pair sort."""
+        if self.presort:
+            return digit_plan(self.end_bit - self.begin_bit, self.digit_bits)
+        return max(1, -(-self.end_bit // self.digit_bits)), self.digit_bits
+
+    def launches_per_forward(self) -> int:
+        n = 1 + 1 + (2 + self.sort_plan()[0] + 1) + 1
+        if self.presort:
+            n += 2 + digit_plan(self.dsort_end, self.digit_bits)[0]
+        return n
+
     # -- stages ---------------------------------------------------------------
     def preprocess(self):
         B.ags_preprocess(self.scene, self.cams, self.params, self.proj, self.status)
 
+    def depth_sort(self):
+        """Stable sort of the Gaussians by (view, depth): the emission order."""
+        if self.presort:
+            passes, db = digit_plan(self.dsort_end, self.digit_bits)
+            alt = B.ags_sort(self.proj["depth_key"], self.order, self.dkey_alt, self.order_alt, self.n_total,
+                             self.V * self.n, 0, self.dsort_end, db, None, 0, self.status, self.ws_dsort,
+                             flags=B.AGS_SORT_IDENTITY_VALUES)
+            self.emit_order = self.order_alt if alt else self.order
+
     def emit(self):
         B.ags_emit_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity, self.num_pairs,
-                         self.status, self.ws_emit)
+                         self.status, self.ws_emit, order=self.emit_order if self.presort else None)
 
     def sort(self):
-        alt = B.ags_sort(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity, 0,
-                         self.end_bit, self.digit_bits, self.ranges, self.V * self.T, self.status, self.ws_sort)
+        _, db = self.sort_plan()
+        alt = B.ags_sort(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity,
+                         self.begin_bit, self.end_bit, db, self.ranges, self.V * self.T, self.status, self.ws_sort)
         self.sorted_keys = self.keys_alt if alt else self.keys
         self.sorted_vals = self.vals_alt if alt else self.vals
 
@@ -124,6 +167,7 @@ class Renderer:
     def forward(self, max_T=None):
         """Enqueue the whole frame on the current stream; returns the image tensor."""
         self.preprocess()
+        self.depth_sort()
         self.emit()
         self.sort()
         self.rasterize(max_T)

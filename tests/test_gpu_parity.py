@@ -200,3 +200,39 @@ def test_backward_c1_scale_and_views():
         a = g[k].cpu().numpy().astype(np.float64).reshape(tot[k].shape)
         rel = np.linalg.norm(a - tot[k]) / max(np.linalg.norm(tot[k]), 1e-30)
         assert rel <= 1e-3, (k, rel)
+
+
+def test_depth_presort_equals_full_key_sort():
+    """Sorting the Gaussians by depth first and then only the tile digits of the
+    pairs gives exactly the stable sort of the full (tile | depth) keys."""
+    scene, cams = _c1(n=12000, W=200, H=150, views=3)
+    sc = R.scene_to_device(scene)
+    for mode, K in ((0, 0.0), (1, 0.5)):
+        a = R.Renderer(sc, cams, mode, K, presort=True)
+        b = R.Renderer(sc, cams, mode, K, presort=False)
+        ia, ib = a.forward().clone(), b.forward().clone()
+        a.check()
+        b.check()
+        assert a.pairs() == b.pairs()
+        np_ = a.pairs()
+        assert torch.equal(a.sorted_keys[:np_], b.sorted_keys[:np_])
+        assert torch.equal(a.sorted_vals[:np_], b.sorted_vals[:np_])
+        assert torch.equal(ia, ib)
+        assert torch.equal(a.ranges, b.ranges)
+
+
+def test_sort_identity_values_flag():
+    rng = np.random.default_rng(3)
+    count = 50000
+    keys = rng.integers(0, 1 << 36, count, dtype=np.uint64)
+    keys[::7] = keys[0]
+    k = torch.from_numpy(keys.view(np.int64)).cuda()
+    v = torch.full((count,), -1, dtype=torch.int32, device="cuda")
+    ka, va = torch.zeros_like(k), torch.zeros_like(v)
+    n = torch.tensor([count], dtype=torch.int64, device="cuda")
+    st = torch.zeros(4, dtype=torch.int64, device="cuda")
+    ws = torch.empty(B.ags_sort_workspace_bytes(count), dtype=torch.uint8, device="cuda")
+    alt = B.ags_sort(k, v, ka, va, n, count, 0, 36, 6, None, 0, st, ws, flags=B.AGS_SORT_IDENTITY_VALUES)
+    B.ags_check(st)
+    vs = (va if alt else v).cpu().numpy()
+    np.testing.assert_array_equal(vs, np.argsort(keys, kind="stable"))

@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(B.AgsCamera) == 4 * (2 + 4 + 12 + 3 + 1)
     assert ctypes.sizeof(B.AgsParams) == 4 * (3 + 5 + 32 + 3)
     assert ctypes.sizeof(B.AgsGaussians) == 8 * 6
-    assert ctypes.sizeof(B.AgsProjected) == 8 * 5
+    assert ctypes.sizeof(B.AgsProjected) == 8 * 6
 
 
 def test_status_strings_and_version(lib):
@@ -57,7 +57,7 @@ def test_workspace_sizes(lib):
     assert B.ags_emit_workspace_bytes(0, 1) == 256
     assert B.ags_emit_workspace_bytes(2048, 1) == 256 + 8
     assert B.ags_emit_workspace_bytes(2049, 1) == 256 + 16
-    assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 256 * 4 + 256 * 4
+    assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 256 * 4 + 2 * 256 * 4
     assert B.ags_backward_workspace_bytes(10, 2) == 10 * 2 * 9 * 4
 
 
@@ -89,12 +89,14 @@ def test_invalid_arguments_rejected_on_host(lib):
     # sort: bad digit width, capacity beyond the limit, missing workspace
     npairs = ctypes.c_void_p(16)
     alt = ctypes.c_int32(0)
-    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 9, None, 0, ctypes.byref(alt), st, None, 0,
+    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 9, 0, None, 0, ctypes.byref(alt), st, None, 0,
                       None) == 1
-    assert L.ags_sort(None, None, None, None, npairs, B.AGS_MAX_PAIRS, 0, 40, 8, None, 0, ctypes.byref(alt), st,
+    assert L.ags_sort(None, None, None, None, npairs, B.AGS_MAX_PAIRS, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st,
                       None, 0, None) == 1
     assert L.ags_sort(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
-                      10, 0, 40, 8, None, 0, ctypes.byref(alt), st, None, 0, None) == 1
+                      10, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st, None, 0, None) == 1
+    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 8, 2, None, 0, ctypes.byref(alt), st, None, 0,
+                      None) == 1
     # emit: workspace too small
     assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, None, 0, None) == 1
     # mismatched view sizes
