@@ -42,6 +42,12 @@ FALLBACK_HBM_GBS = 6800.0
 # 1 - alpha and the transmittance product (2); the three colour FMAs and
 # alpha*T (4) = 18.  The exponential itself runs on the SFU.
 RASTER_OPS_PER_EVAL = 18
+# DRAM bytes (read + write) of one raster_kernel<false,false> launch per view of
+# this workload, from the ncu capture summarised in
+# profiles/raster_kernel_c2_clusters1m_1080p_1view.md (1 view; the kernel's
+# traffic grows with the number of views it renders).  Set to None whenever the
+# kernel changes until it is captured again.
+RASTER_TRAFFIC_PER_VIEW = 16.785664e6 + 0.7872e6
 
 
 def parse():
@@ -402,9 +408,11 @@ def stage_bytes(stage, r, passes):
     if stage == "emit":
         # order (4 B), rectangle (8 B) per Gaussian, depth (4 B) per survivor; 12 B per pair
         return G * 12 + live * 4 + P * 12, "emit_kernel"
-    # preprocess: 44 B geometry per Gaussian and view; survivors read 192 B SH and
-    # write 48 B splat + 4 depth + 8 rect + 4 count + 1 flag + 8 depth key; culled write 21 B
-    return G * 44 + live * (192 + 73) + (G - live) * 21, "preprocess_kernel"
+    # preprocess: 44 B geometry per Gaussian and 192 B SH per Gaussian that survives
+    # in some view, read once per batch; per view, survivors write 48 B splat + 4 depth
+    # + 8 rect + 4 count + 1 flag + 8 depth key = 73 B, culled Gaussians 21 B
+    any_live = int(((r.proj["flags"].view(V, n) & 0x80) == 0).any(0).sum().item())
+    return n * 44 + any_live * 192 + live * 73 + (G - live) * 21, "preprocess_kernel"
 
 
 def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):
@@ -416,8 +424,10 @@ def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12           # FP32 lanes x clock, Tops/s
         achieved = evals * RASTER_OPS_PER_EVAL / (ms / 1e3) / 1e12
+        traffic = None if RASTER_TRAFFIC_PER_VIEW is None else RASTER_TRAFFIC_PER_VIEW * V
         return {"kernel": "raster_kernel", "bound": "alu", "achieved": achieved, "peak": peak_ops,
-                "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read+write of a 1-view capture x views",
                 "work": "%d pixel-pair evaluations x %d FP32 ops" % (evals, RASTER_OPS_PER_EVAL),
                 "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (%s)" % (sms, sm_mhz, pk_src)}
     hbm = pk.get("hbm_gbs", FALLBACK_HBM_GBS)

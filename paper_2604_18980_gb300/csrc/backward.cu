@@ -80,7 +80,7 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
       const float4* rec = splat + (size_t)e * 3;
       Staged st;
       uint32_t m;
-      stage_splat(rec, tx * kTile, ty * kTile, bc.l2tau, st, m);
+      stage_splat<8, 4>(rec, tx * kTile, ty * kTile, bc.l2tau, st, m);
       const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
       s_a[tid] = st.a;
       s_b[tid] = st.b;

@@ -51,6 +51,9 @@ struct Staged {
 };
 
 // Splat record (48 bytes): u v A B | C opacity r g | b Th Sxx Syy.
+// Mask bit w: the ellipse can reach block w of the tile, blocks being
+// BW x BH pixels in row-major order of (16/BW) x (16/BH).
+template <int BW, int BH>
 __device__ __forceinline__ void stage_splat(const float4* rec, int tx0, int ty0, float l2tau, Staged& s,
                                             uint32_t& mask) {
   const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
@@ -66,10 +69,11 @@ __device__ __forceinline__ void stage_splat(const float4* rec, int tx0, int ty0,
     const float hy = sqrtf(r2n * r2.w) * 1.0001f + 0.01f;
     const float lx = r0.x - hx - (float)tx0, ux = r0.x + hx - (float)tx0;   // tile-relative
     const float ly = r0.y - hy - (float)ty0, uy = r0.y + hy - (float)ty0;
+    constexpr int NBX = kTile / BW, NBY = kTile / BH;
 #pragma unroll
-    for (int w = 0; w < 8; w++) {
-      const float cx0 = (float)(8 * (w & 1)), ry0 = (float)(4 * (w >> 1));
-      if (ux >= cx0 && lx <= cx0 + 7.f && uy >= ry0 && ly <= ry0 + 3.f) mask |= 1u << w;
+    for (int w = 0; w < NBX * NBY; w++) {
+      const float cx0 = (float)(BW * (w % NBX)), ry0 = (float)(BH * (w / NBX));
+      if (ux >= cx0 && lx <= cx0 + (float)(BW - 1) && uy >= ry0 && ly <= ry0 + (float)(BH - 1)) mask |= 1u << w;
     }
   }
 }
@@ -89,12 +93,23 @@ __device__ __forceinline__ bool splat_accept(float q, float base) {
   return __float_as_uint(q) <= __float_as_uint(base);
 }
 
+// q = (a2 dx^2 + base) + dy (b2 dx + c2 dy), split so that pixels sharing a
+// column share the dx terms: splat_qx gives (P, Bx), splat_qy finishes q.
+__device__ __forceinline__ void splat_qx(const Staged& s, float dx, float& P, float& Bx) {
+  P = __fmaf_rn(__fmul_rn(s.a.z, dx), dx, s.b.y);
+  Bx = __fmul_rn(s.a.w, dx);
+}
+
+__device__ __forceinline__ float splat_qy(const Staged& s, float P, float Bx, float dy) {
+  return __fmaf_rn(dy, __fmaf_rn(s.b.x, dy, Bx), P);
+}
+
 __device__ __forceinline__ float splat_q(const Staged& s, float px, float py, float& dx, float& dy) {
   dx = __fsub_rn(s.a.x, px);
   dy = __fsub_rn(s.a.y, py);
-  const float t = __fmaf_rn(s.a.z, dx, __fmul_rn(s.a.w, dy));
-  const float base = __fmaf_rn(__fmul_rn(s.b.x, dy), dy, s.b.y);
-  return __fmaf_rn(t, dx, base);
+  float P, Bx;
+  splat_qx(s, dx, P, Bx);
+  return splat_qy(s, P, Bx, dy);
 }
 
 __device__ __forceinline__ float fast_exp2(float x) {

@@ -1,13 +1,13 @@
 // emit.cu -- Gaussian-tile pair emission (Sec. 2.1 pair generation, Sec. 3.3).
 //
-// Single pass: each 256-thread block takes a partition of 2048 Gaussians
+// Single pass: each 256-thread block takes a partition of 1024 Gaussians
 // (partition ids handed out by an atomic counter, so lower partitions are
 // always running), computes the pair counts from the tile rectangles, scans
 // them inside the block, obtains the global offset of the partition through a
 // decoupled look-back over the preceding partitions' published sums, and then
-// emits the partition's pairs load-balanced across the block: thread j of the
-// block writes pairs j, j+256, ... so stores are coalesced whatever the
-// per-Gaussian tile counts are.
+// emits the partition's pairs load-balanced across the block: each warp takes
+// chunks of 256 consecutive pairs and stages them in shared memory, so stores
+// are coalesced whatever the per-Gaussian tile counts are.
 //
 //   key = ((view * tiles_per_view + tile) << 32) | float_bits(depth),  val = view * n + i
 //
@@ -18,8 +18,11 @@
 namespace ags {
 
 constexpr int kEmitThreads = 256;
-constexpr int kEmitItems = 8;
-constexpr int kEmitPart = kEmitThreads * kEmitItems;
+constexpr int kEmitItems = 4;
+constexpr int kEmitPart = kEmitThreads * kEmitItems;      // 1024 Gaussians per partition
+constexpr int kEmitRun = 8;                               // pairs generated per lane per chunk
+constexpr int kEmitChunk = 32 * kEmitRun;                 // pairs per warp chunk
+constexpr int kEmitStride = kEmitRun + 1;                 // padded staging row (fewer bank conflicts)
 constexpr uint64_t kAgg = 1ull << 62;
 constexpr uint64_t kInc = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
@@ -136,23 +139,50 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
   __syncthreads();
   const uint64_t prefix = s_prefix;
 
-  // 4. load-balanced emission
-  for (uint32_t j = tid; j < agg; j += kEmitThreads) {
-    // last entry li with s_off[li] <= j (upper bound - 1): always a non-empty one
-    int lo = 0, hi = kEmitPart;   // invariant: s_off[lo] <= j < s_off[hi]
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (s_off[mid] <= j) lo = mid; else hi = mid;
+  // 4. load-balanced emission: warps take chunks of 256 consecutive pairs; each
+  //    lane generates 8 consecutive pairs (one binary search, then walking the
+  //    rectangle row by row) into a warp-private staging row, and the warp
+  //    writes the chunk out with coalesced stores.
+  __shared__ unsigned long long s_key[kEmitThreads / 32][32 * kEmitStride];
+  __shared__ uint32_t s_val[kEmitThreads / 32][32 * kEmitStride];
+  for (uint32_t w0 = (uint32_t)warp * kEmitChunk; w0 < agg; w0 += (kEmitThreads / 32) * kEmitChunk) {
+    const uint32_t j0 = w0 + (uint32_t)lane * kEmitRun;
+    if (j0 < agg) {
+      int lo = 0, hi = kEmitPart;   // invariant: s_off[lo] <= j0 < s_off[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= j0) lo = mid; else hi = mid;
+      }
+      uint32_t r = j0 - s_off[lo];
+      uint32_t w = s_w[lo];
+      uint32_t ry = r / w, rx = r - ry * w;
+#pragma unroll
+      for (int k = 0; k < kEmitRun; k++) {
+        const uint32_t j = j0 + k;
+        if (j >= agg) break;
+        while (j >= s_off[lo + 1]) {          // next Gaussian with pairs
+          lo++;
+          w = s_w[lo];
+          rx = 0;
+          ry = 0;
+        }
+        const uint32_t tile = s_base[lo] + ry * gx + rx;
+        s_key[warp][lane * kEmitStride + k] = ((unsigned long long)tile << 32) | s_dbits[lo];
+        s_val[warp][lane * kEmitStride + k] = s_idx[lo];
+        if (++rx == w) { rx = 0; ry++; }
+      }
     }
-    uint32_t r = j - s_off[lo];
-    uint32_t w = s_w[lo];
-    uint32_t ty = r / w;
-    uint32_t tile = s_base[lo] + ty * gx + (r - ty * w);
-    uint64_t pos = prefix + j;
-    if (pos < (uint64_t)capacity) {
-      keys[pos] = ((uint64_t)tile << 32) | s_dbits[lo];
-      vals[pos] = s_idx[lo];
+    __syncwarp();
+    const uint32_t nval = min((uint32_t)kEmitChunk, agg - w0);
+    for (uint32_t m = lane; m < nval; m += 32) {
+      const uint64_t pos = prefix + w0 + m;
+      const uint32_t si = (m / kEmitRun) * kEmitStride + (m % kEmitRun);
+      if (pos < (uint64_t)capacity) {
+        keys[pos] = s_key[warp][si];
+        vals[pos] = s_val[warp][si];
+      }
     }
+    __syncwarp();
   }
   if (part == num_parts - 1 && tid == 0) {
     int64_t tot = (int64_t)(prefix + agg);

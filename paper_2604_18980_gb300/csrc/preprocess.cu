@@ -107,9 +107,10 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, in
 
     // colour: SH at the world-space direction from the camera centre
     if (!sh_loaded) {
-      for (int k = 0; k < nc; k++)
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) sh[k][ch] = __ldg(in.sh + (int64_t)(k * 3 + ch) * n + i);
+      for (int k = 0; k < 16; k++)
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) sh[k][ch] = k < nc ? __ldg(in.sh + (int64_t)(k * 3 + ch) * n + i) : 0.f;
       sh_loaded = true;
     }
     const float dx = m[0] - C.campos[0], dy = m[1] - C.campos[1], dz = m[2] - C.campos[2];
@@ -117,9 +118,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, in
     float Y[16];
     sh_basis(P.sh_degree, dx * il, dy * il, dz * il, Y);
     float rgb[3] = {0.5f, 0.5f, 0.5f};
-    for (int k = 0; k < nc; k++) {
 #pragma unroll
-      for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(sh[k][ch], Y[k], rgb[ch]);
+    for (int k = 0; k < 16; k++) {
+      if (k < nc) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(sh[k][ch], Y[k], rgb[ch]);
+      }
     }
     uint8_t flags = (uint8_t)pj.fclamp;
     bool bad = false;

@@ -1,12 +1,12 @@
 // raster.cu -- per-tile front-to-back alpha blending (Eq. 1, Eq. 2) and the
 // T_up calibration table (Sec. 3.4).
 //
-// One 256-thread CTA per 16x16 tile of each view, one pixel per thread (each
-// warp a 4x8 pixel block).  The tile's depth-ordered pairs are staged in
-// batches of 256: each thread gathers one 48-byte splat record, converts it
+// One 128-thread CTA per 16x16 tile of each view, two pixels per thread (each
+// warp an 8x8 pixel block).  The tile's depth-ordered pairs are staged in
+// batches of 128: each thread gathers one 48-byte splat record, converts it
 // to the log2 form of Eq. 1 and computes the mask of warp blocks its
-// alpha >= tau ellipse can reach; then every warp walks the batch, skipping
-// (warp-uniformly) the splats that miss its block.  A warp leaves the batch
+// alpha >= tau ellipse can reach; each warp then compacts the batch to the
+// splats that reach its block and walks that list.  A warp leaves the batch
 // once all its pixels reached the transmittance floor, the CTA once all warps
 // did (__syncthreads_count vote).  The blend always uses the conic of the original
 // covariance and tau (Sec. 3.3 "dual-size strategy"): the scale mode only ever
@@ -17,32 +17,38 @@
 
 namespace ags {
 
-// kStats: count evaluations and blends; kMaxT: calibration output.  The
-// benchmark's kernel is the <false, false> instance.
+// 128 threads per tile, four warps of 8x8 pixels; lane l blends the two
+// pixels (8*(w&1) + (l&7), 8*(w>>1) + (l>>3)) and the one 4 rows below, which
+// share dx.  kStats: count evaluations and blends; kMaxT: calibration output.
+// The benchmark's kernel is the <false, false> instance.
+constexpr int kBlendThreads = 128;
+constexpr int kBlendWarps = kBlendThreads / 32;
+
 template <bool kStats, bool kMaxT>
-__global__ void __launch_bounds__(kRasterThreads)
+__global__ void __launch_bounds__(kBlendThreads)
 raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
               int W, int H, int gx, int tiles_per_view, BlendConst bc, float* __restrict__ image,
               float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ max_T_bits,
               unsigned long long* stats) {
-  constexpr int kPad = kRasterThreads;                // index of an always-rejected entry
-  __shared__ float4 s_a[kRasterThreads + 1];          // u v a2 b2
-  __shared__ float4 s_b[kRasterThreads + 1];          // c2 base r g
-  __shared__ float s_c[kRasterThreads + 1];           // b
-  __shared__ uint32_t s_m[kRasterThreads];            // warp-block mask
-  __shared__ uint32_t s_e[kRasterThreads + 1];        // splat index (calibration only)
-  __shared__ uint16_t s_list[kRasterThreads / 32][kRasterThreads + 4];   // per-warp entries, padded
+  constexpr int kB = kBlendThreads;                    // splats staged per batch
+  constexpr int kPad = kB;                             // index of an always-rejected entry
+  __shared__ float4 s_a[kB + 1];                       // u v a2 b2
+  __shared__ float4 s_b[kB + 1];                       // c2 base r g
+  __shared__ float s_c[kB + 1];                        // b
+  __shared__ uint32_t s_m[kB];                         // 8x8 block mask
+  __shared__ uint32_t s_e[kB + 1];                     // splat index (calibration only)
+  __shared__ uint16_t s_list[kBlendWarps][kB + 4];     // per-warp entries, padded
 
   const int tile = blockIdx.x;
   const int view = tile / tiles_per_view;
   const int lt = tile - view * tiles_per_view;
   const int ty = lt / gx, tx = lt - ty * gx;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int lx, ly;
-  tile_pixel(tid, lx, ly);
-  const int px = tx * kTile + lx, py = ty * kTile + ly;
-  const bool inside = px < W && py < H;
-  const float fpx = (float)px, fpy = (float)py;
+  const int px = tx * kTile + 8 * (warp & 1) + (lane & 7);
+  const int py0 = ty * kTile + 8 * (warp >> 1) + (lane >> 3);
+  const int py1 = py0 + 4;
+  const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
+  const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
   const uint2 rg = __ldg(ranges + tile);
   const uint32_t start = rg.x, end = rg.y;
   if (tid == 0) {   // the pad entry: far away and steep, q = -inf rejects every pixel
@@ -52,18 +58,19 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
     s_e[kPad] = 0u;
   }
 
-  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
-  bool done = !inside;
-  uint32_t last = 0, evals = 0, blends = 0;
+  float T0 = 1.f, r0 = 0.f, g0 = 0.f, b0c = 0.f;
+  float T1 = 1.f, r1 = 0.f, g1 = 0.f, b1c = 0.f;
+  bool done0 = !in0, done1 = !in1;
+  uint32_t last0 = 0, last1 = 0, evals = 0, blends = 0;
 
-  for (uint32_t b0 = start; b0 < end; b0 += kRasterThreads) {
-    if (__syncthreads_count(done) == kRasterThreads) break;
-    const uint32_t idx = b0 + tid;
+  for (uint32_t bb = start; bb < end; bb += kB) {
+    if (__syncthreads_count(done0 && done1) == kBlendThreads) break;
+    const uint32_t idx = bb + tid;
     if (idx < end) {
       const uint32_t e = __ldg(vals + idx);
       Staged st;
       uint32_t m;
-      stage_splat(splat + (size_t)e * 3, tx * kTile, ty * kTile, bc.l2tau, st, m);
+      stage_splat<8, 8>(splat + (size_t)e * 3, tx * kTile, ty * kTile, bc.l2tau, st, m);
       s_a[tid] = st.a;
       s_b[tid] = st.b;
       s_c[tid] = st.c;
@@ -71,11 +78,11 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
       if (kMaxT) s_e[tid] = e;
     }
     __syncthreads();
-    const int nb = (int)min((uint32_t)kRasterThreads, end - b0);
+    const int nb = (int)min((uint32_t)kB, end - bb);
     // this warp's entries of the batch, in depth order, padded to a multiple of 4
     int cnt = 0;
 #pragma unroll
-    for (int k = 0; k < kRasterThreads / 32; k++) {
+    for (int k = 0; k < kB / 32; k++) {
       const int j = k * 32 + lane;
       const bool hit = j < nb && ((s_m[j] >> warp) & 1u);
       const unsigned bal = __ballot_sync(0xffffffffu, hit);
@@ -84,7 +91,7 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
     }
     if (lane < 4) s_list[warp][cnt + lane] = (uint16_t)kPad;
     __syncwarp();
-    if (__all_sync(0xffffffffu, done)) continue;
+    if (__all_sync(0xffffffffu, done0 && done1)) continue;
     for (int t = 0; t < cnt; t += 4) {
 #pragma unroll
       for (int u = 0; u < 4; u++) {
@@ -92,46 +99,79 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
         Staged s;
         s.a = s_a[j];
         s.b = s_b[j];
-        bool blend = false;
-        const float Tbefore = T;
-        if (!done) {
+        const float dx = __fsub_rn(s.a.x, fpx);
+        float P, Bx;
+        splat_qx(s, dx, P, Bx);
+        const uint32_t pos1 = bb - start + j + 1;
+        bool bl0 = false, bl1 = false;
+        const float Tb0 = T0, Tb1 = T1;
+        if (!done0) {
           if (kStats) evals += (j != kPad);
-          float dx, dy;
-          const float q = splat_q(s, fpx, fpy, dx, dy);
-          if (splat_accept(q, s.b.y)) {                  // alpha >= tau and p <= 0
+          const float q = splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy0));
+          if (splat_accept(q, s.b.y)) {
             const float alpha = fminf(bc.alpha_max, __fmul_rn(bc.tau, fast_exp2(q)));
-            const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            const float test_T = __fmul_rn(T0, __fsub_rn(1.f, alpha));
             if (test_T < bc.t_min) {
-              done = true;
+              done0 = true;
             } else {
-              const float w = __fmul_rn(alpha, T);
-              cr = __fmaf_rn(s.b.z, w, cr);
-              cg = __fmaf_rn(s.b.w, w, cg);
-              cb = __fmaf_rn(s_c[j], w, cb);
-              T = test_T;
-              last = b0 - start + j + 1;
-              blend = true;
+              const float w = __fmul_rn(alpha, T0);
+              r0 = __fmaf_rn(s.b.z, w, r0);
+              g0 = __fmaf_rn(s.b.w, w, g0);
+              b0c = __fmaf_rn(s_c[j], w, b0c);
+              T0 = test_T;
+              last0 = pos1;
+              bl0 = true;
+              if (kStats) blends++;
+            }
+          }
+        }
+        if (!done1) {
+          if (kStats) evals += (j != kPad);
+          const float q = splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy1));
+          if (splat_accept(q, s.b.y)) {
+            const float alpha = fminf(bc.alpha_max, __fmul_rn(bc.tau, fast_exp2(q)));
+            const float test_T = __fmul_rn(T1, __fsub_rn(1.f, alpha));
+            if (test_T < bc.t_min) {
+              done1 = true;
+            } else {
+              const float w = __fmul_rn(alpha, T1);
+              r1 = __fmaf_rn(s.b.z, w, r1);
+              g1 = __fmaf_rn(s.b.w, w, g1);
+              b1c = __fmaf_rn(s_c[j], w, b1c);
+              T1 = test_T;
+              last1 = pos1;
+              bl1 = true;
               if (kStats) blends++;
             }
           }
         }
         if (kMaxT) {   // calibration: per-Gaussian max T before blending (warp max, one atomic)
-          const uint32_t m = __reduce_max_sync(0xffffffffu, blend ? __float_as_uint(Tbefore) : 0u);
+          const uint32_t mine = max(bl0 ? __float_as_uint(Tb0) : 0u, bl1 ? __float_as_uint(Tb1) : 0u);
+          const uint32_t m = __reduce_max_sync(0xffffffffu, mine);
           if (lane == 0 && m) atomicMax(max_T_bits + s_e[j], m);
         }
       }
-      if (__all_sync(0xffffffffu, done)) break;
+      if (__all_sync(0xffffffffu, done0 && done1)) break;
     }
   }
-  if (inside) {
-    const size_t hw = (size_t)W * H;
-    const size_t o = (size_t)view * 3 * hw + (size_t)py * W + px;
-    image[o] = cr + T * bc.bg[0];
-    image[o + hw] = cg + T * bc.bg[1];
-    image[o + 2 * hw] = cb + T * bc.bg[2];
-    const size_t op = (size_t)view * hw + (size_t)py * W + px;
-    if (final_T) final_T[op] = T;
-    if (n_contrib) n_contrib[op] = last;
+  const size_t hw = (size_t)W * H;
+  if (in0) {
+    const size_t o = (size_t)view * 3 * hw + (size_t)py0 * W + px;
+    image[o] = r0 + T0 * bc.bg[0];
+    image[o + hw] = g0 + T0 * bc.bg[1];
+    image[o + 2 * hw] = b0c + T0 * bc.bg[2];
+    const size_t op = (size_t)view * hw + (size_t)py0 * W + px;
+    if (final_T) final_T[op] = T0;
+    if (n_contrib) n_contrib[op] = last0;
+  }
+  if (in1) {
+    const size_t o = (size_t)view * 3 * hw + (size_t)py1 * W + px;
+    image[o] = r1 + T1 * bc.bg[0];
+    image[o + hw] = g1 + T1 * bc.bg[1];
+    image[o + 2 * hw] = b1c + T1 * bc.bg[2];
+    const size_t op = (size_t)view * hw + (size_t)py1 * W + px;
+    if (final_T) final_T[op] = T1;
+    if (n_contrib) n_contrib[op] = last1;
   }
   if (kStats) {
     unsigned long long e1 = warp_sum((unsigned long long)evals), e2 = warp_sum((unsigned long long)blends);
@@ -183,7 +223,7 @@ extern "C" ags_status ags_rasterize(const ags_projected* proj, int64_t n, const 
   BlendConst bc = make_blend_const(dp);
   auto kern = stats ? (max_T ? raster_kernel<true, true> : raster_kernel<true, false>)
                     : (max_T ? raster_kernel<false, true> : raster_kernel<false, false>);
-  kern<<<(unsigned)(tiles_per_view * views), kRasterThreads, 0, (cudaStream_t)stream>>>(
+  kern<<<(unsigned)(tiles_per_view * views), kBlendThreads, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const float4*>(proj->splat), sorted_vals, reinterpret_cast<const uint2*>(ranges),
       cb.c[0].W, cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, image, final_T, n_contrib,
       reinterpret_cast<uint32_t*>(max_T), reinterpret_cast<unsigned long long*>(stats));

@@ -26,6 +26,7 @@ constexpr int kMaxPasses = 16;
 constexpr uint32_t kLbAgg = 1u << 30;
 constexpr uint32_t kLbInc = 2u << 30;
 constexpr uint32_t kLbMask = (1u << 30) - 1u;
+constexpr int kLookWindow = 8;                              // predecessors polled per round trip
 constexpr size_t kSortHdr = 256;                           // pass counters
 constexpr size_t kSortHistBytes = (size_t)kMaxPasses * kRadix * 4;
 
@@ -161,24 +162,34 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
   for (int w = 0; w < warp; w++) wpre += S.warp_tot[w];
   S.digit_off[tid] = wpre + incl - tot;
 
-  // decoupled look-back for this digit
+  // decoupled look-back for this digit, kLookWindow predecessors per round trip:
+  // add the aggregates back to the nearest inclusive prefix; re-poll from the
+  // first predecessor that has not published yet.
   uint32_t excl = 0;
   if (part > 0) {
     int64_t p = (int64_t)part - 1;
     const uint64_t t0 = globaltimer_ns();
-    while (p >= 0) {
-      uint32_t s = ld_relaxed_u32(lookback + (size_t)p * kRadix + tid);
-      uint32_t flag = s >> 30;
-      if (flag == 0u) {
-        if (globaltimer_ns() - t0 > kWaitLimitNs) {
-          set_status(status, AGS_ERR_TIMEOUT, kStageSort);
-          break;
-        }
-        continue;
+    bool found = false;
+    while (!found) {
+      uint32_t sv[kLookWindow];
+#pragma unroll
+      for (int k = 0; k < kLookWindow; k++)
+        sv[k] = (p - k >= 0) ? ld_relaxed_u32(lookback + (size_t)(p - k) * kRadix + tid) : kLbInc;
+      int used = 0;
+#pragma unroll
+      for (int k = 0; k < kLookWindow; k++) {
+        if (found || used < k) continue;           // stop at the first unpublished entry
+        const uint32_t flag = sv[k] >> 30;
+        if (flag == 0u) continue;
+        excl += sv[k] & kLbMask;
+        used = k + 1;
+        if (flag == 2u) found = true;
       }
-      excl += s & kLbMask;
-      if (flag == 2u) break;
-      p--;
+      p -= used;
+      if (!found && used < kLookWindow && globaltimer_ns() - t0 > kWaitLimitNs) {
+        set_status(status, AGS_ERR_TIMEOUT, kStageSort);
+        break;
+      }
     }
     st_relaxed_u32(lb + tid, kLbInc | ((excl + tot) & kLbMask));
   }

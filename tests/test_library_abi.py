@@ -55,8 +55,8 @@ def test_status_strings_and_version(lib):
 
 def test_workspace_sizes(lib):
     assert B.ags_emit_workspace_bytes(0, 1) == 256
-    assert B.ags_emit_workspace_bytes(2048, 1) == 256 + 8
-    assert B.ags_emit_workspace_bytes(2049, 1) == 256 + 16
+    assert B.ags_emit_workspace_bytes(1024, 1) == 256 + 8
+    assert B.ags_emit_workspace_bytes(1025, 1) == 256 + 16
     assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 256 * 4 + 2 * 256 * 4
     assert B.ags_backward_workspace_bytes(10, 2) == 10 * 2 * 9 * 4
 
