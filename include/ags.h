@@ -165,6 +165,31 @@ ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32_t views,
                           int64_t* d_num_pairs, int64_t* d_status,
                           void* ws, size_t ws_bytes, void* stream);
 
+/* Largest views*n that ags_emit_pairs_noalloc accepts (2^24). */
+int64_t ags_emit_pairs_noalloc_max_gaussians(void);
+
+/* ags_emit_pairs for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this exists for callers that own no allocator of their
+ * own -- a host application that gives a plugin a fixed device-memory budget
+ * and forbids it to allocate, or code calling this C ABI from a language with
+ * no CUDA allocator binding -- and so cannot provide the workspace that
+ * ags_emit_pairs needs.  Arguments and results are those of ags_emit_pairs
+ * without `ws`/`ws_bytes`; the caller still passes every input and output.
+ * The look-back scratch is a library-owned static device array of
+ * 256 + 8 * (2^24 / 1024) bytes (about 128 KiB), held by every GPU that loads
+ * the library until the process exits; views*n above
+ * ags_emit_pairs_noalloc_max_gaussians() is rejected with
+ * AGS_ERR_INVALID_ARG.  The first call on a device looks up that array's
+ * device address (with the device current) and caches it, so make the first
+ * call on each device before any stream capture.  Every call zeroes the part
+ * of the array it uses on `stream`; calls whose work overlaps on the GPU (on
+ * different streams) share the array and race: serialise them.  No call
+ * allocates or frees memory. */
+ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t n, int32_t views,
+                                  const ags_camera* cams, const uint32_t* order,
+                                  uint64_t* keys, uint32_t* vals, int64_t capacity,
+                                  int64_t* d_num_pairs, int64_t* d_status, void* stream);
+
 /* Scratch bytes needed by ags_sort for up to `capacity` pairs. */
 size_t ags_sort_workspace_bytes(int64_t capacity);
 

@@ -68,6 +68,8 @@ EXPORTS = {
     "ags_preprocess": ([_P, _P, _I32, _P, _P, _P, _P], _I32),
     "ags_emit_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
     "ags_emit_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P], _I32),
+    "ags_emit_pairs_noalloc_max_gaussians": ([], _I64),
+    "ags_emit_pairs_noalloc": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P], _I32),
     "ags_sort_workspace_bytes": ([_I64], ctypes.c_size_t),
     "ags_sort": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _I32, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P],
                  _I32),
@@ -218,6 +220,15 @@ def ags_emit_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, w
                              int(capacity), ptr(d_num_pairs), ptr(d_status), ptr(ws),
                              ws.numel() * ws.element_size() if ws is not None else 0, stream_handle(stream)),
         "ags_emit_pairs")
+
+
+def ags_emit_pairs_noalloc(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, order=None, stream=None):
+    """ags_emit_pairs with the library's static scratch (for callers that cannot allocate)."""
+    pr = projected(proj)
+    cs = cameras(cams)
+    _ok(lib().ags_emit_pairs_noalloc(ctypes.byref(pr), int(n), len(cams), cs, ptr(order), ptr(keys), ptr(vals),
+                                     int(capacity), ptr(d_num_pairs), ptr(d_status), stream_handle(stream)),
+        "ags_emit_pairs_noalloc")
 
 
 def ags_sort_workspace_bytes(capacity: int) -> int:

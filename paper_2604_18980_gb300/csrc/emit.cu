@@ -13,6 +13,8 @@
 //
 // The look-back spins are bounded (globaltimer); on expiry the status block
 // records AGS_ERR_TIMEOUT and every store stays inside `capacity`.
+#include <mutex>
+
 #include "ags_internal.cuh"
 
 namespace ags {
@@ -219,6 +221,73 @@ extern "C" ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32
   const size_t parts = emit_parts(total);
   uint32_t tiles_per_view = (uint32_t)cb.c[0].gx * (uint32_t)cb.c[0].gy;
   if ((uint64_t)tiles_per_view * (uint64_t)views >= (1ull << 32)) return AGS_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemsetAsync(ws, 0, 256 + 8 * parts, st);
+  if (e != cudaSuccess) return AGS_ERR_CUDA;
+  uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
+  uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
+  emit_kernel<<<(unsigned)parts, kEmitThreads, 0, st>>>(
+      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, (uint32_t)n, tiles_per_view,
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, (uint32_t)parts);
+  return launch_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of ags_emit_pairs (see include/ags.h).
+//
+// The look-back state lives in a library-owned device array instead of a
+// caller workspace.  In host code `g_emit_scratch` names a host-side stand-in,
+// not a device address, so the device address is looked up with
+// cudaGetSymbolAddress once per device (with that device current) and cached.
+// ---------------------------------------------------------------------------
+namespace ags {
+
+constexpr int64_t kNoAllocMaxGaussianViews = (int64_t)1 << 24;     // views * n limit
+constexpr size_t kNoAllocScratchBytes = 256 + 8 * (size_t)(kNoAllocMaxGaussianViews / kEmitPart);   // 128.25 KiB
+
+static __device__ __align__(256) unsigned char g_emit_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_scratch_mutex;
+static void* g_scratch_ptr[256];          // device address per CUDA device ordinal (nullptr: not set up)
+
+static ags_status scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return AGS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_emit_scratch) != cudaSuccess || !p) return AGS_ERR_CUDA;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return AGS_OK;
+}
+
+}  // namespace ags
+
+extern "C" int64_t ags_emit_pairs_noalloc_max_gaussians(void) { return ags::kNoAllocMaxGaussianViews; }
+
+extern "C" ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t n, int32_t views,
+                                             const ags_camera* cams, const uint32_t* order, uint64_t* keys,
+                                             uint32_t* vals, int64_t capacity, int64_t* d_num_pairs,
+                                             int64_t* d_status, void* stream) {
+  using namespace ags;
+  if (!proj || !d_num_pairs || !d_status || n < 0 || capacity < 0 || capacity > AGS_MAX_PAIRS)
+    return AGS_ERR_INVALID_ARG;
+  CamBatch cb;
+  ags_status s = build_cams(cams, views, &cb);
+  if (s != AGS_OK) return s;
+  const int64_t total = n * (int64_t)views;
+  if (total > kNoAllocMaxGaussianViews) return AGS_ERR_INVALID_ARG;   // beyond the static scratch
+  cudaStream_t st = (cudaStream_t)stream;
+  void* ws = nullptr;
+  s = scratch_address(&ws);
+  if (s != AGS_OK) return s;
+  if (total == 0) return launch_status(cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st));
+  if (!proj->rect || !proj->depth || (capacity > 0 && (!keys || !vals))) return AGS_ERR_INVALID_ARG;
+  const size_t parts = emit_parts(total);
+  const uint32_t tiles_per_view = (uint32_t)cb.c[0].gx * (uint32_t)cb.c[0].gy;
+  if ((uint64_t)tiles_per_view * (uint64_t)views >= (1ull << 32)) return AGS_ERR_INVALID_ARG;
+  // the array keeps the previous call's contents: clear the counter and look-back flags
   cudaError_t e = cudaMemsetAsync(ws, 0, 256 + 8 * parts, st);
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
