@@ -197,7 +197,7 @@ size_t ags_sort_workspace_bytes(int64_t capacity);
 
 /* Stable LSD radix sort of (keys, vals) by key bits [begin_bit, end_bit)
  * (Sec. 2.1 sorting stage): one global-histogram pass, then one single-pass
- * ("onesweep") scatter per digit of `digit_bits` (4..8) bits, with warp-level
+ * ("onesweep") scatter per digit of `digit_bits` (4..9) bits, with warp-level
  * match/ballot ranking and decoupled look-back between blocks.  The count is
  * read on the device from *d_num_pairs (clamped to capacity < AGS_MAX_PAIRS).
  * Keys already stably ordered by their bits below begin_bit stay so ordered

@@ -137,7 +137,7 @@ class Oracle:
         L = ctypes.CDLL(path)
         L.oracle_preprocess.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, _P, _P]
         L.oracle_preprocess.restype = None
-        L.oracle_tile_lists.argtypes = [ctypes.c_int64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
+        L.oracle_tile_lists.argtypes = [ctypes.c_int64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]
         L.oracle_tile_lists.restype = ctypes.c_int64
         L.oracle_rasterize.argtypes = [ctypes.c_int64, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                        _P, _P, _P, _P, _P, _P]
@@ -165,14 +165,17 @@ class Oracle:
                                  ctypes.byref(par), _ptr(dbl), _ptr(irec))
         return dbl, irec
 
-    def tile_lists(self, dbl, irec, width: int, height: int):
-        """(tile_start[num_tiles+1] int64, ids[num_pairs] int32) in (tile, depth, id) order."""
+    def tile_lists(self, dbl, irec, width: int, height: int, tile_mask=None):
+        """(tile_start[num_tiles+1] int64, ids[num_pairs] int32) in (tile, depth, id) order.
+
+        tile_mask (optional, [num_tiles]) builds the lists of the selected tiles only."""
         n = dbl.shape[0]
         nt = ((width + TILE - 1) // TILE) * ((height + TILE - 1) // TILE)
         ts = np.zeros(nt + 1, dtype=np.int64)
-        total = self.L.oracle_tile_lists(n, _ptr(dbl), _ptr(irec), width, height, _ptr(ts), None)
+        mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
+        total = self.L.oracle_tile_lists(n, _ptr(dbl), _ptr(irec), width, height, _ptr(mask), _ptr(ts), None)
         ids = np.zeros(max(total, 1), dtype=np.int32)
-        self.L.oracle_tile_lists(n, _ptr(dbl), _ptr(irec), width, height, _ptr(ts), _ptr(ids))
+        self.L.oracle_tile_lists(n, _ptr(dbl), _ptr(irec), width, height, _ptr(mask), _ptr(ts), _ptr(ids))
         return ts, ids[:total]
 
     def rasterize(self, dbl, tile_start, ids, width: int, height: int, par: OcParams, tile_mask=None,
@@ -195,7 +198,7 @@ class Oracle:
                want_state: bool = False) -> dict:
         """Full forward: preprocess, tile lists, blend."""
         dbl, irec = self.preprocess(scene, cam, par)
-        ts, ids = self.tile_lists(dbl, irec, cam["width"], cam["height"])
+        ts, ids = self.tile_lists(dbl, irec, cam["width"], cam["height"], tile_mask)
         out = self.rasterize(dbl, ts, ids, cam["width"], cam["height"], par, tile_mask, want_max_T, want_state)
         out.update(dbl=dbl, irec=irec, tile_start=ts, ids=ids)
         return out

@@ -421,9 +421,11 @@ static int cmp_pair(const void* a, const void* b) {
   return (x->id > y->id) - (x->id < y->id);
 }
 
-/* tile_start has num_tiles+1 entries; returns the number of pairs. */
+/* tile_start has num_tiles+1 entries; returns the number of pairs.  tile_mask
+ * (nullable, [num_tiles]) restricts the lists to the selected tiles (the
+ * others stay empty), so large scenes can be checked on a sample of tiles. */
 int64_t oracle_tile_lists(int64_t n, const double* dbl, const int32_t* irec, int32_t width,
-                          int32_t height, int64_t* tile_start, int32_t* ids) {
+                          int32_t height, const uint8_t* tile_mask, int64_t* tile_start, int32_t* ids) {
   int gx = (width + OC_TILE - 1) / OC_TILE, gy = (height + OC_TILE - 1) / OC_TILE;
   int64_t nt = (int64_t)gx * gy;
   int64_t* cnt = (int64_t*)calloc(nt, sizeof(int64_t));
@@ -431,7 +433,10 @@ int64_t oracle_tile_lists(int64_t n, const double* dbl, const int32_t* irec, int
     const int32_t* r = irec + i * OC_NI;
     if (r[I_TOUCHED] <= 0) continue;
     for (int ty = r[I_Y0]; ty < r[I_Y1]; ty++)
-      for (int tx = r[I_X0]; tx < r[I_X1]; tx++) cnt[(int64_t)ty * gx + tx]++;
+      for (int tx = r[I_X0]; tx < r[I_X1]; tx++) {
+        int64_t t = (int64_t)ty * gx + tx;
+        if (!tile_mask || tile_mask[t]) cnt[t]++;
+      }
   }
   tile_start[0] = 0;
   for (int64_t t = 0; t < nt; t++) tile_start[t + 1] = tile_start[t] + cnt[t];
@@ -446,6 +451,7 @@ int64_t oracle_tile_lists(int64_t n, const double* dbl, const int32_t* irec, int
       for (int ty = r[I_Y0]; ty < r[I_Y1]; ty++)
         for (int tx = r[I_X0]; tx < r[I_X1]; tx++) {
           int64_t t = (int64_t)ty * gx + tx;
+          if (tile_mask && !tile_mask[t]) continue;
           oc_pair* p = &pairs[tile_start[t] + cnt[t]++];
           p->depth = d;
           p->id = (int32_t)i;

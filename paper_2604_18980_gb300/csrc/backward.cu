@@ -7,8 +7,11 @@
 // T_j = T_{j+1} / (1 - alpha_j), and keeps R, the colour behind pair j
 // (background included): R <- c_j alpha_j + (1 - alpha_j) R.  Then
 //   dL/dalpha_j = T_j sum_ch g_ch (c_j,ch - R_ch),   dL/dc_j = alpha_j T_j g.
-// Per-splat gradients (u, v, A, B, C, opacity, r, g, b) are reduced across the
-// warp before one atomic add per warp.
+// Per-splat gradients (u, v, conic, opacity, r, g, b) are reduced across the
+// warp before one atomic add per warp.  The conic gradient is accumulated in
+// the splat's eigenframe (pixel offsets rotated onto its axes): in Cartesian
+// components the minor-axis part of a long thin splat would be lost to fp32
+// cancellation against the far larger major-axis terms.
 //
 // Preprocess adjoint: one thread per Gaussian, summing over views; it
 // recomputes the projection with the forward's code and applies the chain
@@ -22,7 +25,7 @@
 
 namespace ags {
 
-constexpr int kGradStride = 9;   // u v A B C opacity r g b
+constexpr int kGradStride = 9;   // u v | conic gradient in the eigenframe (aa, ab, bb) | opacity r g b
 
 __global__ void __launch_bounds__(kRasterThreads)
 raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
@@ -32,6 +35,7 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
   __shared__ float4 s_a[kRasterThreads];    // u v a2 b2
   __shared__ float4 s_b[kRasterThreads];    // c2 l2s r g
   __shared__ float4 s_o[kRasterThreads];    // A B C opacity (original units, for the gradients)
+  __shared__ float2 s_f[kRasterThreads];    // eigenframe (cos, sin) of the conic
   __shared__ float s_c[kRasterThreads];
   __shared__ uint32_t s_m[kRasterThreads];
   __shared__ uint32_t s_e[kRasterThreads];
@@ -86,6 +90,9 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
       s_b[tid] = st.b;
       s_c[tid] = st.c;
       s_o[tid] = make_float4(r0.z, r0.w, r1.x, r1.y);
+      float ca, sa;
+      conic_frame(r0.z, r0.w, r1.x, ca, sa);
+      s_f[tid] = make_float2(ca, sa);
       s_m[tid] = m;
       s_e[tid] = e;
     }
@@ -123,9 +130,11 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
             gO = dLda * (alpha / o.w);
             gu = -dLdp * (o.x * dx + o.y * dy);
             gv = -dLdp * (o.y * dx + o.z * dy);
-            gA = -0.5f * dLdp * dx * dx;
-            gB = -dLdp * dx * dy;
-            gC = -0.5f * dLdp * dy * dy;
+            const float2 f = s_f[j];
+            const float da = f.x * dx + f.y * dy, db = f.x * dy - f.y * dx;
+            gA = -0.5f * dLdp * da * da;
+            gB = -dLdp * da * db;
+            gC = -0.5f * dLdp * db * db;
           }
         }
       }
@@ -155,7 +164,8 @@ __global__ void __launch_bounds__(128)
 preprocess_backward_kernel(const float* __restrict__ mean, const float* __restrict__ lsc, const float* __restrict__ quat,
                            const float* __restrict__ logit_in, const float* __restrict__ sh, int64_t n, int views,
                            const __grid_constant__ CamBatch cams, const __grid_constant__ DevParams P,
-                           const uint8_t* __restrict__ flags, const float* __restrict__ gsplat, GradOut out) {
+                           const uint8_t* __restrict__ flags, const float* __restrict__ gsplat,
+                           const float* __restrict__ conic_rec, GradOut out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int deg = P.sh_degree;
@@ -168,6 +178,8 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
   float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
   float gsh[16][3];
   for (int k = 0; k < 16; k++) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+  Frame F;
+  make_frame(ls, q, logit, F);
 
   for (int view = 0; view < views; view++) {
     const int64_t e = (int64_t)view * n + i;
@@ -178,7 +190,7 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
     const float gcol[3] = {(fl & 1) ? 0.f : G[6], (fl & 2) ? 0.f : G[7], (fl & 4) ? 0.f : G[8]};
     const DevCam& C = cams.c[view];
     Proj pj;
-    if (!project_geometry(C, m, ls, q, logit, pj)) continue;
+    if (!project_view(C, m, F, pj)) continue;
 
     // colour: rgb_ch = sum_k sh[k][ch] Y_k(dir) + 0.5
     float dx = m[0] - C.campos[0], dy = m[1] - C.campos[1], dz = m[2] - C.campos[2];
@@ -203,14 +215,26 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
     gm[2] += (gd2 - dot * dir[2]) * il;
 
     // opacity
-    glogit += gO * pj.opac * (1.f - pj.opac);
+    glogit += gO * F.opac * (1.f - F.opac);
 
-    // conic (A, B, C) = (c', -b, a') / det of the dilated covariance (a', b, c')
-    const float ad = pj.a + 0.3f, cd = pj.c + 0.3f, b = pj.b;
-    const float id = 1.f / pj.det, id2 = id * id;
-    const float ga = (-cd * cd * gA + b * cd * gB - b * b * gC) * id2;
-    const float gbb = (2.f * b * cd * gA - (pj.det + 2.f * b * b) * gB + 2.f * ad * b * gC) * id2;
-    const float gc = (-b * b * gA + b * ad * gB - ad * ad * gC) * id2;
+    // conic M = Sigma^-1 of the dilated covariance: dL/dSigma = -M (dL/dM) M,
+    // evaluated in the eigenframe (e_a minor axis, e_b major axis) where
+    // M = diag(1/lambda_min, 1/lambda_max) and dL/dM = (gA gB/2; gB/2 gC)
+    // as accumulated by the blend adjoint, then rotated back.
+    const float4 c0 = __ldg(reinterpret_cast<const float4*>(conic_rec + (size_t)e * kSplatFloats));
+    const float cC = conic_rec[(size_t)e * kSplatFloats + 4];
+    float ca, sa;
+    conic_frame(c0.z, c0.w, cC, ca, sa);
+    const float ad = pj.a + 0.3f, cd = pj.c + 0.3f;
+    const float half = 0.5f * (ad - cd);
+    const float lmax = 0.5f * (ad + cd) + sqrtf(half * half + pj.b * pj.b);
+    const float ma = lmax / pj.det, mb = 1.f / lmax;               // 1/lambda_min, 1/lambda_max
+    const float eaa = -ma * ma * gA, eab = -ma * mb * 0.5f * gB, ebb = -mb * mb * gC;
+    // Cartesian dL/d(a, b, c) of Sigma = R E R^T with R = (e_a e_b)
+    const float ga = ca * ca * eaa - 2.f * ca * sa * eab + sa * sa * ebb;
+    const float g12 = ca * sa * eaa + (ca * ca - sa * sa) * eab - ca * sa * ebb;
+    const float gc = sa * sa * eaa + 2.f * ca * sa * eab + ca * ca * ebb;
+    const float gbb = 2.f * g12;
     // a = |v0|^2, b = v0.v1, c = |v1|^2
     float gV[6];
     for (int k = 0; k < 3; k++) {
@@ -223,18 +247,18 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
     for (int k = 0; k < 3; k++) {
       float gs = 0.f;
       for (int r = 0; r < 2; r++) {
-        float wm = pj.Tm[r * 3 + 0] * pj.Rq[k] + pj.Tm[r * 3 + 1] * pj.Rq[3 + k] + pj.Tm[r * 3 + 2] * pj.Rq[6 + k];
+        float wm = pj.Tm[r * 3 + 0] * F.Rq[k] + pj.Tm[r * 3 + 1] * F.Rq[3 + k] + pj.Tm[r * 3 + 2] * F.Rq[6 + k];
         gs += gV[r * 3 + k] * wm;
-        float gw = gV[r * 3 + k] * pj.s[k];
+        float gw = gV[r * 3 + k] * F.s[k];
         for (int j = 0; j < 3; j++) {
-          gT[r * 3 + j] += gw * pj.Rq[j * 3 + k];
+          gT[r * 3 + j] += gw * F.Rq[j * 3 + k];
           gR[j * 3 + k] += pj.Tm[r * 3 + j] * gw;
         }
       }
-      gls[k] += gs * pj.s[k];
+      gls[k] += gs * F.s[k];
     }
     // rotation matrix -> normalised quaternion (w, x, y, z)
-    const float w = pj.qn[0], x = pj.qn[1], y = pj.qn[2], z = pj.qn[3];
+    const float w = F.qn[0], x = F.qn[1], y = F.qn[2], z = F.qn[3];
     float gw_ = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
     float gx_ = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] -
                        2.f * x * gR[8]);
@@ -243,10 +267,10 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
     float gz_ = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] +
                        x * gR[6] + y * gR[7]);
     float qd = gw_ * w + gx_ * x + gy_ * y + gz_ * z;
-    gq[0] += (gw_ - qd * w) * pj.qinv;
-    gq[1] += (gx_ - qd * x) * pj.qinv;
-    gq[2] += (gy_ - qd * y) * pj.qinv;
-    gq[3] += (gz_ - qd * z) * pj.qinv;
+    gq[0] += (gw_ - qd * w) * F.qinv;
+    gq[1] += (gx_ - qd * x) * F.qinv;
+    gq[2] += (gy_ - qd * y) * F.qinv;
+    gq[3] += (gz_ - qd * z) * F.qinv;
 
     // T = J W: row 0 = fx/tz (W0 - ctx W2), row 1 = fy/tz (W1 - cty W2)
     float gt[3] = {0.f, 0.f, 0.f};
@@ -321,6 +345,6 @@ extern "C" ags_status ags_rasterize_backward(const ags_gaussians* g, const ags_c
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   GradOut go{g_mean, g_log_scale, g_quat, g_opacity_logit, g_sh};
   preprocess_backward_kernel<<<(unsigned)((g->n + 127) / 128), 128, 0, st>>>(
-      g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh, g->n, views, cb, dp, proj->flags, gs, go);
+      g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh, g->n, views, cb, dp, proj->flags, gs, proj->splat, go);
   return launch_status(cudaGetLastError());
 }

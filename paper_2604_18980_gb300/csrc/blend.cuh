@@ -112,6 +112,14 @@ __device__ __forceinline__ float splat_q(const Staged& s, float px, float py, fl
   return splat_qy(s, P, Bx, dy);
 }
 
+// Eigenframe of a conic (A B; B C): e_a = (ca, sa) maximises the quadratic
+// form (the splat's minor axis), e_b = (-sa, ca).  Shared by the blend adjoint
+// and the preprocess adjoint so both use the same frame.
+__device__ __forceinline__ void conic_frame(float A, float B, float C, float& ca, float& sa) {
+  const float th = 0.5f * atan2f(2.f * B, A - C);
+  sincosf(th, &sa, &ca);
+}
+
 __device__ __forceinline__ float fast_exp2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

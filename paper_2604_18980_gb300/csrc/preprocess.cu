@@ -6,9 +6,9 @@
 // test), Sec. 3.4 (T_up from a depth look-up table).
 //
 // One thread per Gaussian, looping over all views of the batch: the
-// structure-of-arrays parameters are read once (coalesced) whatever the number
-// of views, and the 48 SH floats only once, when the first view in which the
-// Gaussian survives and touches a tile needs its colour.  Outputs per view and
+// structure-of-arrays geometry is read once (coalesced) whatever the number of
+// views; the 48 SH floats are read only for views in which the Gaussian
+// survives and touches a tile (from DRAM the first time, then from cache).  Outputs per view and
 // survivor: a 48-byte splat record (three 16-byte stores), depth, the tile
 // rectangle (one 8-byte store), the tile count, a flag byte and the depth key.
 #include "project.cuh"
@@ -48,7 +48,10 @@ __device__ __forceinline__ void tile_span(float lo, float hi, int len, int& t0, 
   t1 = ((int)phi >> 4) + 1;
 }
 
-__global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, int views,
+// kCacheSH: keep the 48 SH coefficients in registers after the first view that
+// needs them (multi-view batches); otherwise re-read them through the caches.
+template <bool kCacheSH>
+__global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn in, int64_t n, int views,
                                                          const __grid_constant__ CamBatch cams,
                                                          const __grid_constant__ DevParams P, PreOut out,
                                                          int64_t* status) {
@@ -73,14 +76,16 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, in
     return;
   }
   const int nc = (P.sh_degree + 1) * (P.sh_degree + 1);
-  float sh[16][3];            // loaded on the first view that needs a colour
+  Frame F;                    // scales, rotation, R S and opacity: once for all views
+  make_frame(ls, q, logit, F);
+  float shc[kCacheSH ? 16 : 1][3];
   bool sh_loaded = false;
 
   for (int view = 0; view < views; view++) {
     const DevCam& C = cams.c[view];
     const int64_t e = (int64_t)view * n + i;
     Proj pj;
-    if (!project_geometry(C, m, ls, q, logit, pj)) {
+    if (!project_view(C, m, F, pj)) {
       write_culled(out, e);
       continue;
     }
@@ -92,8 +97,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, in
       const float tup = P.lut[bin];
       if (!(tup > 0.f)) { write_culled(out, e); continue; }
       th = P.K / (tup * 6.2831853f * sqrtf(pj.det)) + P.tau;
-      if (th > pj.opac) { write_culled(out, e); continue; }
-      rf = ceilf(sqrtf(pj.lam1) * fminf(3.f, sqrtf(2.f * logf(pj.opac / th))));
+      if (th > F.opac) { write_culled(out, e); continue; }
+      rf = ceilf(sqrtf(pj.lam1) * fminf(3.f, sqrtf(2.f * logf(F.opac / th))));
     } else {
       rf = ceilf(3.f * sqrtf(pj.lam1));
     }
@@ -105,24 +110,33 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, in
     const uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
     if (touched == 0u) { write_culled(out, e); continue; }
 
-    // colour: SH at the world-space direction from the camera centre
-    if (!sh_loaded) {
-#pragma unroll
-      for (int k = 0; k < 16; k++)
-#pragma unroll
-        for (int ch = 0; ch < 3; ch++) sh[k][ch] = k < nc ? __ldg(in.sh + (int64_t)(k * 3 + ch) * n + i) : 0.f;
-      sh_loaded = true;
-    }
+    // colour: SH at the world-space direction from the camera centre (the
+    // coefficients come from DRAM for the first view that needs them and from
+    // the caches for the others)
     const float dx = m[0] - C.campos[0], dy = m[1] - C.campos[1], dz = m[2] - C.campos[2];
     const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
     float Y[16];
     sh_basis(P.sh_degree, dx * il, dy * il, dz * il, Y);
     float rgb[3] = {0.5f, 0.5f, 0.5f};
+    if (kCacheSH) {
+      if (!sh_loaded) {
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-      if (k < nc) {
+        for (int k = 0; k < (kCacheSH ? 16 : 1); k++)
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(sh[k][ch], Y[k], rgb[ch]);
+          for (int ch = 0; ch < 3; ch++) shc[k][ch] = k < nc ? __ldg(in.sh + (int64_t)(k * 3 + ch) * n + i) : 0.f;
+        sh_loaded = true;
+      }
+#pragma unroll
+      for (int k = 0; k < (kCacheSH ? 16 : 1); k++)
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(shc[k][ch], Y[k], rgb[ch]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        if (k < nc) {
+#pragma unroll
+          for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(__ldg(in.sh + (int64_t)(k * 3 + ch) * n + i), Y[k], rgb[ch]);
+        }
       }
     }
     uint8_t flags = (uint8_t)pj.fclamp;
@@ -139,7 +153,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreIn in, int64_t n, in
     }
     float4* sp = reinterpret_cast<float4*>(out.splat + e * kSplatFloats);
     sp[0] = make_float4(pj.u, pj.v, pj.A, pj.B);
-    sp[1] = make_float4(pj.C, pj.opac, rgb[0], rgb[1]);
+    sp[1] = make_float4(pj.C, F.opac, rgb[0], rgb[1]);
     sp[2] = make_float4(rgb[2], th, pj.a + 0.3f, pj.c + 0.3f);
     out.depth[e] = pj.t[2];
     reinterpret_cast<uint2*>(out.rect)[e] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16),
@@ -171,7 +185,7 @@ extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* c
   if (((uintptr_t)out->splat & 15u) || ((uintptr_t)out->rect & 7u)) return AGS_ERR_INVALID_ARG;
   PreIn in{g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
   PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags, out->depth_key};
-  preprocess_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, g->n, views, cb, dp, po,
-                                                                                      d_status);
+  auto kern = views > 1 ? preprocess_kernel<true> : preprocess_kernel<false>;
+  kern<<<(unsigned)((g->n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, g->n, views, cb, dp, po, d_status);
   return launch_status(cudaGetLastError());
 }

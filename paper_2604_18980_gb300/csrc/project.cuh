@@ -109,16 +109,39 @@ __device__ __forceinline__ float dot3_plus(float a0, float b0, float a1, float b
   return __fadd_rn(s, __fadd_rn(e, t));
 }
 
+// View-independent quantities of one Gaussian.
+struct Frame {
+  float s[3];          // exp(log_scale)
+  float qn[4];         // normalised quaternion
+  float qinv;          // 1 / |q|
+  float Rq[9];         // rotation matrix
+  float M[9];          // Rq S
+  float opac;          // sigmoid(logit)
+};
+
+__device__ __forceinline__ void make_frame(const float ls[3], const float q[4], float logit, Frame& F) {
+#pragma unroll
+  for (int k = 0; k < 3; k++) F.s[k] = expf(ls[k]);
+  const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  F.qinv = rsqrtf(qq);
+  const float w = q[0] * F.qinv, x = q[1] * F.qinv, y = q[2] * F.qinv, z = q[3] * F.qinv;
+  F.qn[0] = w; F.qn[1] = x; F.qn[2] = y; F.qn[3] = z;
+  F.Rq[0] = 1.f - 2.f * (y * y + z * z); F.Rq[1] = 2.f * (x * y - w * z);       F.Rq[2] = 2.f * (x * z + w * y);
+  F.Rq[3] = 2.f * (x * y + w * z);       F.Rq[4] = 1.f - 2.f * (x * x + z * z); F.Rq[5] = 2.f * (y * z - w * x);
+  F.Rq[6] = 2.f * (x * z - w * y);       F.Rq[7] = 2.f * (y * z + w * x);       F.Rq[8] = 1.f - 2.f * (x * x + y * y);
+#pragma unroll
+  for (int r = 0; r < 3; r++)
+#pragma unroll
+    for (int k = 0; k < 3; k++) F.M[r * 3 + k] = F.Rq[r * 3 + k] * F.s[k];
+  F.opac = 1.0f / (1.0f + expf(-logit));
+}
+
 // Everything the forward computes for one Gaussian in one view.
 struct Proj {
   float t[3];          // view-space mean
   float iz;            // 1 / t_z
   float ctx, cty;      // x/z and y/z after the frustum clamp
   int fclamp;          // bit3 x clamped, bit4 y clamped
-  float s[3];          // exp(log_scale)
-  float qn[4];         // normalised quaternion
-  float qinv;          // 1 / |q|
-  float Rq[9];         // rotation matrix
   float Tm[6];         // T = J W (2x3)
   float V[6];          // V = T Rq S (2x3)
   float a, b, c;       // V V^T (undilated)
@@ -126,13 +149,11 @@ struct Proj {
   float A, B, C;       // conic
   float lam1;          // largest eigenvalue of the dilated covariance
   float u, v;          // 2D mean
-  float opac;          // sigmoid(logit)
 };
 
-// Projection of the geometry of Gaussian (m, ls, q, logit) for camera C.
-// Returns false when the Gaussian is culled (near plane or degenerate).
-__device__ __forceinline__ bool project_geometry(const DevCam& C, const float m[3], const float ls[3],
-                                                 const float q[4], float logit, Proj& P) {
+// Projection of Gaussian (m, F) for camera C.  Returns false when the
+// Gaussian is culled (near plane or degenerate).
+__device__ __forceinline__ bool project_view(const DevCam& C, const float m[3], const Frame& F, Proj& P) {
   // view transform t = R m + t_cam (compensated: depth keys and the near-plane
   // test see the correctly rounded value up to an ulp)
 #pragma unroll
@@ -140,7 +161,7 @@ __device__ __forceinline__ bool project_geometry(const DevCam& C, const float m[
     P.t[r] = dot3_plus(C.R[r * 3 + 0], m[0], C.R[r * 3 + 1], m[1], C.R[r * 3 + 2], m[2], C.t[r]);
   if (!(P.t[2] > C.near_z)) return false;
   P.iz = 1.0f / P.t[2];
-  float txtz = P.t[0] * P.iz, tytz = P.t[1] * P.iz;
+  const float txtz = P.t[0] * P.iz, tytz = P.t[1] * P.iz;
   P.fclamp = 0;
   P.ctx = txtz;
   P.cty = tytz;
@@ -149,51 +170,39 @@ __device__ __forceinline__ bool project_geometry(const DevCam& C, const float m[
   if (tytz > C.limy) { P.cty = C.limy; P.fclamp |= 16; }
   else if (tytz < -C.limy) { P.cty = -C.limy; P.fclamp |= 16; }
 
-  // scales and rotation
-#pragma unroll
-  for (int k = 0; k < 3; k++) P.s[k] = expf(ls[k]);
-  float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-  P.qinv = rsqrtf(qq);
-  float w = q[0] * P.qinv, x = q[1] * P.qinv, y = q[2] * P.qinv, z = q[3] * P.qinv;
-  P.qn[0] = w; P.qn[1] = x; P.qn[2] = y; P.qn[3] = z;
-  P.Rq[0] = 1.f - 2.f * (y * y + z * z); P.Rq[1] = 2.f * (x * y - w * z);       P.Rq[2] = 2.f * (x * z + w * y);
-  P.Rq[3] = 2.f * (x * y + w * z);       P.Rq[4] = 1.f - 2.f * (x * x + z * z); P.Rq[5] = 2.f * (y * z - w * x);
-  P.Rq[6] = 2.f * (x * z - w * y);       P.Rq[7] = 2.f * (y * z + w * x);       P.Rq[8] = 1.f - 2.f * (x * x + y * y);
-
   // T = J W: row 0 = fx/tz (W0 - ctx W2), row 1 = fy/tz (W1 - cty W2)
-  float jx = C.fx * P.iz, jy = C.fy * P.iz;
+  const float jx = C.fx * P.iz, jy = C.fy * P.iz;
 #pragma unroll
   for (int k = 0; k < 3; k++) {
     P.Tm[k] = jx * fmaf(-P.ctx, C.R[6 + k], C.R[k]);
     P.Tm[3 + k] = jy * fmaf(-P.cty, C.R[6 + k], C.R[3 + k]);
   }
-  // V = T Rq S
+  // V = T (Rq S)
 #pragma unroll
   for (int r = 0; r < 2; r++)
 #pragma unroll
     for (int k = 0; k < 3; k++)
-      P.V[r * 3 + k] = (P.Tm[r * 3 + 0] * P.Rq[0 * 3 + k] + P.Tm[r * 3 + 1] * P.Rq[1 * 3 + k] +
-                        P.Tm[r * 3 + 2] * P.Rq[2 * 3 + k]) * P.s[k];
+      P.V[r * 3 + k] = P.Tm[r * 3 + 0] * F.M[0 * 3 + k] + P.Tm[r * 3 + 1] * F.M[1 * 3 + k] +
+                       P.Tm[r * 3 + 2] * F.M[2 * 3 + k];
   const float* v0 = P.V;
   const float* v1 = P.V + 3;
   P.a = v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2];
   P.b = v0[0] * v1[0] + v0[1] * v1[1] + v0[2] * v1[2];
   P.c = v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2];
-  float cx_ = v0[1] * v1[2] - v0[2] * v1[1];
-  float cy_ = v0[2] * v1[0] - v0[0] * v1[2];
-  float cz_ = v0[0] * v1[1] - v0[1] * v1[0];
-  float ad = P.a + 0.3f, cd = P.c + 0.3f;
+  const float cx_ = v0[1] * v1[2] - v0[2] * v1[1];
+  const float cy_ = v0[2] * v1[0] - v0[0] * v1[2];
+  const float cz_ = v0[0] * v1[1] - v0[1] * v1[0];
+  const float ad = P.a + 0.3f, cd = P.c + 0.3f;
   P.det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + 0.3f * (P.a + P.c) + 0.09f;
   if (!(P.det > 0.f)) return false;
-  float id = 1.0f / P.det;
+  const float id = 1.0f / P.det;
   P.A = cd * id;
   P.B = -P.b * id;
   P.C = ad * id;
-  float half = 0.5f * (ad - cd);
+  const float half = 0.5f * (ad - cd);
   P.lam1 = 0.5f * (ad + cd) + sqrtf(fmaxf(0.1f, half * half + P.b * P.b));
   P.u = fmaf(C.fx, P.t[0] * P.iz, C.cx);
   P.v = fmaf(C.fy, P.t[1] * P.iz, C.cy);
-  P.opac = 1.0f / (1.0f + expf(-logit));
   return true;
 }
 

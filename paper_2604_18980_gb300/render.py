@@ -33,7 +33,7 @@ def key_end_bit(views: int, tiles: int) -> int:
     return 32 + max(1, int(views * tiles - 1).bit_length())
 
 
-def digit_plan(bits: int, max_digit: int = 8) -> tuple:
+def digit_plan(bits: int, max_digit: int = 9) -> tuple:
     """(passes, digit_bits) covering `bits` key bits with the fewest passes."""
     passes = max(1, -(-bits // max_digit))
     return passes, max(4, -(-bits // passes))
@@ -43,7 +43,7 @@ class Renderer:
     """Buffers and launch sequence for rendering `scene` into `cams` (one batch)."""
 
     def __init__(self, scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_PLAIN, K: float = 0.0, lut=None,
-                 sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 8,
+                 sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 9,
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
                  presort: bool = True):
         self.scene = scene
@@ -131,6 +131,7 @@ class Renderer:
         return max(1, -(-self.end_bit // self.digit_bits)), self.digit_bits
 
     def launches_per_forward(self) -> int:
+        # preprocess, emit, (histogram, digit scan, passes, ranges fix-up), blend
         n = 1 + 1 + (2 + self.sort_plan()[0] + 1) + 1
         if self.presort:
             n += 2 + digit_plan(self.dsort_end, self.digit_bits)[0]
@@ -172,6 +173,23 @@ class Renderer:
         self.sort()
         self.rasterize(max_T)
         return self.image
+
+    def capture(self) -> "torch.cuda.CUDAGraph":
+        """Capture one whole forward (every stage, all views) in a CUDA graph.
+
+        Replaying the graph re-renders from the current contents of the scene
+        tensors and writes the same output buffers; the pair capacity must
+        cover the pairs of every replay (an overflow is reported in the status
+        block, as for an eager forward)."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):          # warm-up outside the capture
+            self.forward()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.forward()
+        return graph
 
     def backward(self, dL_dimage: torch.Tensor, grads: dict | None = None) -> dict:
         if self.ws_bwd is None:

@@ -78,11 +78,13 @@ def gpu_pairs(r):
     return keys, vals
 
 
-def compare_lists(r, orc_outs):
+def compare_lists(r, orc_outs, tile_masks=None):
     """Per-tile sorted id lists: bit-exact outside edge-flagged Gaussians and depth near-ties.
 
-    orc_outs: one oracle render dict per view.  Returns the number of tiles whose
-    order differs only by near-ties."""
+    orc_outs: one oracle render dict per view (None to skip a view).
+    tile_masks: optional per-view boolean masks of the tiles to compare (the
+    oracle built lists for those tiles only).  Returns (number of tiles whose
+    order differs only by near-ties, per-view edge tiles)."""
     keys, vals = gpu_pairs(r)
     n, T = r.n, r.T
     g_tile = (keys >> np.uint64(32)).astype(np.int64)
@@ -92,10 +94,15 @@ def compare_lists(r, orc_outs):
     tie_tiles = 0
     edge_tiles = []
     for v, oo in enumerate(orc_outs):
+        if oo is None:
+            edge_tiles.append([])
+            continue
         edge = oo["irec"][:, oracle.I_EDGE] != 0
         ts, ids = oo["tile_start"], oo["ids"]
         o_tile = np.repeat(np.arange(T), np.diff(ts))
         sel = (g_tile // T) == v
+        if tile_masks is not None:
+            sel &= np.asarray(tile_masks[v], dtype=bool)[np.clip(g_tile - v * T, 0, T - 1)]
         gt, gi, gd = g_tile[sel] - v * T, vals[sel] - v * n, g_depth_bits[sel]
         # tiles whose lists differ only through edge-class Gaussians (excluded from image parity)
         eo = set(zip(o_tile[edge[ids]].tolist(), ids[edge[ids]].tolist()))
@@ -129,7 +136,17 @@ def compare_lists(r, orc_outs):
     return tie_tiles, edge_tiles
 
 
-def compare_image(img_gpu, oo, tol=IMG_TOL, edge_tiles=()):
+def tile_pixel_mask(tile_mask, W, H):
+    """Pixel mask [H][W] of the selected tiles."""
+    gx = (W + 15) // 16
+    m = np.zeros((H, W), dtype=bool)
+    for t in np.nonzero(tile_mask)[0]:
+        ty, tx = divmod(int(t), gx)
+        m[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    return m
+
+
+def compare_image(img_gpu, oo, tol=IMG_TOL, edge_tiles=(), pixel_mask=None):
     """Image parity: max-abs <= tol outside edge-flagged pixels; PSNR over all pixels.
 
     Edge pixels: a near-threshold alpha decision (oracle flip budget > 0), or a
@@ -145,10 +162,17 @@ def compare_image(img_gpu, oo, tol=IMG_TOL, edge_tiles=()):
         tile_px[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
     flagged_budget = flagged & ~tile_px
     flagged = flagged | tile_px
+    if pixel_mask is not None:
+        o = o[:, pixel_mask]
+        g = g[:, pixel_mask]
+        flagged, flagged_budget = flagged[pixel_mask], flagged_budget[pixel_mask]
+        budget = oo["budget"][pixel_mask]
+    else:
+        budget = oo["budget"]
     err = np.abs(g - o).max(axis=0)
     ok = err[~flagged]
     assert ok.size == 0 or ok.max() <= tol, "max abs error %.3g outside edge pixels" % ok.max()
-    assert np.all(err[flagged_budget] <= tol + oo["budget"][flagged_budget]), "edge pixel beyond its flip bound"
+    assert np.all(err[flagged_budget] <= tol + budget[flagged_budget]), "edge pixel beyond its flip bound"
     mse = float(np.mean((g - o) ** 2))
     psnr = math.inf if mse == 0 else 10 * math.log10(1.0 / mse)
     assert psnr >= PSNR_MIN, psnr

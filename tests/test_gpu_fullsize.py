@@ -1,0 +1,95 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark times: every Gaussian's features and rectangle, and the pair lists
+and pixels of a seeded sample of tiles per view (the oracle builds and blends
+those tiles only)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import compare_features, compare_image, compare_lists, oracle_params, tile_pixel_mask
+from paper_2604_18980_gb300 import binding as B
+from paper_2604_18980_gb300 import calibrate as C
+from paper_2604_18980_gb300 import render as R
+from paper_2604_18980_gb300 import synth
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2604_18980_gb300 import build
+    build.build()
+    B.lib()
+
+
+def _tile_sample(T, k, seed):
+    rng = np.random.default_rng(seed)
+    m = np.zeros(T, dtype=bool)
+    m[rng.choice(T, size=min(k, T), replace=False)] = True
+    return m
+
+
+def _check_views(scene_np, r, views, mode, K, lut, ntiles=96, seed=0):
+    outs, masks = [], []
+    for v in range(r.V):
+        if v not in views:
+            outs.append(None)
+            masks.append(None)
+            continue
+        cam = r.cams[v]
+        par = oracle_params(cam, mode, K, lut)
+        m = _tile_sample(r.T, ntiles, seed + v)
+        oo = oracle.render(scene_np, cam, par, tile_mask=m)
+        compare_features(r, oo, v)
+        outs.append(oo)
+        masks.append(m)
+    _, edge_tiles = compare_lists(r, outs, [m if m is not None else np.zeros(r.T, bool) for m in masks])
+    for v in views:
+        pm = tile_pixel_mask(masks[v], r.W, r.H)
+        compare_image(r.image[v].cpu().numpy(), outs[v], edge_tiles=edge_tiles[v], pixel_mask=pm)
+
+
+def test_c2_bench_configuration():
+    """1M Gaussians, 1920x1080, all 10 poses in one batch, AdaGScale at the calibrated K."""
+    name = "c2_clusters1m_1080p"
+    scene, cams, _ = synth.workload(name)
+    wp = C.load_params(name)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"])
+    r.forward()
+    r.check()
+    _check_views(scene, r, (0, 3, 7), 1, wp["K"], wp["lut"])
+
+
+def test_c2_plain_full_frame():
+    """Plain 3-sigma at 1920x1080, one view, every tile."""
+    scene, cams, _ = synth.workload("c2_clusters1m_1080p", views=1)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, B.AGS_SCALE_PLAIN)
+    r.forward()
+    r.check()
+    _check_views(scene, r, (0,), 0, 0.0, None, ntiles=r.T)
+
+
+def test_c5_gradients_full_size():
+    """Forward + backward at 1M Gaussians, 1080p, AdaGScale pair selection fixed."""
+    name = "c2_clusters1m_1080p"
+    scene, cams, _ = synth.workload(name, views=1)
+    wp = C.load_params(name)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"])
+    r.forward()
+    rng = np.random.default_rng(11)
+    w = rng.normal(size=(3, r.H, r.W)).astype(np.float32)
+    g = r.backward(torch.from_numpy(w).cuda()[None])
+    r.check()
+    par = oracle_params(cams[0], 1, wp["K"], wp["lut"])
+    oo = oracle.render(scene, cams[0], par)
+    og = oracle.backward(scene, cams[0], par, oo["tile_start"], oo["ids"], w.astype(np.float64))
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        a = g[k].cpu().numpy().astype(np.float64).reshape(og[k].shape)
+        b = og[k]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel <= 1e-3, (k, rel)

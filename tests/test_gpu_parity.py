@@ -101,7 +101,8 @@ def test_capacity_overflow_is_reported_and_bounded():
 
 
 @pytest.mark.parametrize("count,bits,digit", [(1, 40, 8), (4095, 40, 8), (4097, 45, 8), (100003, 49, 8),
-                                              (250000, 52, 7), (77777, 40, 5)])
+                                              (250000, 52, 7), (77777, 40, 5), (2049, 41, 9), (300001, 49, 9),
+                                              (65536, 36, 9)])
 def test_sort_random_keys_stable(count, bits, digit):
     rng = np.random.default_rng(count)
     tile_bits = bits - 32
@@ -236,3 +237,40 @@ def test_sort_identity_values_flag():
     B.ags_check(st)
     vs = (va if alt else v).cpu().numpy()
     np.testing.assert_array_equal(vs, np.argsort(keys, kind="stable"))
+
+
+def test_cuda_graph_replay_matches_eager_and_follows_scene_updates():
+    scene, cams = _c1(n=6000, W=160, H=120, views=2)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, 1, 0.4)
+    eager = r.forward().clone()
+    r.check()
+    g = r.capture()
+    r.image.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(r.image, eager)
+    # the graph reads the scene buffers: an in-place update is rendered on replay
+    sc["opacity_logit"].add_(0.5)
+    sc["mean"][0].add_(0.01)
+    g.replay()
+    torch.cuda.synchronize()
+    replayed = r.image.clone()
+    r2 = R.Renderer(sc, cams, 1, 0.4, capacity=r.capacity)
+    assert torch.equal(replayed, r2.forward())
+    r.check()
+
+
+def test_autotuner_candidates_render_identically():
+    from paper_2604_18980_gb300 import autotune
+    scene, cams = _c1(n=8000, W=192, H=144, views=2)
+    sc = R.scene_to_device(scene)
+    imgs = []
+    for cand in autotune.CANDIDATES:
+        r = R.Renderer(sc, cams, 1, 0.3, **cand)
+        imgs.append(r.forward().clone())
+        r.check()
+    for im in imgs[1:]:
+        assert torch.equal(im, imgs[0])
+    best = autotune.tune(sc, cams, 1, 0.3, use_cache=False, warmup=1, reps=2)
+    assert best["digit_bits"] in (7, 8, 9) and len(best["table"]) == len(autotune.CANDIDATES)

@@ -57,7 +57,7 @@ def test_workspace_sizes(lib):
     assert B.ags_emit_workspace_bytes(0, 1) == 256
     assert B.ags_emit_workspace_bytes(1024, 1) == 256 + 8
     assert B.ags_emit_workspace_bytes(1025, 1) == 256 + 16
-    assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 256 * 4 + 2 * 256 * 4
+    assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 512 * 4 + 2 * 512 * 4
     assert B.ags_backward_workspace_bytes(10, 2) == 10 * 2 * 9 * 4
 
 
@@ -89,7 +89,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     # sort: bad digit width, capacity beyond the limit, missing workspace
     npairs = ctypes.c_void_p(16)
     alt = ctypes.c_int32(0)
-    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 9, 0, None, 0, ctypes.byref(alt), st, None, 0,
+    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 10, 0, None, 0, ctypes.byref(alt), st, None, 0,
                       None) == 1
     assert L.ags_sort(None, None, None, None, npairs, B.AGS_MAX_PAIRS, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st,
                       None, 0, None) == 1
