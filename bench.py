@@ -240,6 +240,7 @@ def run_ours(args, world, rank, local):
     ada.forward()
     ada.check()
     evals_per_step = int(ada.stats[0].item())
+    blends_per_step = int(ada.stats[1].item())
     ada_pairs = ada.pairs()
     passes = ada.sort_plan()[0]
     launches_per_step = ada.launches_per_forward()
@@ -399,6 +400,7 @@ def run_ours(args, world, rank, local):
         "stage_ms": stage_ms,
         "stage_hbm": stage_frac,
         "roofline": roof,
+        "blend_work": {"evaluations_per_frame": evals_per_step / V, "blended_per_frame": blends_per_step / V},
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }

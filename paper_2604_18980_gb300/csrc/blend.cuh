@@ -11,11 +11,13 @@
 // Each CTA blends one 16x16 tile with eight warps; warp w owns the 4x8 pixel
 // block rows 4*(w>>1).., columns 8*(w&1)...  For every staged splat the loading
 // thread also computes which of the eight blocks can hold a pixel with
-// alpha >= tau: the bounding box of the ellipse p >= ln(tau/opacity), i.e.
-// half-widths sqrt(2 ln(opacity/tau) Sigma_xx) and sqrt(2 ln(opacity/tau) Sigma_yy)
-// of the dilated covariance, widened by a slack far above fp32 rounding.  A
-// warp skips a splat whose bit is clear: those pixels would have rejected it
-// with alpha < tau anyway, so the result is unchanged.
+// alpha >= tau: its ellipse p >= ln(tau/opacity) must reach the block's
+// rectangle of pixel centres -- a bounding-box test (half-widths
+// sqrt(2 ln(opacity/tau) Sigma_xx), sqrt(2 ln(opacity/tau) Sigma_yy)) and then
+// the exact minimum of the quadratic form over the rectangle, both with a slack
+// far above fp32 rounding.  A warp skips a splat whose bit is clear: those
+// pixels would have rejected it with alpha < tau anyway, so the result is
+// unchanged.
 #pragma once
 
 #include <cmath>
@@ -50,6 +52,26 @@ struct Staged {
   float c;       // b
 };
 
+// Minimum over the rectangle [xl,xh] x [yl,yh] of A x^2 + 2 B x y + C y^2 for a
+// positive-definite (A B; B C): zero when the rectangle holds the origin,
+// otherwise attained on an edge, where the 1-D minimiser is clamped to it.
+__device__ __forceinline__ float rect_min_quad(float A, float B, float C, float xl, float xh, float yl, float yh) {
+  if (xl <= 0.f && xh >= 0.f && yl <= 0.f && yh >= 0.f) return 0.f;
+  const float iA = 1.f / A, iC = 1.f / C;
+  float m = 3.402823466e38f;
+  const float xs[2] = {xl, xh}, ys[2] = {yl, yh};
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const float x = xs[k];
+    const float y = fminf(fmaxf(-B * x * iC, yl), yh);
+    m = fminf(m, fmaf(A * x, x, fmaf(2.f * B * x, y, C * y * y)));
+    const float y2 = ys[k];
+    const float x2 = fminf(fmaxf(-B * y2 * iA, xl), xh);
+    m = fminf(m, fmaf(A * x2, x2, fmaf(2.f * B * x2, y2, C * y2 * y2)));
+  }
+  return m;
+}
+
 // Splat record (48 bytes): u v A B | C opacity r g | b Th Sxx Syy.
 // Mask bit w: the ellipse can reach block w of the tile, blocks being
 // BW x BH pixels in row-major order of (16/BW) x (16/BH).
@@ -70,10 +92,16 @@ __device__ __forceinline__ void stage_splat(const float4* rec, int tx0, int ty0,
     const float lx = r0.x - hx - (float)tx0, ux = r0.x + hx - (float)tx0;   // tile-relative
     const float ly = r0.y - hy - (float)ty0, uy = r0.y + hy - (float)ty0;
     constexpr int NBX = kTile / BW, NBY = kTile / BH;
+    const float cu = r0.x - (float)tx0, cv = r0.y - (float)ty0;    // tile-relative centre
+    const float lim = r2n * 1.0001f;
 #pragma unroll
     for (int w = 0; w < NBX * NBY; w++) {
       const float cx0 = (float)(BW * (w % NBX)), ry0 = (float)(BH * (w / NBX));
-      if (ux >= cx0 && lx <= cx0 + (float)(BW - 1) && uy >= ry0 && ly <= ry0 + (float)(BH - 1)) mask |= 1u << w;
+      // bounding box first, then the exact ellipse-rectangle test on the pixel centres' rectangle
+      if (ux >= cx0 && lx <= cx0 + (float)(BW - 1) && uy >= ry0 && ly <= ry0 + (float)(BH - 1) &&
+          rect_min_quad(r0.z, r0.w, r1.x, cx0 - cu, cx0 + (float)(BW - 1) - cu, ry0 - cv,
+                        ry0 + (float)(BH - 1) - cv) <= lim)
+        mask |= 1u << w;
     }
   }
 }
