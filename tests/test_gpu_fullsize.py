@@ -93,3 +93,39 @@ def test_c5_gradients_full_size():
         b = og[k]
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         assert rel <= 1e-3, (k, rel)
+
+
+def test_c3_city_full_size():
+    """8M Gaussians on a 1 km city, 4608x3456, all 8 poses in one batch, AdaGScale at the calibrated K."""
+    name = "c3_city8m_4608x3456"
+    scene, cams, _ = synth.workload(name)
+    wp = C.load_params(name)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"])
+    r.forward()
+    r.check()
+    _check_views(scene, r, (0, 6), 1, wp["K"], wp["lut"], ntiles=64, seed=30)
+
+
+def test_c3_city_plain_street_view():
+    name = "c3_city8m_4608x3456"
+    scene, cams, _ = synth.workload(name, views=1)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, B.AGS_SCALE_PLAIN)
+    r.forward()
+    r.check()
+    _check_views(scene, r, (0,), 0, 0.0, None, ntiles=64, seed=31)
+
+
+def test_c4_vr_batch_full_size():
+    """4M city Gaussians, 8 eye pairs = 16 views of 3660x3200 in one launch per stage."""
+    name = "c4_city4m_vr16x3660x3200"
+    scene, cams, _ = synth.workload(name)
+    assert len(cams) == 16
+    wp = C.load_params(name)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"])
+    g = r.capture()
+    g.replay()
+    r.check()
+    _check_views(scene, r, (0, 1, 15), 1, wp["K"], wp["lut"], ntiles=48, seed=40)
