@@ -27,18 +27,80 @@ namespace ags {
 
 constexpr int kGradStride = 9;   // u v | conic gradient in the eigenframe (aa, ab, bb) | opacity r g b
 
-__global__ void __launch_bounds__(kRasterThreads)
+// Sums v[0..8] over the warp with a transposed butterfly (16 shuffles for all
+// nine sums instead of 45): after it, lane 2c (c < 9) holds the total of v[c].
+__device__ __forceinline__ float warp_reduce9(const float v[9], int lane) {
+  float a[16];
+#pragma unroll
+  for (int k = 0; k < 9; k++) a[k] = v[k];
+#pragma unroll
+  for (int k = 9; k < 16; k++) a[k] = 0.f;
+#pragma unroll
+  for (int o = 16, h = 8; o >= 2; o >>= 1, h >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < h; k++) {
+      const float send = hi ? a[k] : a[k + h];
+      const float keep = hi ? a[k + h] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
+// One pixel's step of the reverse walk over a splat it may have blended:
+// recovers T before the splat, updates the colour behind it, and adds the
+// pixel's share of the splat's nine gradients to acc.  Returns whether the
+// splat was blended here (the forward's accept test, bit for bit).
+__device__ __forceinline__ bool pixel_adjoint(const Staged& s, float cbl, const float4& o, const float2& f,
+                                              const BlendConst& bc, float dx, float dy, float P, float Bx, float ga,
+                                              float gb, float gc, float& T, float& Ra, float& Rb, float& Rc,
+                                              float acc[9]) {
+  const float q = splat_qy(s, P, Bx, dy);
+  if (!splat_accept(q, s.b.y)) return false;
+  const float raw = __fmul_rn(bc.tau, fast_exp2(q));
+  const float alpha = fminf(bc.alpha_max, raw);
+  const float om = 1.f - alpha;
+  T = __fdividef(T, om);                         // transmittance before this splat
+  const float w = alpha * T;
+  acc[6] += w * ga;
+  acc[7] += w * gb;
+  acc[8] += w * gc;
+  const float dLda = T * (ga * (s.b.z - Ra) + gb * (s.b.w - Rb) + gc * (cbl - Rc));
+  Ra = s.b.z * alpha + om * Ra;
+  Rb = s.b.w * alpha + om * Rb;
+  Rc = cbl * alpha + om * Rc;
+  if (!(raw > bc.alpha_max)) {                   // the clamp cuts the gradient through alpha
+    const float dLdp = dLda * alpha;
+    acc[5] += dLdp * o.w;                        // d alpha / d opacity = alpha / opacity
+    acc[0] -= dLdp * (o.x * dx + o.y * dy);
+    acc[1] -= dLdp * (o.y * dx + o.z * dy);
+    const float da = f.x * dx + f.y * dy, db = f.x * dy - f.y * dx;
+    acc[2] -= 0.5f * dLdp * da * da;
+    acc[3] -= dLdp * da * db;
+    acc[4] -= 0.5f * dLdp * db * db;
+  }
+  return true;
+}
+
+// Blend adjoint, laid out like the forward: 128 threads per tile, warps of
+// 8x8 pixels, two pixels per thread (rows y and y+4), per-warp lists of the
+// splats whose alpha >= tau ellipse reaches the warp's block, walked from the
+// back.  Each pixel starts from its final T and its last blended position.
+__global__ void __launch_bounds__(128)
 raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
                        const uint2* __restrict__ ranges, int W, int H, int gx, int tiles_per_view, BlendConst bc,
                        const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
                        const float* __restrict__ dL_dimage, float* __restrict__ gsplat) {
-  __shared__ float4 s_a[kRasterThreads];    // u v a2 b2
-  __shared__ float4 s_b[kRasterThreads];    // c2 l2s r g
-  __shared__ float4 s_o[kRasterThreads];    // A B C opacity (original units, for the gradients)
-  __shared__ float2 s_f[kRasterThreads];    // eigenframe (cos, sin) of the conic
-  __shared__ float s_c[kRasterThreads];
-  __shared__ uint32_t s_m[kRasterThreads];
-  __shared__ uint32_t s_e[kRasterThreads];
+  constexpr int kB = 128;
+  __shared__ float4 s_a[kB];      // u v a2 b2
+  __shared__ float4 s_b[kB];      // c2 base r g
+  __shared__ float4 s_o[kB];      // A B C 1/opacity
+  __shared__ float2 s_f[kB];      // eigenframe (cos, sin) of the conic
+  __shared__ float s_c[kB];       // b
+  __shared__ uint32_t s_m[kB];
+  __shared__ uint32_t s_e[kB];
+  __shared__ uint16_t s_list[4][kB];
   __shared__ uint32_t s_maxlast;
 
   const int tile = blockIdx.x;
@@ -46,37 +108,43 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
   const int lt = tile - view * tiles_per_view;
   const int ty = lt / gx, tx = lt - ty * gx;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int lx, ly;
-  tile_pixel(tid, lx, ly);
-  const int px = tx * kTile + lx, py = ty * kTile + ly;
-  const bool inside = px < W && py < H;
-  const float fpx = (float)px, fpy = (float)py;
+  const int px = tx * kTile + 8 * (warp & 1) + (lane & 7);
+  const int py0 = ty * kTile + 8 * (warp >> 1) + (lane >> 3);
+  const int py1 = py0 + 4;
+  const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
+  const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
   const uint2 rg = __ldg(ranges + tile);
   const uint32_t start = rg.x, end = rg.y;
-
   const size_t hw = (size_t)W * H;
-  float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  uint32_t last = 0;
-  if (inside) {
-    const size_t op = (size_t)view * hw + (size_t)py * W + px;
-    T = final_T[op];
-    last = n_contrib[op];
-    const size_t o = (size_t)view * 3 * hw + (size_t)py * W + px;
-    g0 = dL_dimage[o];
-    g1 = dL_dimage[o + hw];
-    g2 = dL_dimage[o + 2 * hw];
+
+  float T0 = 1.f, T1 = 1.f, g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f;
+  uint32_t last0 = 0, last1 = 0;
+  if (in0) {
+    const size_t op = (size_t)view * hw + (size_t)py0 * W + px;
+    T0 = final_T[op];
+    last0 = n_contrib[op];
+    const size_t o = (size_t)view * 3 * hw + (size_t)py0 * W + px;
+    g00 = dL_dimage[o]; g01 = dL_dimage[o + hw]; g02 = dL_dimage[o + 2 * hw];
   }
-  float R0 = bc.bg[0], R1 = bc.bg[1], R2 = bc.bg[2];
+  if (in1) {
+    const size_t op = (size_t)view * hw + (size_t)py1 * W + px;
+    T1 = final_T[op];
+    last1 = n_contrib[op];
+    const size_t o = (size_t)view * 3 * hw + (size_t)py1 * W + px;
+    g10 = dL_dimage[o]; g11 = dL_dimage[o + hw]; g12 = dL_dimage[o + 2 * hw];
+  }
+  float R00 = bc.bg[0], R01 = bc.bg[1], R02 = bc.bg[2];
+  float R10 = bc.bg[0], R11 = bc.bg[1], R12 = bc.bg[2];
   if (tid == 0) s_maxlast = 0u;
   __syncthreads();
-  if (last) atomicMax(&s_maxlast, last);
+  const uint32_t mylast = max(last0, last1);
+  if (mylast) atomicMax(&s_maxlast, mylast);
   __syncthreads();
   const uint32_t maxlast = min(s_maxlast, end - start);
-  // the warp walks only the positions below its own largest "last"
-  const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
+  const uint32_t wlast = __reduce_max_sync(0xffffffffu, mylast);   // this warp's entries end here
 
-  for (int32_t bend = (int32_t)maxlast; bend > 0; bend -= kRasterThreads) {
-    const int32_t bbeg = max(0, bend - kRasterThreads);
+  for (int32_t bend = (int32_t)maxlast; bend > 0; bend -= kB) {
+    const int32_t bbeg = max(0, bend - kB);
     const int nb = bend - bbeg;
     __syncthreads();
     if (tid < nb) {
@@ -84,12 +152,12 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
       const float4* rec = splat + (size_t)e * 3;
       Staged st;
       uint32_t m;
-      stage_splat<8, 4>(rec, tx * kTile, ty * kTile, bc.l2tau, st, m);
+      stage_splat<8, 8>(rec, tx * kTile, ty * kTile, bc.l2tau, st, m);
       const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
       s_a[tid] = st.a;
       s_b[tid] = st.b;
       s_c[tid] = st.c;
-      s_o[tid] = make_float4(r0.z, r0.w, r1.x, r1.y);
+      s_o[tid] = make_float4(r0.z, r0.w, r1.x, __frcp_rn(r1.y));
       float ca, sa;
       conic_frame(r0.z, r0.w, r1.x, ca, sa);
       s_f[tid] = make_float2(ca, sa);
@@ -97,56 +165,41 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
       s_e[tid] = e;
     }
     __syncthreads();
+    // this warp's entries below its last blended position, in depth order
     const int jtop = min(nb, (int)wlast - bbeg);
-    for (int j = jtop - 1; j >= 0; j--) {
-      if (!((s_m[j] >> warp) & 1u)) continue;         // warp-uniform skip, as in the forward
-      const uint32_t pos = (uint32_t)(bbeg + j);       // 0-based position in the tile list
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kB / 32; k++) {
+      const int j = k * 32 + lane;
+      const bool hit = j < jtop && ((s_m[j] >> warp) & 1u);
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) s_list[warp][cnt + __popc(bal & lanemask_lt())] = (uint16_t)j;
+      cnt += __popc(bal);
+    }
+    __syncwarp();
+    for (int t = cnt - 1; t >= 0; t--) {                // back to front
+      const int j = s_list[warp][t];
+      const uint32_t pos = (uint32_t)(bbeg + j);         // 0-based position in the tile list
       Staged s;
       s.a = s_a[j];
       s.b = s_b[j];
       const float cbl = s_c[j];
-      float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, gO = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
+      const float4 o = s_o[j];
+      const float2 f = s_f[j];
+      const float dx = __fsub_rn(s.a.x, fpx);
+      float P, Bx;
+      splat_qx(s, dx, P, Bx);
+      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool contrib = false;
-      if (pos < last) {
-        float dx, dy;
-        const float q = splat_q(s, fpx, fpy, dx, dy);
-        if (splat_accept(q, s.b.y)) {
-          const float raw = __fmul_rn(bc.tau, fast_exp2(q));
-          const float alpha = fminf(bc.alpha_max, raw);
-          contrib = true;
-          const float4 o = s_o[j];
-          const float om = 1.f - alpha;
-          T = T / om;
-          const float w = alpha * T;
-          gr = w * g0;
-          gg = w * g1;
-          gb = w * g2;
-          const float dLda = T * (g0 * (s.b.z - R0) + g1 * (s.b.w - R1) + g2 * (cbl - R2));
-          R0 = s.b.z * alpha + om * R0;
-          R1 = s.b.w * alpha + om * R1;
-          R2 = cbl * alpha + om * R2;
-          if (!(raw > bc.alpha_max)) {
-            const float dLdp = dLda * alpha;
-            gO = dLda * (alpha / o.w);
-            gu = -dLdp * (o.x * dx + o.y * dy);
-            gv = -dLdp * (o.y * dx + o.z * dy);
-            const float2 f = s_f[j];
-            const float da = f.x * dx + f.y * dy, db = f.x * dy - f.y * dx;
-            gA = -0.5f * dLdp * da * da;
-            gB = -dLdp * da * db;
-            gC = -0.5f * dLdp * db * db;
-          }
-        }
-      }
+      if (pos < last0)
+        contrib |= pixel_adjoint(s, cbl, o, f, bc, dx, __fsub_rn(s.a.y, fpy0), P, Bx, g00, g01, g02, T0, R00, R01,
+                                 R02, acc);
+      if (pos < last1)
+        contrib |= pixel_adjoint(s, cbl, o, f, bc, dx, __fsub_rn(s.a.y, fpy1), P, Bx, g10, g11, g12, T1, R10, R11,
+                                 R12, acc);
       if (__any_sync(0xffffffffu, contrib)) {
-        gu = warp_sum(gu); gv = warp_sum(gv); gA = warp_sum(gA); gB = warp_sum(gB); gC = warp_sum(gC);
-        gO = warp_sum(gO); gr = warp_sum(gr); gg = warp_sum(gg); gb = warp_sum(gb);
-        if (lane == 0) {
-          float* G = gsplat + (size_t)s_e[j] * kGradStride;
-          atomicAdd(G + 0, gu); atomicAdd(G + 1, gv); atomicAdd(G + 2, gA); atomicAdd(G + 3, gB);
-          atomicAdd(G + 4, gC); atomicAdd(G + 5, gO); atomicAdd(G + 6, gr); atomicAdd(G + 7, gg);
-          atomicAdd(G + 8, gb);
-        }
+        const float sum = warp_reduce9(acc, lane);
+        if ((lane & 1) == 0 && lane < 18) atomicAdd(gsplat + (size_t)s_e[j] * kGradStride + (lane >> 1), sum);
       }
     }
   }
@@ -160,7 +213,10 @@ struct GradOut {
   float* sh;
 };
 
-__global__ void __launch_bounds__(128)
+// kOneView: a single view needs no per-Gaussian SH accumulator; its SH
+// gradient is written as soon as it is known, which frees 48 registers.
+template <bool kOneView>
+__global__ void __launch_bounds__(128, kOneView ? 4 : 3)
 preprocess_backward_kernel(const float* __restrict__ mean, const float* __restrict__ lsc, const float* __restrict__ quat,
                            const float* __restrict__ logit_in, const float* __restrict__ sh, int64_t n, int views,
                            const __grid_constant__ CamBatch cams, const __grid_constant__ DevParams P,
@@ -171,23 +227,47 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
   const int deg = P.sh_degree;
   const int nc = (deg + 1) * (deg + 1);
   float m[3], ls[3], q[4];
-  for (int k = 0; k < 3; k++) m[k] = mean[k * n + i];
-  for (int k = 0; k < 3; k++) ls[k] = lsc[k * n + i];
-  for (int k = 0; k < 4; k++) q[k] = quat[k * n + i];
-  const float logit = logit_in[i];
+  for (int k = 0; k < 3; k++) m[k] = __ldg(mean + k * n + i);
+  for (int k = 0; k < 3; k++) ls[k] = __ldg(lsc + k * n + i);
+  for (int k = 0; k < 4; k++) q[k] = __ldg(quat + k * n + i);
+  const float logit = __ldg(logit_in + i);
   float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
-  float gsh[16][3];
-  for (int k = 0; k < 16; k++) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+  float gsh[kOneView ? 1 : 16][3];
+  if constexpr (!kOneView)
+    for (int k = 0; k < 16; k++) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+  bool sh_written = false;
+  // One view: every load of a visible Gaussian is issued up front, so that
+  // they are all in flight together instead of one dependent phase at a time.
+  float shv[kOneView ? 48 : 1], Gv[kOneView ? 9 : 1];
+  float4 cv0 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float cvC = 0.f;
+  uint8_t fl0 = 0;
+  if constexpr (kOneView) {
+    fl0 = __ldg(flags + i);
+    if (!(fl0 & kFlagCulled)) {
+#pragma unroll
+      for (int k = 0; k < 16; k++)
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) shv[k * 3 + ch] = k < nc ? __ldg(sh + (int64_t)(k * 3 + ch) * n + i) : 0.f;
+#pragma unroll
+      for (int k = 0; k < kGradStride; k++) Gv[k] = __ldg(gsplat + (size_t)i * kGradStride + k);
+      cv0 = __ldg(reinterpret_cast<const float4*>(conic_rec + (size_t)i * kSplatFloats));
+      cvC = __ldg(conic_rec + (size_t)i * kSplatFloats + 4);
+    }
+  }
   Frame F;
   make_frame(ls, q, logit, F);
 
   for (int view = 0; view < views; view++) {
     const int64_t e = (int64_t)view * n + i;
-    const uint8_t fl = flags[e];
+    const uint8_t fl = kOneView ? fl0 : __ldg(flags + e);
     if (fl & kFlagCulled) continue;
     const float* G = gsplat + (size_t)e * kGradStride;
-    const float gu = G[0], gv = G[1], gA = G[2], gB = G[3], gC = G[4], gO = G[5];
-    const float gcol[3] = {(fl & 1) ? 0.f : G[6], (fl & 2) ? 0.f : G[7], (fl & 4) ? 0.f : G[8]};
+    float Gl[kGradStride];
+#pragma unroll
+    for (int k = 0; k < kGradStride; k++) Gl[k] = kOneView ? Gv[k] : __ldg(G + k);
+    const float gu = Gl[0], gv = Gl[1], gA = Gl[2], gB = Gl[3], gC = Gl[4], gO = Gl[5];
+    const float gcol[3] = {(fl & 1) ? 0.f : Gl[6], (fl & 2) ? 0.f : Gl[7], (fl & 4) ? 0.f : Gl[8]};
     const DevCam& C = cams.c[view];
     Proj pj;
     if (!project_view(C, m, F, pj)) continue;
@@ -199,14 +279,26 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
     float Y[16];
     sh_basis(deg, dir[0], dir[1], dir[2], Y);
     float wk[16];
-    for (int k = 0; k < nc; k++) {
-      float s0 = sh[(int64_t)(k * 3 + 0) * n + i], s1 = sh[(int64_t)(k * 3 + 1) * n + i],
-            s2 = sh[(int64_t)(k * 3 + 2) * n + i];
-      wk[k] = gcol[0] * s0 + gcol[1] * s1 + gcol[2] * s2;
-      gsh[k][0] += gcol[0] * Y[k];
-      gsh[k][1] += gcol[1] * Y[k];
-      gsh[k][2] += gcol[2] * Y[k];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      wk[k] = 0.f;
+      if (k < nc) {
+        const float s0 = kOneView ? shv[k * 3 + 0] : __ldg(sh + (int64_t)(k * 3 + 0) * n + i),
+                    s1 = kOneView ? shv[k * 3 + 1] : __ldg(sh + (int64_t)(k * 3 + 1) * n + i),
+                    s2 = kOneView ? shv[k * 3 + 2] : __ldg(sh + (int64_t)(k * 3 + 2) * n + i);
+        wk[k] = gcol[0] * s0 + gcol[1] * s1 + gcol[2] * s2;
+        if constexpr (kOneView) {
+          out.sh[(int64_t)(k * 3 + 0) * n + i] = gcol[0] * Y[k];
+          out.sh[(int64_t)(k * 3 + 1) * n + i] = gcol[1] * Y[k];
+          out.sh[(int64_t)(k * 3 + 2) * n + i] = gcol[2] * Y[k];
+        } else {
+          gsh[k][0] += gcol[0] * Y[k];
+          gsh[k][1] += gcol[1] * Y[k];
+          gsh[k][2] += gcol[2] * Y[k];
+        }
+      }
     }
+    sh_written = true;
     float gd0, gd1, gd2;
     sh_basis_grad(deg, dir[0], dir[1], dir[2], wk, gd0, gd1, gd2);
     float dot = gd0 * dir[0] + gd1 * dir[1] + gd2 * dir[2];
@@ -221,8 +313,8 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
     // evaluated in the eigenframe (e_a minor axis, e_b major axis) where
     // M = diag(1/lambda_min, 1/lambda_max) and dL/dM = (gA gB/2; gB/2 gC)
     // as accumulated by the blend adjoint, then rotated back.
-    const float4 c0 = __ldg(reinterpret_cast<const float4*>(conic_rec + (size_t)e * kSplatFloats));
-    const float cC = conic_rec[(size_t)e * kSplatFloats + 4];
+    const float4 c0 = kOneView ? cv0 : __ldg(reinterpret_cast<const float4*>(conic_rec + (size_t)e * kSplatFloats));
+    const float cC = kOneView ? cvC : __ldg(conic_rec + (size_t)e * kSplatFloats + 4);
     float ca, sa;
     conic_frame(c0.z, c0.w, cC, ca, sa);
     const float ad = pj.a + 0.3f, cd = pj.c + 0.3f;
@@ -301,8 +393,14 @@ preprocess_backward_kernel(const float* __restrict__ mean, const float* __restri
   for (int k = 0; k < 3; k++) out.ls[k * n + i] = gls[k];
   for (int k = 0; k < 4; k++) out.quat[k * n + i] = gq[k];
   out.logit[i] = glogit;
-  for (int k = 0; k < nc; k++)
-    for (int ch = 0; ch < 3; ch++) out.sh[(int64_t)(k * 3 + ch) * n + i] = gsh[k][ch];
+  if constexpr (kOneView) {
+    if (!sh_written)
+      for (int k = 0; k < nc; k++)
+        for (int ch = 0; ch < 3; ch++) out.sh[(int64_t)(k * 3 + ch) * n + i] = 0.f;
+  } else {
+    for (int k = 0; k < nc; k++)
+      for (int ch = 0; ch < 3; ch++) out.sh[(int64_t)(k * 3 + ch) * n + i] = gsh[k][ch];
+  }
 }
 
 }  // namespace ags
@@ -338,13 +436,18 @@ extern "C" ags_status ags_rasterize_backward(const ags_gaussians* g, const ags_c
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   const int tiles_per_view = cb.c[0].gx * cb.c[0].gy;
   BlendConst bc = make_blend_const(dp);
-  raster_backward_kernel<<<(unsigned)(tiles_per_view * views), kRasterThreads, 0, st>>>(
+  raster_backward_kernel<<<(unsigned)(tiles_per_view * views), 128, 0, st>>>(
       reinterpret_cast<const float4*>(proj->splat), sorted_vals, reinterpret_cast<const uint2*>(ranges), cb.c[0].W,
       cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, final_T, n_contrib, dL_dimage, gs);
   e = cudaGetLastError();
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   GradOut go{g_mean, g_log_scale, g_quat, g_opacity_logit, g_sh};
-  preprocess_backward_kernel<<<(unsigned)((g->n + 127) / 128), 128, 0, st>>>(
-      g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh, g->n, views, cb, dp, proj->flags, gs, proj->splat, go);
+  const unsigned grid = (unsigned)((g->n + 127) / 128);
+  if (views == 1)
+    preprocess_backward_kernel<true><<<grid, 128, 0, st>>>(g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh,
+                                                           g->n, views, cb, dp, proj->flags, gs, proj->splat, go);
+  else
+    preprocess_backward_kernel<false><<<grid, 128, 0, st>>>(g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh,
+                                                            g->n, views, cb, dp, proj->flags, gs, proj->splat, go);
   return launch_status(cudaGetLastError());
 }
