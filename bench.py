@@ -218,7 +218,7 @@ def run_ours(args, world, rank, local):
     # launch parameters from the autotuner (untimed set-up; identical results for every candidate)
     from paper_2604_18980_gb300 import autotune
     tuned = autotune.tune(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"])
-    knobs = dict(digit_bits=tuned["digit_bits"], presort=tuned["presort"])
+    knobs = dict(digit_bits=tuned["digit_bits"], presort=tuned["presort"], pair_rank_or=tuned["pair_rank_or"])
     ada = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_stats=True, **knobs)
     plain = R.Renderer(sc, cams, B.AGS_SCALE_PLAIN, **knobs)
     stream = torch.cuda.current_stream()
@@ -396,7 +396,8 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
         "timing": "CUDA-graph replay of the whole forward per step; stage_ms from the same steps launched "
                   "eagerly with events between stages (eager %.3f ms/step)" % eager_ms,
-        "tuned": {"digit_bits": knobs["digit_bits"], "presort": knobs["presort"]},
+        "tuned": {"digit_bits": knobs["digit_bits"], "presort": knobs["presort"],
+                  "pair_rank_or": knobs["pair_rank_or"]},
         "stage_ms": stage_ms,
         "stage_hbm": stage_frac,
         "roofline": roof,
@@ -423,22 +424,29 @@ def stage_bytes(stage, r, passes):
     V, n, P = r.V, r.n, r.pairs()
     G = V * n
     live = int(((r.proj["flags"] & 0x80) == 0).sum().item())
+    kb = 4 if r.presort else 8          # pair key bytes: 32-bit tile keys after the depth pre-sort
     if stage == "sort":
-        # histogram read (8 B/pair), each digit pass reads and writes key+value (24 B/pair);
-        # the last pass also writes the tile ranges (8 B/tile, initialised and fixed up: 24 B/tile)
-        return P * 8 + passes * P * 24 + V * r.T * 24, "onesweep_kernel (+hist, ranges)"
+        # histogram read (kb B/pair); each digit pass reads key + value and writes
+        # them (2 (kb + 4) B/pair) except that the last pass writes no key; the
+        # last pass also writes the tile ranges (8 B/tile, initialised and fixed up: 24 B/tile)
+        return P * kb + passes * P * 2 * (kb + 4) - P * kb + V * r.T * 24, "onesweep_kernel (+hist, ranges)"
     if stage == "depth_sort":
         from paper_2604_18980_gb300.render import digit_plan
         dp = digit_plan(r.dsort_end, r.digit_bits)[0] if r.presort else 0
-        return G * 8 + dp * G * 24 - G * 4, "onesweep_kernel (depth keys, identity values)"
+        # 32-bit depth keys: histogram 4 B, each pass 16 B, minus the values the first
+        # pass does not read (identity) and the keys the last pass does not write
+        return (G * 4 + dp * G * 16 - G * 8) if dp else 0, "onesweep_kernel (depth keys, identity values)"
     if stage == "emit":
-        # order (4 B), rectangle (8 B) per Gaussian, depth (4 B) per survivor; 12 B per pair
-        return G * 12 + live * 4 + P * 12, "emit_kernel"
+        if r.presort:
+            # order (4 B) and rectangle (8 B) per Gaussian; 8 B per pair (tile key, value)
+            return G * 12 + P * 8, "emit_kernel"
+        # rectangle (8 B) per Gaussian, depth (4 B) per survivor; 12 B per pair
+        return G * 8 + live * 4 + P * 12, "emit_kernel"
     # preprocess: 44 B geometry per Gaussian and 192 B SH per Gaussian that survives
     # in some view, read once per batch; per view, survivors write 48 B splat + 4 depth
-    # + 8 rect + 4 count + 1 flag + 8 depth key = 73 B, culled Gaussians 21 B
+    # + 8 rect + 4 count + 1 flag + 4 depth key = 69 B, culled Gaussians 17 B
     any_live = int(((r.proj["flags"].view(V, n) & 0x80) == 0).any(0).sum().item())
-    return n * 44 + any_live * 192 + live * 73 + (G - live) * 21, "preprocess_kernel"
+    return n * 44 + any_live * 192 + live * 69 + (G - live) * 17, "preprocess_kernel"
 
 
 def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):

@@ -12,6 +12,12 @@
  *                           (Sec. 2.1, Sec. 3.3 "Gaussian-tile pair generation")
  *   ags_sort                stable LSD radix sort of the pairs (Sec. 2.1) and the
  *                           per-tile [start, end) ranges
+ *
+ * and the same tile lists by a shorter route: sort the Gaussians of every view
+ * by depth first (ags_sort32 of depth_key), emit 32-bit tile keys in that order
+ * (ags_emit_tile_pairs) and sort only those (ags_sort32) -- bit-identical
+ * lists with fewer, narrower digit passes.
+ *
  *   ags_rasterize           per-16x16-tile front-to-back alpha blending, Eq. 1
  *                           and Eq. 2, always with the original covariance and
  *                           tau (Sec. 3.3 "dual-size strategy")
@@ -113,10 +119,13 @@ typedef struct {
   uint32_t* tiles_touched;  /* [views*n] (x1-x0)*(y1-y0), nullable */
   uint8_t* flags;           /* [views*n] bit0-2 colour clamped at 0, bit3/bit4
                                EWA x/y frustum clamp, bit7 culled */
-  uint64_t* depth_key;      /* [views*n] (view << 32) | float_bits(depth), all
-                               ones for Gaussians without pairs; nullable.
-                               Sorting these first lets the pair sort skip the
-                               depth digits (see ags_emit_pairs `order`). */
+  uint32_t* depth_key;      /* [views*n] float_bits(depth) (depth > 0, so the
+                               bits order as the depths do), all ones for
+                               Gaussians without pairs; nullable.  A stable
+                               sort of these (ags_sort32) gives an emission
+                               order in which each view's Gaussians are in
+                               depth order (equal depths in index order); see
+                               ags_emit_tile_pairs. */
 } ags_projected;
 
 /* Device status block: int64_t[4] = {status code, detail, non-finite count, reserved}. */
@@ -165,6 +174,20 @@ ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32_t views,
                           int64_t* d_num_pairs, int64_t* d_status,
                           void* ws, size_t ws_bytes, void* stream);
 
+/* Pair emission with 32-bit tile keys (Sec. 2.1, Sec. 3.3): ags_emit_pairs
+ * with key = view * tiles_per_view + tile and no depth bits.  Pairs come out
+ * in the order of `order`; when `order` is the stable depth order (a sort of
+ * depth_key, see ags_projected), a stable sort of these keys (ags_sort32 over
+ * their bits) yields exactly the per-tile lists that sorting the 64-bit
+ * (tile | depth) keys of ags_emit_pairs yields: the tile, then the depth, then
+ * the Gaussian index.  `proj->depth` is not read.  Workspace: as
+ * ags_emit_pairs (ags_emit_workspace_bytes). */
+ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, int32_t views,
+                               const ags_camera* cams, const uint32_t* order,
+                               uint32_t* keys, uint32_t* vals, int64_t capacity,
+                               int64_t* d_num_pairs, int64_t* d_status,
+                               void* ws, size_t ws_bytes, void* stream);
+
 /* Largest views*n that ags_emit_pairs_noalloc accepts (2^24). */
 int64_t ags_emit_pairs_noalloc_max_gaussians(void);
 
@@ -193,7 +216,14 @@ ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t n, int32_t 
 /* Scratch bytes needed by ags_sort for up to `capacity` pairs. */
 size_t ags_sort_workspace_bytes(int64_t capacity);
 
-#define AGS_SORT_IDENTITY_VALUES 1   /* ags_sort flag: values are 0..count-1; `vals` is not read */
+#define AGS_SORT_IDENTITY_VALUES 1   /* sort flag: values are 0..count-1; `vals` is not read */
+#define AGS_SORT_DISCARD_KEYS 2      /* sort flag: the last digit pass writes no keys, so the
+                                        key buffer that would hold the result is left
+                                        unspecified (values and ranges only) */
+#define AGS_SORT_RANK_OR 4           /* sort flag: rank a warp's equal digits with shared-memory
+                                        atomic-OR peer masks instead of warp match; same result,
+                                        faster when a warp's keys mostly carry distinct digits
+                                        (tile keys in emission order) */
 
 /* Stable LSD radix sort of (keys, vals) by key bits [begin_bit, end_bit)
  * (Sec. 2.1 sorting stage): one global-histogram pass, then one single-pass
@@ -203,7 +233,8 @@ size_t ags_sort_workspace_bytes(int64_t capacity);
  * Keys already stably ordered by their bits below begin_bit stay so ordered
  * within equal [begin_bit, end_bit) fields: pairs emitted in depth order
  * need only the tile digits, with the same result as a sort of all bits.
- * flags: AGS_SORT_IDENTITY_VALUES.
+ * flags: AGS_SORT_IDENTITY_VALUES, AGS_SORT_DISCARD_KEYS, AGS_SORT_RANK_OR.  `keys` must be
+ * 16-byte aligned when a digit pass runs (read 16 bytes at a time).
  * The sorted result lands in (keys, vals) when the number of digit passes is
  * even and in (keys_alt, vals_alt) when it is odd; *result_in_alt (host)
  * reports which.  If `ranges` is non-null it then receives, for each of
@@ -214,6 +245,17 @@ ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t
                     int32_t end_bit, int32_t digit_bits, int32_t flags, uint32_t* ranges,
                     int64_t num_ranges, int32_t* result_in_alt, int64_t* d_status, void* ws,
                     size_t ws_bytes, void* stream);
+
+/* ags_sort for 32-bit keys (end_bit <= 32): the depth pre-sort of depth_key
+ * and the sort of the tile keys of ags_emit_tile_pairs.  Same arguments,
+ * workspace (ags_sort_workspace_bytes), flags and results; the range index of
+ * a key is the whole key.  `keys` must be 16-byte aligned when a digit pass
+ * runs (it is read 16 bytes at a time), as for ags_sort. */
+ags_status ags_sort32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                      const int64_t* d_num_pairs, int64_t capacity, int32_t begin_bit,
+                      int32_t end_bit, int32_t digit_bits, int32_t flags, uint32_t* ranges,
+                      int64_t num_ranges, int32_t* result_in_alt, int64_t* d_status, void* ws,
+                      size_t ws_bytes, void* stream);
 
 /* Blending (Eq. 1, Eq. 2; Sec. 3.3 dual size).  One CTA per 16x16 tile of
  * each view; per pixel, front to back over the tile's sorted pairs:

@@ -1,9 +1,10 @@
 """Autotuner for the launch parameters of a rendering workload.
 
 The knobs are the digit width of the radix sorts (7, 8 or 9 bits: fewer,
-wider passes against more contention and larger look-back tables) and
-whether the Gaussians are depth-sorted before emission (the pair sort then
-runs only the tile digits).  Every candidate renders the same frames through
+wider passes against more contention and larger look-back tables), whether
+the Gaussians are depth-sorted before emission (the pair sort then runs only
+the tile digits, on 32-bit keys) and how the pair sort ranks a warp's equal
+digits (warp match, or atomic-OR peer masks in shared memory).  Every candidate renders the same frames through
 the same kernels -- results are identical -- and the fastest one (CUDA-event
 time of a whole forward, after warm-up) is kept.  Results are cached in a JSON
 file keyed by GPU name and workload shape.
@@ -19,7 +20,8 @@ from . import binding as B
 from . import render as R
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
-CANDIDATES = [dict(digit_bits=d, presort=p) for p in (True, False) for d in (9, 8, 7)]
+CANDIDATES = [dict(digit_bits=d, presort=p, pair_rank_or=o) for p in (True, False) for o in (True, False)
+              for d in (9, 8, 7)]
 
 
 def workload_key(scene: dict, cams: list, scale_mode: int) -> str:
@@ -44,7 +46,7 @@ def _time_forward(r: R.Renderer, warmup: int, reps: int) -> float:
 
 def tune(scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_ADAGSCALE, K: float = 0.0, lut=None,
          warmup: int = 2, reps: int = 5, use_cache: bool = True, candidates=None) -> dict:
-    """Fastest configuration for this workload: {"digit_bits", "presort", "ms", "table"}."""
+    """Fastest configuration for this workload: {"digit_bits", "presort", "pair_rank_or", "ms", "table"}."""
     key = workload_key(scene, cams, scale_mode)
     cache = {}
     if use_cache and os.path.exists(CACHE):
@@ -63,7 +65,8 @@ def tune(scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_ADAGSCALE, K: fl
         table.append(dict(cand, ms=ms))
         del r
     best = min(table, key=lambda t: t["ms"])
-    out = dict(digit_bits=best["digit_bits"], presort=best["presort"], ms=best["ms"], table=table)
+    out = dict(digit_bits=best["digit_bits"], presort=best["presort"], pair_rank_or=best["pair_rank_or"],
+               ms=best["ms"], table=table)
     if use_cache:
         cache[key] = out
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)

@@ -68,11 +68,14 @@ EXPORTS = {
     "ags_preprocess": ([_P, _P, _I32, _P, _P, _P, _P], _I32),
     "ags_emit_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
     "ags_emit_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P], _I32),
+    "ags_emit_tile_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P], _I32),
     "ags_emit_pairs_noalloc_max_gaussians": ([], _I64),
     "ags_emit_pairs_noalloc": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P], _I32),
     "ags_sort_workspace_bytes": ([_I64], ctypes.c_size_t),
     "ags_sort": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _I32, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P],
                  _I32),
+    "ags_sort32": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _I32, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P],
+                   _I32),
     "ags_rasterize": ([_P, _I64, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "ags_calibrate_lut": ([_P, _P, _I64, _I32, _F, _P, _P], _I32),
     "ags_backward_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
@@ -222,6 +225,16 @@ def ags_emit_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, w
         "ags_emit_pairs")
 
 
+def ags_emit_tile_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, ws, order=None, stream=None):
+    """Pairs with 32-bit tile keys, emitted in `order` (normally the depth order)."""
+    pr = projected(proj)
+    cs = cameras(cams)
+    _ok(lib().ags_emit_tile_pairs(ctypes.byref(pr), int(n), len(cams), cs, ptr(order), ptr(keys), ptr(vals),
+                                  int(capacity), ptr(d_num_pairs), ptr(d_status), ptr(ws),
+                                  ws.numel() * ws.element_size() if ws is not None else 0, stream_handle(stream)),
+        "ags_emit_tile_pairs")
+
+
 def ags_emit_pairs_noalloc(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, order=None, stream=None):
     """ags_emit_pairs with the library's static scratch (for callers that cannot allocate)."""
     pr = projected(proj)
@@ -236,6 +249,8 @@ def ags_sort_workspace_bytes(capacity: int) -> int:
 
 
 AGS_SORT_IDENTITY_VALUES = 1
+AGS_SORT_DISCARD_KEYS = 2
+AGS_SORT_RANK_OR = 4
 
 
 def ags_sort(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit, digit_bits, ranges,
@@ -246,6 +261,17 @@ def ags_sort(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, e
                        int(begin_bit), int(end_bit), int(digit_bits), int(flags), ptr(ranges), int(num_ranges),
                        ctypes.byref(alt), ptr(d_status), ptr(ws), ws.numel() * ws.element_size(),
                        stream_handle(stream)), "ags_sort")
+    return bool(alt.value)
+
+
+def ags_sort32(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit, digit_bits, ranges,
+               num_ranges, d_status, ws, flags=0, stream=None) -> bool:
+    """ags_sort for 32-bit keys; returns True when the sorted result is in (keys_alt, vals_alt)."""
+    alt = ctypes.c_int32(0)
+    _ok(lib().ags_sort32(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt), ptr(d_num_pairs), int(capacity),
+                         int(begin_bit), int(end_bit), int(digit_bits), int(flags), ptr(ranges), int(num_ranges),
+                         ctypes.byref(alt), ptr(d_status), ptr(ws), ws.numel() * ws.element_size(),
+                         stream_handle(stream)), "ags_sort32")
     return bool(alt.value)
 
 

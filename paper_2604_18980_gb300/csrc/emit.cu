@@ -9,7 +9,9 @@
 // chunks of 256 consecutive pairs and stages them in shared memory, so stores
 // are coalesced whatever the per-Gaussian tile counts are.
 //
-//   key = ((view * tiles_per_view + tile) << 32) | float_bits(depth),  val = view * n + i
+//   64-bit keys: key = ((view * tiles_per_view + tile) << 32) | float_bits(depth)
+//   32-bit keys: key = view * tiles_per_view + tile (pairs emitted in depth order)
+//   val = view * n + i
 //
 // The look-back spins are bounded (globaltimer); on expiry the status block
 // records AGS_ERR_TIMEOUT and every store stays inside `capacity`.
@@ -29,9 +31,16 @@ constexpr uint64_t kAgg = 1ull << 62;
 constexpr uint64_t kInc = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 
+// Pair key of a tile: 64-bit keys append the depth bits, 32-bit keys are the tile alone.
+__device__ __forceinline__ void make_key(uint32_t tile, uint32_t dbits, uint64_t& k) {
+  k = ((uint64_t)tile << 32) | dbits;
+}
+__device__ __forceinline__ void make_key(uint32_t tile, uint32_t, uint32_t& k) { k = tile; }
+
+template <typename K>
 __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, const uint32_t* __restrict__ order,
-            int64_t total, uint32_t n, uint32_t tiles_per_view, uint32_t gx, uint64_t* __restrict__ keys,
+            int64_t total, uint32_t n, uint32_t tiles_per_view, uint32_t gx, K* __restrict__ keys,
             uint32_t* __restrict__ vals, int64_t capacity, int64_t* d_num_pairs, int64_t* status,
             uint64_t* part_status, uint32_t* counter, uint32_t num_parts) {
   __shared__ uint32_t s_base[kEmitPart];   // key high word of the rectangle's first tile
@@ -64,7 +73,7 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
       uint32_t view = e / n;
       s_base[li] = view * tiles_per_view + y0 * gx + x0;
       s_w[li] = w;
-      s_dbits[li] = c ? __float_as_uint(__ldg(depth + e)) : 0u;
+      if (sizeof(K) == 8) s_dbits[li] = c ? __float_as_uint(__ldg(depth + e)) : 0u;
       s_idx[li] = e;
     }
     s_off[li] = c;
@@ -145,7 +154,7 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
   //    lane generates 8 consecutive pairs (one binary search, then walking the
   //    rectangle row by row) into a warp-private staging row, and the warp
   //    writes the chunk out with coalesced stores.
-  __shared__ unsigned long long s_key[kEmitThreads / 32][32 * kEmitStride];
+  __shared__ K s_key[kEmitThreads / 32][32 * kEmitStride];
   __shared__ uint32_t s_val[kEmitThreads / 32][32 * kEmitStride];
   for (uint32_t w0 = (uint32_t)warp * kEmitChunk; w0 < agg; w0 += (kEmitThreads / 32) * kEmitChunk) {
     const uint32_t j0 = w0 + (uint32_t)lane * kEmitRun;
@@ -169,7 +178,7 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
           ry = 0;
         }
         const uint32_t tile = s_base[lo] + ry * gx + rx;
-        s_key[warp][lane * kEmitStride + k] = ((unsigned long long)tile << 32) | s_dbits[lo];
+        make_key(tile, sizeof(K) == 8 ? s_dbits[lo] : 0u, s_key[warp][lane * kEmitStride + k]);
         s_val[warp][lane * kEmitStride + k] = s_idx[lo];
         if (++rx == w) { rx = 0; ry++; }
       }
@@ -225,7 +234,36 @@ extern "C" ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
   uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
-  emit_kernel<<<(unsigned)parts, kEmitThreads, 0, st>>>(
+  emit_kernel<uint64_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
+      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, (uint32_t)n, tiles_per_view,
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, (uint32_t)parts);
+  return launch_status(cudaGetLastError());
+}
+
+extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, int32_t views,
+                                          const ags_camera* cams, const uint32_t* order, uint32_t* keys,
+                                          uint32_t* vals, int64_t capacity, int64_t* d_num_pairs, int64_t* d_status,
+                                          void* ws, size_t ws_bytes, void* stream) {
+  using namespace ags;
+  if (!proj || !d_num_pairs || !d_status || n < 0 || capacity < 0 || capacity > AGS_MAX_PAIRS)
+    return AGS_ERR_INVALID_ARG;
+  CamBatch cb;
+  ags_status s = build_cams(cams, views, &cb);
+  if (s != AGS_OK) return s;
+  const int64_t total = n * (int64_t)views;
+  if (total >= ((int64_t)1 << 32)) return AGS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (total == 0) return launch_status(cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st));
+  if (!proj->rect || (capacity > 0 && (!keys || !vals))) return AGS_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < ags_emit_workspace_bytes(n, views) || ((uintptr_t)ws & 7u)) return AGS_ERR_INVALID_ARG;
+  const size_t parts = emit_parts(total);
+  uint32_t tiles_per_view = (uint32_t)cb.c[0].gx * (uint32_t)cb.c[0].gy;
+  if ((uint64_t)tiles_per_view * (uint64_t)views >= (1ull << 32)) return AGS_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemsetAsync(ws, 0, 256 + 8 * parts, st);
+  if (e != cudaSuccess) return AGS_ERR_CUDA;
+  uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
+  uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
+  emit_kernel<uint32_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
       reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, (uint32_t)n, tiles_per_view,
       (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, (uint32_t)parts);
   return launch_status(cudaGetLastError());
@@ -292,7 +330,7 @@ extern "C" ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t 
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
   uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
-  emit_kernel<<<(unsigned)parts, kEmitThreads, 0, st>>>(
+  emit_kernel<uint64_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
       reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, (uint32_t)n, tiles_per_view,
       (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, (uint32_t)parts);
   return launch_status(cudaGetLastError());

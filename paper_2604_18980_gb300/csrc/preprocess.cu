@@ -29,14 +29,14 @@ struct PreOut {
   uint16_t* rect;
   uint32_t* touched;
   uint8_t* flags;
-  uint64_t* dkey;
+  uint32_t* dkey;
 };
 
 __device__ __forceinline__ void write_culled(const PreOut& o, int64_t e) {
   reinterpret_cast<uint2*>(o.rect)[e] = make_uint2(0u, 0u);
   if (o.touched) o.touched[e] = 0u;
   o.flags[e] = kFlagCulled;
-  if (o.dkey) o.dkey[e] = ~0ull;
+  if (o.dkey) o.dkey[e] = 0xffffffffu;
 }
 
 // Tiles [t0, t1) holding a pixel centre in [lo, hi] on an axis of `len` pixels.
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn
                                                        (uint32_t)x1 | ((uint32_t)y1 << 16));
     if (out.touched) out.touched[e] = touched;
     out.flags[e] = flags;
-    if (out.dkey) out.dkey[e] = ((uint64_t)view << 32) | __float_as_uint(pj.t[2]);
+    if (out.dkey) out.dkey[e] = __float_as_uint(pj.t[2]);
   }
 }
 

@@ -1,60 +1,105 @@
-// sort.cu -- stable LSD radix sort of the Gaussian-tile pairs (Sec. 2.1 sorting
-// stage) and the per-tile ranges.
+// sort.cu -- stable LSD radix sorts (Sec. 2.1 sorting stage) of 32- or 64-bit
+// keys with 32-bit values, and the per-tile ranges of the sorted pairs.
 //
-// "Onesweep" organisation: one pass over the keys builds the histograms of
-// every digit at once; then each digit pass is a single kernel in which each
-// block (256 threads x 8 keys) ranks its keys with warp-level match/ballot
+// Used three ways: the depth pre-sort of the Gaussians (32-bit keys: the fp32
+// depth bits), the sort of the tile keys of depth-ordered pairs (32-bit keys:
+// view * tiles + tile), and the sort of full 64-bit (tile | depth) pair keys.
+//
+// "Onesweep" organisation: one kernel reads every key once and builds the
+// histograms of all digits; then each digit pass is a single kernel in which
+// each block (512 threads x 8 keys) ranks its keys with warp-level match/ballot
 // (per-warp digit counters in shared memory), publishes its digit counts,
-// obtains each digit's global offset by a decoupled look-back over the
-// preceding blocks (bounded spin, partition ids from an atomic counter), and
-// scatters through shared memory so that global stores are contiguous runs.
-// Ranking visits keys in index order (warp-major, then item, then lane), so
-// every pass is stable and equal keys keep their emission (Gaussian) order.
+// places its keys in shared memory in block-sorted order, obtains each digit's
+// global offset by a decoupled look-back over the preceding blocks (bounded
+// spin, partition ids from an atomic counter), and writes runs of equal digits
+// as contiguous stores.  Ranking visits keys in index order (warp-major, then
+// item, then lane), so every pass is stable and equal keys keep their input
+// order.
 #include <algorithm>
+#include <cstddef>
 #include <utility>
 
 #include "ags_internal.cuh"
 
 namespace ags {
 
+constexpr int kSortThreads = 512;
 constexpr int kSortItems = 8;                             // keys per thread
-constexpr int kMinPart = 256 * kSortItems;                // smallest partition (workspace sizing)
+constexpr int kSortPart = kSortThreads * kSortItems;      // 4096 keys per partition
 constexpr int kMaxRadix = 512;                            // digits of up to 9 bits
 constexpr int kMaxPasses = 16;
 constexpr uint32_t kLbAgg = 1u << 30;
 constexpr uint32_t kLbInc = 2u << 30;
 constexpr uint32_t kLbMask = (1u << 30) - 1u;
-constexpr int kLookWindow = 32;                             // predecessors polled per round trip
-constexpr size_t kSortHdr = 256;                           // pass counters
+constexpr int kLookWindow = 8;                           // predecessors polled per round trip
+constexpr size_t kSortHdr = 256;                          // pass counters
 constexpr size_t kSortHistBytes = (size_t)kMaxPasses * kMaxRadix * 4;
 
-template <int THREADS, int RADIX>
+__device__ __forceinline__ uint32_t key_digit(uint32_t k, int shift, uint32_t mask) { return (k >> shift) & mask; }
+__device__ __forceinline__ uint32_t key_digit(uint64_t k, int shift, uint32_t mask) {
+  return (uint32_t)(k >> shift) & mask;
+}
+// Range (tile) index of a key: 32-bit keys are the index, 64-bit pair keys
+// carry it in the high word.
+__device__ __forceinline__ uint32_t key_range(uint32_t k) { return k; }
+__device__ __forceinline__ uint32_t key_range(uint64_t k) { return (uint32_t)(k >> 32); }
+
+// Staging index with one padding word per 32: keys of consecutive digits are
+// staged about 4096 / RADIX words apart, which would otherwise put many lanes
+// of a warp on one shared-memory bank.
+__device__ __forceinline__ uint32_t stage_index(uint32_t i) { return i + (i >> 5); }
+constexpr int kStageWords = kSortPart + kSortPart / 32;
+
+template <int RADIX, typename K>
 struct SortSmem {
-  static constexpr int kWarps = THREADS / 32;
-  static constexpr int kPart = THREADS * kSortItems;
-  union {
-    uint16_t warp_hist[kWarps][RADIX];                     // ranking phase (<= 256 per warp)
-    struct {
-      uint64_t keys[kPart];
-      uint32_t vals[kPart];
-    } stage;                                               // block-sorted keys, before the look-back
-  } u;
-  uint32_t bhist[RADIX];        // block digit counts, then the block-local exclusive digit starts
+  static constexpr int kWarps = kSortThreads / 32;
+  uint32_t bhist[RADIX];        // block-local exclusive digit starts
   uint32_t gbase[RADIX];        // global index of block-local position 0, per digit (mod 2^32)
   uint32_t scan_tot[kWarps];
   uint32_t part;
+  union {
+    struct {
+      uint16_t warp_hist[kWarps][RADIX + 2];               // ranking; slot RADIX absorbs keys past the count
+      uint32_t bins[kWarps][RADIX + 1];                    // peer masks of the atomic-OR ranking (last member:
+    } r;                                                   // absent from the launch when ranking by match)
+    struct {
+      K keys[kStageWords];
+      uint32_t vals[kStageWords];
+    } stage;                                               // block-sorted keys, before the look-back
+  } u;
 };
 
-__device__ __forceinline__ uint32_t digit_mask(int shift, int end_bit, int digit_bits) {
-  int b = min(digit_bits, end_bit - shift);
-  return (1u << b) - 1u;
+// Dynamic shared memory of a digit pass: the peer-mask table only when it is used.
+template <int RADIX, typename K>
+static size_t sort_smem_bytes(bool rank_or) {
+  using Sm = SortSmem<RADIX, K>;
+  if (rank_or) return sizeof(Sm);
+  return offsetof(Sm, u) + std::max(sizeof(Sm::u.r.warp_hist), sizeof(Sm::u.stage));   // <= sizeof(Sm)
 }
 
-// The pair count is read on the device and clamped to the buffer capacity (after
+// The count is read on the device and clamped to the buffer capacity (after
 // an emission overflow it exceeds it; the status block already records that).
-__device__ __forceinline__ int64_t clamped_count(const int64_t* count_ptr, int64_t capacity) {
+__device__ __forceinline__ uint32_t clamped_count(const int64_t* count_ptr, int64_t capacity) {
   int64_t c = *count_ptr;
-  return c < 0 ? 0 : (c > capacity ? capacity : c);
+  return (uint32_t)(c < 0 ? 0 : (c > capacity ? capacity : c));
+}
+
+// Sixteen consecutive keys from a 16-byte aligned address.
+__device__ __forceinline__ void load16(const uint32_t* p, uint32_t (&k)[16]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const uint4 t = __ldcs(q + i);
+    k[4 * i] = t.x; k[4 * i + 1] = t.y; k[4 * i + 2] = t.z; k[4 * i + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void load16(const uint64_t* p, uint64_t (&k)[16]) {
+  const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const ulonglong2 t = __ldcs(q + i);
+    k[2 * i] = t.x; k[2 * i + 1] = t.y;
+  }
 }
 
 // Global digit histograms of every pass in one read.  Each thread takes 16
@@ -62,34 +107,33 @@ __device__ __forceinline__ int64_t clamped_count(const int64_t* count_ptr, int64
 // keys are highly clustered (pairs of one Gaussian are consecutive, the depth
 // exponent byte is nearly constant), so a run costs one shared atomic instead
 // of one per key, and unclustered digits do not contend anyway.
-__global__ void __launch_bounds__(256) hist_kernel(const uint64_t* __restrict__ keys, const int64_t* count_ptr,
+template <typename K>
+__global__ void __launch_bounds__(256) hist_kernel(const K* __restrict__ keys, const int64_t* count_ptr,
                                                    int64_t capacity, int begin_bit, int end_bit, int digit_bits,
                                                    int passes, int radix, uint32_t* ghist) {
   __shared__ uint32_t h[kMaxPasses * kMaxRadix];
   for (int i = threadIdx.x; i < passes * radix; i += blockDim.x) h[i] = 0u;
   __syncthreads();
-  const int64_t count = clamped_count(count_ptr, capacity);
+  const uint32_t count = clamped_count(count_ptr, capacity);
   constexpr int R = 16;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * R;
-  for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * R; i0 < count; i0 += stride) {
-    uint64_t k[R];
+  const uint32_t stride = gridDim.x * blockDim.x * R;
+  for (uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) * R; i0 < count; i0 += stride) {
+    K k[R];
     if (i0 + R <= count) {
-      const ulonglong2* p = reinterpret_cast<const ulonglong2*>(keys + i0);
-#pragma unroll
-      for (int q = 0; q < R / 2; q++) { ulonglong2 t = __ldcs(p + q); k[2 * q] = t.x; k[2 * q + 1] = t.y; }
+      load16(keys + i0, k);
     } else {
 #pragma unroll
-      for (int q = 0; q < R; q++) k[q] = (i0 + q < count) ? keys[i0 + q] : ~0ull;
+      for (int q = 0; q < R; q++) k[q] = (i0 + q < count) ? keys[i0 + q] : (K)0;
     }
-    const int nv = (int)min((int64_t)R, count - i0);
+    const int nv = (int)min((uint32_t)R, count - i0);
     for (int p = 0; p < passes; p++) {
       const int sh = begin_bit + p * digit_bits;
-      const uint32_t m = digit_mask(sh, end_bit, digit_bits);
-      uint32_t cur = (uint32_t)(k[0] >> sh) & m, run = 1;
+      const uint32_t m = (1u << min(digit_bits, end_bit - sh)) - 1u;
+      uint32_t cur = key_digit(k[0], sh, m), run = 1;
 #pragma unroll
       for (int q = 1; q < R; q++) {
         if (q >= nv) break;
-        const uint32_t d = (uint32_t)(k[q] >> sh) & m;
+        const uint32_t d = key_digit(k[q], sh, m);
         if (d == cur) { run++; } else { atomicAdd(&h[p * radix + cur], run); cur = d; run = 1; }
       }
       atomicAdd(&h[p * radix + cur], run);
@@ -121,80 +165,94 @@ __global__ void __launch_bounds__(RADIX) hist_scan_kernel(uint32_t* ghist) {
   h[t] = pre + incl - v;
 }
 
-// One digit pass over a partition of THREADS x 8 keys.  The keys are ranked
-// within each warp (match.any, index order, so the pass is stable); the
-// per-warp counts give the block's digit totals, which are published to the
-// look-back at once; the keys are placed in shared memory in block-sorted
-// order, and only then does the block look back for each digit's global
-// offset (a window of 32 predecessors per round trip), with its registers
-// free.  Large partitions keep the number of look-back steps small.
-template <int THREADS, int RADIX>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
-onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+// One digit pass over a partition of 4096 keys.  The keys are ranked within
+// each warp (match.any, index order, so the pass is stable); the per-warp
+// counts give the block's digit totals, which are published to the look-back
+// at once; the keys are placed in shared memory in block-sorted order, and
+// only then does the block look back for each digit's global offset (up to
+// kLookWindow predecessors per round trip, consumed front to back until the
+// first inclusive prefix), with its registers free.  kout may be null (the
+// last pass of a sort whose caller needs only the values); ranges, when not
+// null, receive [start, end) of every range index met in this last pass.
+template <int RADIX, typename K>
+__global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 3 : 2)
+onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
                 uint32_t* __restrict__ vout, const int64_t* count_ptr, int64_t capacity, int identity, int shift,
-                uint32_t mask, const uint32_t* __restrict__ gprefix, uint32_t* lookback, uint32_t* counter,
-                int64_t* status, uint32_t* ranges, int64_t num_ranges) {
-  using Sm = SortSmem<THREADS, RADIX>;
+                uint32_t mask, int rank_or, const uint32_t* __restrict__ gprefix, uint32_t* lookback,
+                uint32_t* counter, int64_t* status, uint32_t* ranges, uint32_t num_ranges) {
+  using Sm = SortSmem<RADIX, K>;
   constexpr int kWarps = Sm::kWarps;
-  constexpr int kPart = Sm::kPart;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sm& S = *reinterpret_cast<Sm*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool digit_thread = tid < RADIX;                   // threads owning one digit each
   if (tid == 0) S.part = atomicAdd(counter, 1u);
   {
-    uint32_t* wh = reinterpret_cast<uint32_t*>(&S.u.warp_hist[0][0]);
-    for (int i = tid; i < kWarps * RADIX / 2; i += THREADS) wh[i] = 0u;
-    for (int i = tid; i < RADIX; i += THREADS) S.bhist[i] = 0u;
+    uint32_t* wh = reinterpret_cast<uint32_t*>(&S.u.r.warp_hist[0][0]);
+    for (int i = tid; i < kWarps * (RADIX + 2) / 2; i += kSortThreads) wh[i] = 0u;
+    if (rank_or) {
+      uint32_t* bz = &S.u.r.bins[0][0];
+      for (int i = tid; i < kWarps * (RADIX + 1); i += kSortThreads) bz[i] = 0u;
+    }
   }
   const uint32_t gp = digit_thread ? __ldg(gprefix + tid) : 0u;   // prefetched, used at the end
   __syncthreads();
   const uint32_t part = S.part;
-  const uint32_t count = (uint32_t)clamped_count(count_ptr, capacity);
-  const uint32_t nparts = (count + kPart - 1) / kPart;
-  if (part >= nparts) return;   // no block waits on a higher partition
-  const uint32_t base = part * kPart;
+  const uint32_t count = clamped_count(count_ptr, capacity);
+  if (part >= (count + kSortPart - 1) / kSortPart) return;   // no block waits on a higher partition
+  const uint32_t base = part * kSortPart;
+  const uint32_t ibase = base + warp * (32 * kSortItems) + lane;   // item i sits at ibase + 32 i
 
   // load (warp-striped, coalesced), all loads first
-  uint64_t key[kSortItems];
+  K key[kSortItems];
   uint32_t val[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    const uint32_t idx = base + warp * (32 * kSortItems) + i * 32 + lane;
+    const uint32_t idx = ibase + 32 * i;
     const bool valid = idx < count;
-    key[i] = valid ? __ldcs(kin + idx) : 0ull;
+    key[i] = valid ? __ldcs(kin + idx) : (K)0;
     val[i] = valid ? (identity ? idx : __ldcs(vin + idx)) : 0u;
   }
-  uint32_t* lb = lookback + (size_t)part * RADIX;
-  uint32_t tot = 0;
 
-  // rank within the warp (match.any), in index order
+  // rank within the warp (match.any), in index order; keys past the count
+  // take the dummy digit RADIX
+  uint16_t* wh = S.u.r.warp_hist[warp];
+  uint32_t* bins = rank_or ? S.u.r.bins[warp] : nullptr;
   uint32_t rank[kSortItems];
   const unsigned lt_mask = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    const uint32_t idx = base + warp * (32 * kSortItems) + i * 32 + lane;
-    const bool valid = idx < count;
-    const uint32_t d = valid ? ((uint32_t)(key[i] >> shift) & mask) : (uint32_t)RADIX;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t before = valid ? S.u.warp_hist[warp][d] : 0u;
+    const uint32_t d = ibase + 32 * i < count ? key_digit(key[i], shift, mask) : (uint32_t)RADIX;
+    unsigned peers;
+    if (rank_or) {                      // peers by atomic OR of lane bits into the digit's word
+      atomicOr(bins + d, 1u << lane);
+      __syncwarp();
+      peers = bins[d];
+    } else {
+      peers = __match_any_sync(0xffffffffu, d);
+    }
+    const uint32_t before = wh[d];
+    const uint32_t below = (uint32_t)__popc(peers & lt_mask);
     __syncwarp();
-    if (valid && (peers & lt_mask) == 0u) S.u.warp_hist[warp][d] = (uint16_t)(before + __popc(peers));
+    if (below == 0u) {
+      wh[d] = (uint16_t)(before + __popc(peers));
+      if (rank_or) bins[d] = 0u;
+    }
     __syncwarp();
-    rank[i] = before + (uint32_t)__popc(peers & lt_mask);
+    rank[i] = before + below;
   }
   __syncthreads();
 
   // per digit: per-warp exclusive prefixes and the block-exclusive digit start
+  uint32_t tot = 0;
+  uint32_t* lb = lookback + (size_t)part * RADIX;
   if (digit_thread) {
-    uint32_t run = 0;
 #pragma unroll 4
     for (int w = 0; w < kWarps; w++) {
-      const uint32_t v = S.u.warp_hist[w][tid];
-      S.u.warp_hist[w][tid] = (uint16_t)run;
-      run += v;
+      const uint32_t v = S.u.r.warp_hist[w][tid];
+      S.u.r.warp_hist[w][tid] = (uint16_t)tot;
+      tot += v;
     }
-    tot = run;
     st_relaxed_u32(lb + tid, (part == 0 ? kLbInc : kLbAgg) | tot);
   }
   uint32_t incl = tot;
@@ -215,27 +273,26 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
   uint32_t pos[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    const uint32_t idx = base + warp * (32 * kSortItems) + i * 32 + lane;
-    const uint32_t d = (uint32_t)(key[i] >> shift) & mask;
-    pos[i] = idx < count ? S.bhist[d] + S.u.warp_hist[warp][d] + rank[i] : 0xffffffffu;
+    const uint32_t d = key_digit(key[i], shift, mask);
+    pos[i] = ibase + 32 * i < count ? S.bhist[d] + wh[d] + rank[i] : 0xffffffffu;
   }
   __syncthreads();   // the staging area aliases the warp counters
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    if (pos[i] < (uint32_t)kPart) {
-      S.u.stage.keys[pos[i]] = key[i];
-      S.u.stage.vals[pos[i]] = val[i];
+    if (pos[i] < (uint32_t)kSortPart) {
+      const uint32_t si = stage_index(pos[i]);
+      S.u.stage.keys[si] = key[i];
+      S.u.stage.vals[si] = val[i];
     }
   }
 
-  // decoupled look-back per digit, kLookWindow predecessors per round trip:
-  // add the aggregates back to the nearest inclusive prefix; re-poll from the
-  // first predecessor that has not published yet.
+  // decoupled look-back per digit: add the predecessors' aggregates back to
+  // the nearest inclusive prefix; re-poll from the first one not yet published
   if (digit_thread) {
     uint32_t excl = 0;
     if (part > 0) {
       const uint64_t t0 = globaltimer_ns();
-      int64_t p = (int64_t)part - 1;
+      int32_t p = (int32_t)part - 1;
       bool found = false;
       while (!found) {
         uint32_t sv[kLookWindow];
@@ -245,12 +302,11 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
         int used = 0;
 #pragma unroll
         for (int q = 0; q < kLookWindow; q++) {
-          if (found || used < q) continue;           // stop at the first unpublished entry
           const uint32_t flag = sv[q] >> 30;
-          if (flag == 0u) continue;
+          if (flag == 0u) break;
           excl += sv[q] & kLbMask;
           used = q + 1;
-          if (flag == 2u) found = true;
+          if (flag == 2u) { found = true; break; }
         }
         p -= used;
         if (!found && used < kLookWindow && globaltimer_ns() - t0 > kWaitLimitNs) {
@@ -263,29 +319,38 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
     S.gbase[tid] = gp + excl - doff;
   }
   __syncthreads();
-  const uint32_t nvalid = min((uint32_t)kPart, count - base);
-  for (uint32_t j = tid; j < nvalid; j += THREADS) {
-    const uint64_t k = S.u.stage.keys[j];
-    const uint32_t d = (uint32_t)(k >> shift) & mask;
-    const uint32_t dst = S.gbase[d] + j;
+
+  // scatter: consecutive positions of one digit go to consecutive addresses
+  const uint32_t nvalid = min((uint32_t)kSortPart, count - base);
+#pragma unroll 2
+  for (int t = 0; t < kSortItems; t++) {
+    const uint32_t j = (uint32_t)(t * kSortThreads + tid);
+    const bool v = j < nvalid;
+    const K k = v ? S.u.stage.keys[stage_index(j)] : (K)0;
+    const uint32_t dst = v ? S.gbase[key_digit(k, shift, mask)] + j : 0xffffffffu;
     if (dst < count) {
-      kout[dst] = k;
-      vout[dst] = S.u.stage.vals[j];
-      if (ranges) {
-        // last pass: the output is fully sorted and one tile's keys are consecutive
-        // (equal tiles share the digit), so a tile's first and last keys in this
-        // block bound its range; other blocks holding the same tile do the same.
-        const uint64_t tile = k >> 32;
-        if (tile < (uint64_t)num_ranges) {
-          if (j == 0 || (S.u.stage.keys[j - 1] >> 32) != tile) atomicMin(ranges + 2 * tile, dst);
-          if (j + 1 == nvalid || (S.u.stage.keys[j + 1] >> 32) != tile) atomicMax(ranges + 2 * tile + 1, dst + 1);
-        }
+      if (kout) kout[dst] = k;
+      vout[dst] = S.u.stage.vals[stage_index(j)];
+    }
+    if (ranges) {
+      // last pass: the output is fully sorted, so a range index's keys are
+      // consecutive here and in the output; its first and last key in this
+      // block bound its range (other blocks holding it do the same)
+      const uint32_t r = key_range(k);
+      uint32_t rp = __shfl_up_sync(0xffffffffu, r, 1), rn = __shfl_down_sync(0xffffffffu, r, 1);
+      if (lane == 0) rp = (v && j > 0) ? key_range(S.u.stage.keys[stage_index(j - 1)]) : 0xffffffffu;
+      if (lane == 31) rn = (j + 1 < nvalid) ? key_range(S.u.stage.keys[stage_index(j + 1)]) : 0xffffffffu;
+      if (j + 1 >= nvalid) rn = 0xffffffffu;
+      if (j == 0) rp = 0xffffffffu;
+      if (dst < count && r < num_ranges) {
+        if (rp != r) atomicMin(ranges + 2 * (size_t)r, dst);
+        if (rn != r) atomicMax(ranges + 2 * (size_t)r + 1, dst + 1);
       }
     }
   }
 }
 
-// Tiles no pair reached still hold the (0xffffffff, 0) of the initialisation.
+// Ranges no key reached still hold the (0xffffffff, 0) of the initialisation.
 __global__ void ranges_fixup_kernel(uint2* ranges, int64_t num_ranges) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < num_ranges; t += (int64_t)gridDim.x * blockDim.x) {
     const uint2 r = ranges[t];
@@ -293,31 +358,35 @@ __global__ void ranges_fixup_kernel(uint2* ranges, int64_t num_ranges) {
   }
 }
 
-__global__ void ranges_kernel(const uint64_t* __restrict__ keys, const int64_t* count_ptr, int64_t capacity,
+// Ranges of keys that are already sorted (a sort with no digit pass).
+template <typename K>
+__global__ void ranges_kernel(const K* __restrict__ keys, const int64_t* count_ptr, int64_t capacity,
                               uint32_t* ranges, int64_t num_ranges) {
   const int64_t count = clamped_count(count_ptr, capacity);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t tile = keys[i] >> 32;
-    if (tile >= (uint64_t)num_ranges) continue;
-    if (i == 0 || (keys[i - 1] >> 32) != tile) ranges[2 * tile] = (uint32_t)i;
-    if (i == count - 1 || (keys[i + 1] >> 32) != tile) ranges[2 * tile + 1] = (uint32_t)(i + 1);
+    const uint32_t r = key_range(keys[i]);
+    if (r >= (uint64_t)num_ranges) continue;
+    if (i == 0 || key_range(keys[i - 1]) != r) ranges[2 * (size_t)r] = (uint32_t)i;
+    if (i == count - 1 || key_range(keys[i + 1]) != r) ranges[2 * (size_t)r + 1] = (uint32_t)(i + 1);
   }
 }
 
-static size_t sort_parts(int64_t capacity) { return (size_t)((capacity + kMinPart - 1) / kMinPart); }
+static size_t sort_parts(int64_t capacity) { return (size_t)((capacity + kSortPart - 1) / kSortPart); }
 
-template <int THREADS, int RADIX>
-static cudaError_t launch_passes(uint64_t*& kin, uint32_t*& vin, uint64_t* kout, uint32_t* vout,
-                                 const int64_t* d_num_pairs, int64_t capacity, int begin_bit, int end_bit,
-                                 int digit_bits, int passes, int flags, uint32_t* ghist, uint32_t* lookback,
-                                 uint32_t* counters, int64_t* d_status, uint32_t* ranges, int64_t num_ranges,
-                                 cudaStream_t st) {
+template <int RADIX, typename K>
+static cudaError_t launch_passes(K*& kin, uint32_t*& vin, K* kout, uint32_t* vout, const int64_t* d_num_pairs,
+                                 int64_t capacity, int begin_bit, int end_bit, int digit_bits, int passes,
+                                 int flags, uint32_t* ghist, uint32_t* lookback, uint32_t* counters,
+                                 int64_t* d_status, uint32_t* ranges, int64_t num_ranges, cudaStream_t st) {
   hist_scan_kernel<RADIX><<<passes, RADIX, 0, st>>>(ghist);
-  const int smem = (int)sizeof(SortSmem<THREADS, RADIX>);
-  cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<THREADS, RADIX>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int rank_or = (flags & AGS_SORT_RANK_OR) ? 1 : 0;
+  const int smem = (int)sort_smem_bytes<RADIX, K>(rank_or != 0);
+  // the attribute always allows the larger layout, so that launches of either
+  // ranking method (e.g. recorded together in one CUDA graph) stay valid
+  cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<RADIX, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sort_smem_bytes<RADIX, K>(true));
   if (e != cudaSuccess) return e;
-  const size_t parts = (size_t)((capacity + SortSmem<THREADS, RADIX>::kPart - 1) / SortSmem<THREADS, RADIX>::kPart);
+  const size_t parts = sort_parts(capacity);
   for (int p = 0; p < passes; p++) {
     e = cudaMemsetAsync(lookback, 0, parts * RADIX * 4, st);
     if (e != cudaSuccess) return e;
@@ -325,9 +394,11 @@ static cudaError_t launch_passes(uint64_t*& kin, uint32_t*& vin, uint64_t* kout,
     const uint32_t mask = (1u << std::min(digit_bits, end_bit - sh)) - 1u;
     const int identity = (p == 0 && (flags & AGS_SORT_IDENTITY_VALUES)) ? 1 : 0;
     const bool last = p == passes - 1;
-    onesweep_kernel<THREADS, RADIX><<<(unsigned)parts, THREADS, smem, st>>>(
-        kin, vin, kout, vout, d_num_pairs, capacity, identity, sh, mask, ghist + p * RADIX, lookback, counters + p,
-        d_status, last ? ranges : nullptr, num_ranges);
+    K* ko = (last && (flags & AGS_SORT_DISCARD_KEYS)) ? nullptr : kout;
+    onesweep_kernel<RADIX, K><<<(unsigned)parts, kSortThreads, smem, st>>>(
+        kin, vin, ko, vout, d_num_pairs, capacity, identity, sh, mask, rank_or, ghist + p * RADIX, lookback,
+        counters + p,
+        d_status, last ? ranges : nullptr, (uint32_t)num_ranges);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     std::swap(kin, kout);
@@ -336,6 +407,12 @@ static cudaError_t launch_passes(uint64_t*& kin, uint32_t*& vin, uint64_t* kout,
   return cudaSuccess;
 }
 
+template <typename K>
+static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, const int64_t* d_num_pairs,
+                            int64_t capacity, int32_t begin_bit, int32_t end_bit, int32_t digit_bits, int32_t flags,
+                            uint32_t* ranges, int64_t num_ranges, int32_t* result_in_alt, int64_t* d_status,
+                            void* ws, size_t ws_bytes, void* stream);
+
 }  // namespace ags
 
 extern "C" size_t ags_sort_workspace_bytes(int64_t capacity) {
@@ -343,20 +420,23 @@ extern "C" size_t ags_sort_workspace_bytes(int64_t capacity) {
   return ags::kSortHdr + ags::kSortHistBytes + ags::sort_parts(capacity) * ags::kMaxRadix * 4;
 }
 
-extern "C" ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                               const int64_t* d_num_pairs, int64_t capacity, int32_t begin_bit, int32_t end_bit,
-                               int32_t digit_bits, int32_t flags, uint32_t* ranges, int64_t num_ranges,
-                               int32_t* result_in_alt, int64_t* d_status, void* ws, size_t ws_bytes,
-                               void* stream) {
-  using namespace ags;
+namespace ags {
+
+template <typename K>
+static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, const int64_t* d_num_pairs,
+                            int64_t capacity, int32_t begin_bit, int32_t end_bit, int32_t digit_bits, int32_t flags,
+                            uint32_t* ranges, int64_t num_ranges, int32_t* result_in_alt, int64_t* d_status,
+                            void* ws, size_t ws_bytes, void* stream) {
+  constexpr int kKeyBits = 8 * (int)sizeof(K);
   if (!d_num_pairs || !d_status || capacity < 0 || capacity >= AGS_MAX_PAIRS) return AGS_ERR_INVALID_ARG;
-  if (begin_bit < 0 || end_bit > 64 || begin_bit > end_bit || digit_bits < 4 || digit_bits > 9)
+  if (begin_bit < 0 || end_bit > kKeyBits || begin_bit > end_bit || digit_bits < 4 || digit_bits > 9)
     return AGS_ERR_INVALID_ARG;
-  if (flags & ~AGS_SORT_IDENTITY_VALUES) return AGS_ERR_INVALID_ARG;
+  if (flags & ~(AGS_SORT_IDENTITY_VALUES | AGS_SORT_DISCARD_KEYS | AGS_SORT_RANK_OR)) return AGS_ERR_INVALID_ARG;
   const int passes = (end_bit - begin_bit + digit_bits - 1) / digit_bits;
   if (passes > kMaxPasses) return AGS_ERR_INVALID_ARG;
-  if (ranges && num_ranges <= 0) return AGS_ERR_INVALID_ARG;
+  if (ranges && (num_ranges <= 0 || num_ranges > ((int64_t)1 << 32) - 1)) return AGS_ERR_INVALID_ARG;
   if (capacity > 0 && (!keys || !vals || (passes > 0 && (!keys_alt || !vals_alt)))) return AGS_ERR_INVALID_ARG;
+  if (capacity > 0 && passes > 0 && ((uintptr_t)keys & 15u)) return AGS_ERR_INVALID_ARG;   // 16-byte key loads
   if (!ws || ws_bytes < ags_sort_workspace_bytes(capacity) || ((uintptr_t)ws & 15u)) return AGS_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   if (result_in_alt) *result_in_alt = passes & 1;
@@ -366,7 +446,7 @@ extern "C" ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_al
   uint32_t* lookback = reinterpret_cast<uint32_t*>(w + kSortHdr + kSortHistBytes);
   const int radix = digit_bits > 8 ? 512 : 256;
   cudaError_t e = cudaSuccess;
-  uint64_t* kin = keys;
+  K* kin = keys;
   uint32_t* vin = vals;
   if (capacity > 0 && passes > 0) {
     e = cudaMemsetAsync(w, 0, kSortHdr + kSortHistBytes, st);
@@ -375,19 +455,19 @@ extern "C" ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_al
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     unsigned hb = (unsigned)std::min<int64_t>((capacity + 255) / 256, (int64_t)sms * 4);
-    hist_kernel<<<hb, 256, 0, st>>>(keys, d_num_pairs, capacity, begin_bit, end_bit, digit_bits, passes, radix, ghist);
-    // partitions of 512 threads x 8 keys, two blocks per SM
+    hist_kernel<K><<<hb, 256, 0, st>>>(keys, d_num_pairs, capacity, begin_bit, end_bit, digit_bits, passes, radix,
+                                       ghist);
     if (ranges) {   // start = 0xffffffff, end = 0: the last pass narrows them with atomics
       e = cudaMemset2DAsync(ranges, 8, 0xff, 4, (size_t)num_ranges, st);
       if (e == cudaSuccess) e = cudaMemset2DAsync(ranges + 1, 8, 0, 4, (size_t)num_ranges, st);
       if (e != cudaSuccess) return AGS_ERR_CUDA;
     }
-    e = radix == 512 ? launch_passes<512, 512>(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit,
-                                               end_bit, digit_bits, passes, flags, ghist, lookback, counters,
-                                               d_status, ranges, num_ranges, st)
-                     : launch_passes<512, 256>(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit,
-                                               end_bit, digit_bits, passes, flags, ghist, lookback, counters,
-                                               d_status, ranges, num_ranges, st);
+    e = radix == 512 ? launch_passes<512, K>(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
+                                             digit_bits, passes, flags, ghist, lookback, counters, d_status, ranges,
+                                             num_ranges, st)
+                     : launch_passes<256, K>(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
+                                             digit_bits, passes, flags, ghist, lookback, counters, d_status, ranges,
+                                             num_ranges, st);
     if (e != cudaSuccess) return AGS_ERR_CUDA;
   }
   if (ranges) {
@@ -399,9 +479,31 @@ extern "C" ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_al
       if (e != cudaSuccess) return AGS_ERR_CUDA;
       if (capacity > 0) {
         const int blocks = (int)std::min<int64_t>((capacity + 255) / 256, 65535 * 4);
-        ranges_kernel<<<blocks, 256, 0, st>>>(kin, d_num_pairs, capacity, ranges, num_ranges);
+        ranges_kernel<K><<<blocks, 256, 0, st>>>(kin, d_num_pairs, capacity, ranges, num_ranges);
       }
     }
   }
   return launch_status(cudaGetLastError());
+}
+
+}  // namespace ags
+
+extern "C" ags_status ags_sort(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                               const int64_t* d_num_pairs, int64_t capacity, int32_t begin_bit, int32_t end_bit,
+                               int32_t digit_bits, int32_t flags, uint32_t* ranges, int64_t num_ranges,
+                               int32_t* result_in_alt, int64_t* d_status, void* ws, size_t ws_bytes,
+                               void* stream) {
+  return ags::sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
+                                  digit_bits, flags, ranges, num_ranges, result_in_alt, d_status, ws, ws_bytes,
+                                  stream);
+}
+
+extern "C" ags_status ags_sort32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                                 const int64_t* d_num_pairs, int64_t capacity, int32_t begin_bit, int32_t end_bit,
+                                 int32_t digit_bits, int32_t flags, uint32_t* ranges, int64_t num_ranges,
+                                 int32_t* result_in_alt, int64_t* d_status, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  return ags::sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
+                                  digit_bits, flags, ranges, num_ranges, result_in_alt, d_status, ws, ws_bytes,
+                                  stream);
 }

@@ -28,9 +28,14 @@ def tiles_per_view(cam: dict) -> int:
     return ((cam["width"] + B.AGS_TILE - 1) // B.AGS_TILE) * ((cam["height"] + B.AGS_TILE - 1) // B.AGS_TILE)
 
 
+def tile_key_bits(views: int, tiles: int) -> int:
+    """Bits of the largest tile key view * tiles + tile."""
+    return max(1, int(views * tiles - 1).bit_length())
+
+
 def key_end_bit(views: int, tiles: int) -> int:
-    """Highest key bit + 1: 32 depth bits plus the bits of the largest tile id."""
-    return 32 + max(1, int(views * tiles - 1).bit_length())
+    """Highest bit + 1 of a 64-bit (tile | depth) key: 32 depth bits plus the tile key."""
+    return 32 + tile_key_bits(views, tiles)
 
 
 def digit_plan(bits: int, max_digit: int = 9) -> tuple:
@@ -45,7 +50,7 @@ class Renderer:
     def __init__(self, scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_PLAIN, K: float = 0.0, lut=None,
                  sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 9,
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
-                 presort: bool = True):
+                 presort: bool = True, pair_rank_or: bool = True):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -55,6 +60,7 @@ class Renderer:
         self.device = scene["mean"].device
         self.digit_bits = digit_bits
         self.presort = presort
+        self.pair_rank_or = pair_rank_or
         self.set_params(scale_mode, K, lut, sh_degree, bg)
         dev, V, n = self.device, self.V, self.n
         self.proj = dict(splat=torch.empty(V * n * 12, dtype=torch.float32, device=dev),
@@ -63,14 +69,15 @@ class Renderer:
                          tiles_touched=torch.empty(V * n, dtype=torch.int32, device=dev),
                          flags=torch.empty(V * n, dtype=torch.uint8, device=dev))
         if presort:
-            # depth pre-sort of the Gaussians: the pair sort then needs only the tile digits
-            self.proj["depth_key"] = torch.empty(V * n, dtype=torch.int64, device=dev)
-            self.dkey_alt = torch.empty(V * n, dtype=torch.int64, device=dev)
+            # depth pre-sort of the Gaussians (32-bit depth keys); pairs then carry
+            # 32-bit tile keys and the pair sort needs only the tile digits
+            self.proj["depth_key"] = torch.empty(V * n, dtype=torch.int32, device=dev)
+            self.dkey_alt = torch.empty(V * n, dtype=torch.int32, device=dev)
             self.order = torch.empty(V * n, dtype=torch.int32, device=dev)
             self.order_alt = torch.empty(V * n, dtype=torch.int32, device=dev)
             self.n_total = torch.tensor([V * n], dtype=torch.int64, device=dev)
             self.ws_dsort = torch.empty(B.ags_sort_workspace_bytes(V * n), dtype=torch.uint8, device=dev)
-            self.dsort_end = 32 + int(V - 1).bit_length()
+            self.dsort_end = 32
         self.status = torch.zeros(4, dtype=torch.int64, device=dev)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
         self.ws_emit = torch.empty(max(B.ags_emit_workspace_bytes(n, V), 16), dtype=torch.uint8, device=dev)
@@ -102,9 +109,10 @@ class Renderer:
             raise ValueError("more than %d pairs in one batch; render fewer views at once" % B.AGS_MAX_PAIRS)
         dev = self.device
         self.capacity = int(capacity)
-        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+        kt = torch.int32 if self.presort else torch.int64
+        self.keys = torch.empty(self.capacity, dtype=kt, device=dev)
         self.vals = torch.empty(self.capacity, dtype=torch.int32, device=dev)
-        self.keys_alt = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+        self.keys_alt = torch.empty(self.capacity, dtype=kt, device=dev)
         self.vals_alt = torch.empty(self.capacity, dtype=torch.int32, device=dev)
         self.ws_sort = torch.empty(B.ags_sort_workspace_bytes(self.capacity), dtype=torch.uint8, device=dev)
 
@@ -118,16 +126,13 @@ class Renderer:
 
     @property
     def end_bit(self) -> int:
-        return key_end_bit(self.V, self.T)
-
-    @property
-    def begin_bit(self) -> int:
-        return 32 if self.presort else 0
+        """Highest sorted key bit + 1: the tile key (32-bit keys) or tile | depth (64-bit keys)."""
+        return tile_key_bits(self.V, self.T) if self.presort else key_end_bit(self.V, self.T)
 
     def sort_plan(self) -> tuple:
         """(passes, digit_bits) of the pair sort."""
         if self.presort:
-            return digit_plan(self.end_bit - self.begin_bit, self.digit_bits)
+            return digit_plan(self.end_bit, self.digit_bits)
         return max(1, -(-self.end_bit // self.digit_bits)), self.digit_bits
 
     def launches_per_forward(self) -> int:
@@ -142,23 +147,31 @@ class Renderer:
         B.ags_preprocess(self.scene, self.cams, self.params, self.proj, self.status)
 
     def depth_sort(self):
-        """Stable sort of the Gaussians by (view, depth): the emission order."""
+        """Stable sort of the Gaussians by depth: the emission order (each view's
+        Gaussians in depth order, equal depths in index order)."""
         if self.presort:
             passes, db = digit_plan(self.dsort_end, self.digit_bits)
-            alt = B.ags_sort(self.proj["depth_key"], self.order, self.dkey_alt, self.order_alt, self.n_total,
-                             self.V * self.n, 0, self.dsort_end, db, None, 0, self.status, self.ws_dsort,
-                             flags=B.AGS_SORT_IDENTITY_VALUES)
+            alt = B.ags_sort32(self.proj["depth_key"], self.order, self.dkey_alt, self.order_alt, self.n_total,
+                               self.V * self.n, 0, self.dsort_end, db, None, 0, self.status, self.ws_dsort,
+                               flags=B.AGS_SORT_IDENTITY_VALUES | B.AGS_SORT_DISCARD_KEYS)
             self.emit_order = self.order_alt if alt else self.order
 
     def emit(self):
-        B.ags_emit_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity, self.num_pairs,
-                         self.status, self.ws_emit, order=self.emit_order if self.presort else None)
+        if self.presort:
+            B.ags_emit_tile_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity,
+                                  self.num_pairs, self.status, self.ws_emit, order=self.emit_order)
+        else:
+            B.ags_emit_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity, self.num_pairs,
+                             self.status, self.ws_emit)
 
     def sort(self):
+        """Stable sort of the pairs by tile (and depth); only the values and the
+        per-tile ranges are kept."""
         _, db = self.sort_plan()
-        alt = B.ags_sort(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity,
-                         self.begin_bit, self.end_bit, db, self.ranges, self.V * self.T, self.status, self.ws_sort)
-        self.sorted_keys = self.keys_alt if alt else self.keys
+        fn = B.ags_sort32 if self.presort else B.ags_sort
+        flags = B.AGS_SORT_DISCARD_KEYS | (B.AGS_SORT_RANK_OR if self.pair_rank_or else 0)
+        alt = fn(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity, 0, self.end_bit,
+                 db, self.ranges, self.V * self.T, self.status, self.ws_sort, flags=flags)
         self.sorted_vals = self.vals_alt if alt else self.vals
 
     def rasterize(self, max_T=None):

@@ -72,10 +72,22 @@ def compare_features(r, orc_out, view=0):
 
 
 def gpu_pairs(r):
+    """Sorted pairs as 64-bit (tile | depth) keys and values, rebuilt from the
+    sorted values, the tile ranges and the per-splat depths (the renderer keeps
+    no sorted keys).  Checks on the way that the non-empty ranges tile
+    [0, pairs) in tile order."""
     npairs = r.pairs()
-    keys = r.sorted_keys[:npairs].cpu().numpy().view(np.uint64)
     vals = r.sorted_vals[:npairs].cpu().numpy().view(np.uint32).astype(np.int64)
-    return keys, vals
+    rg = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    length = rg[:, 1] - rg[:, 0]
+    assert np.all(length >= 0)
+    full = np.nonzero(length > 0)[0]
+    ends = np.cumsum(length[full])
+    assert ends.size == 0 or ends[-1] == npairs, "ranges do not cover the pairs"
+    np.testing.assert_array_equal(rg[full, 0], ends - length[full])
+    tile = np.repeat(full, length[full]).astype(np.uint64)
+    dbits = r.proj["depth"].cpu().numpy().view(np.uint32)[vals].astype(np.uint64)
+    return (tile << np.uint64(32)) | dbits, vals
 
 
 def compare_lists(r, orc_outs, tile_masks=None):

@@ -100,10 +100,10 @@ def test_capacity_overflow_is_reported_and_bounded():
     del guard
 
 
-@pytest.mark.parametrize("count,bits,digit", [(1, 40, 8), (4095, 40, 8), (4097, 45, 8), (100003, 49, 8),
-                                              (250000, 52, 7), (77777, 40, 5), (2049, 41, 9), (300001, 49, 9),
-                                              (65536, 36, 9)])
-def test_sort_random_keys_stable(count, bits, digit):
+@pytest.mark.parametrize("count,bits,digit,flags", [(1, 40, 8, 0), (4095, 40, 8, 4), (4097, 45, 8, 0),
+                                                    (100003, 49, 8, 4), (250000, 52, 7, 0), (77777, 40, 5, 4),
+                                                    (2049, 41, 9, 0), (300001, 49, 9, 4), (65536, 36, 9, 0)])
+def test_sort_random_keys_stable(count, bits, digit, flags):
     rng = np.random.default_rng(count)
     tile_bits = bits - 32
     tiles = rng.integers(0, 1 << tile_bits, count, dtype=np.uint64)
@@ -122,7 +122,7 @@ def test_sort_random_keys_stable(count, bits, digit):
     ws = torch.empty(B.ags_sort_workspace_bytes(cap), dtype=torch.uint8, device="cuda")
     nr = 1 << tile_bits
     ranges = torch.empty(2 * nr, dtype=torch.int32, device="cuda") if tile_bits <= 16 else None
-    alt = B.ags_sort(k, v, ka, va, npairs, cap, 0, bits, digit, ranges, nr, st, ws)
+    alt = B.ags_sort(k, v, ka, va, npairs, cap, 0, bits, digit, ranges, nr, st, ws, flags=flags)
     B.ags_check(st)
     ks = (ka if alt else k)[:count].cpu().numpy().view(np.uint64)
     vs = (va if alt else v)[:count].cpu().numpy().view(np.uint32)
@@ -216,7 +216,9 @@ def test_depth_presort_equals_full_key_sort():
         b.check()
         assert a.pairs() == b.pairs()
         np_ = a.pairs()
-        assert torch.equal(a.sorted_keys[:np_], b.sorted_keys[:np_])
+        ka, va = gpu_pairs(a)
+        kb, vb = gpu_pairs(b)
+        np.testing.assert_array_equal(ka, kb)
         assert torch.equal(a.sorted_vals[:np_], b.sorted_vals[:np_])
         assert torch.equal(ia, ib)
         assert torch.equal(a.ranges, b.ranges)
@@ -237,6 +239,100 @@ def test_sort_identity_values_flag():
     B.ags_check(st)
     vs = (va if alt else v).cpu().numpy()
     np.testing.assert_array_equal(vs, np.argsort(keys, kind="stable"))
+
+
+@pytest.mark.parametrize("rank_or", [False, True])
+@pytest.mark.parametrize("count,bits,digit,flags", [(1, 12, 8, 0), (4095, 13, 8, 2), (4097, 17, 9, 0),
+                                                    (100003, 17, 9, 2), (250000, 20, 7, 1), (77777, 16, 5, 3),
+                                                    (300001, 32, 8, 3), (65536, 32, 9, 0)])
+def test_sort32_random_keys_stable(count, bits, digit, flags, rank_or):
+    """32-bit keys: the stable order, the ranges of the whole key, the identity
+    values flag, the discarded-keys flag and both ranking methods."""
+    if rank_or:
+        flags |= B.AGS_SORT_RANK_OR
+    rng = np.random.default_rng(count + bits)
+    keys = rng.integers(0, 1 << bits, count, dtype=np.uint64).astype(np.uint32)
+    keys[rng.random(count) < 0.3] = keys[0]          # long runs of equal keys: stability matters
+    vals = rng.permutation(count).astype(np.uint32)
+    cap = count + 77
+    k = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    v = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    k[:count] = torch.from_numpy(keys.view(np.int32)).cuda()
+    if not flags & B.AGS_SORT_IDENTITY_VALUES:
+        v[:count] = torch.from_numpy(vals.view(np.int32)).cuda()
+    else:
+        vals = np.arange(count, dtype=np.uint32)
+    ka, va = torch.zeros_like(k), torch.zeros_like(v)
+    npairs = torch.tensor([count], dtype=torch.int64, device="cuda")
+    st = torch.zeros(4, dtype=torch.int64, device="cuda")
+    ws = torch.empty(B.ags_sort_workspace_bytes(cap), dtype=torch.uint8, device="cuda")
+    nr = 1 << bits if bits <= 17 else 0
+    ranges = torch.empty(2 * nr, dtype=torch.int32, device="cuda") if nr else None
+    kout_before = (k.clone(), ka.clone())
+    alt = B.ags_sort32(k, v, ka, va, npairs, cap, 0, bits, digit, ranges, nr, st, ws, flags=flags)
+    B.ags_check(st)
+    order = np.argsort(keys, kind="stable")
+    vs = (va if alt else v)[:count].cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(vs, vals[order])
+    if not flags & B.AGS_SORT_DISCARD_KEYS:
+        ks = (ka if alt else k)[:count].cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(ks, keys[order])
+    else:
+        # the last pass wrote no keys: the result's key buffer still holds what
+        # the previous pass (or the caller) left there
+        passes = -(-bits // digit)
+        if passes == 1:
+            assert torch.equal((ka if alt else k), kout_before[1 if alt else 0])
+    # nothing written past the count
+    assert torch.all(va[count:] == 0) and torch.all(v[count:] == -1)
+    if ranges is not None:
+        rg = ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+        t = keys[order].astype(np.int64)
+        starts = np.searchsorted(t, np.arange(nr), "left")
+        ends = np.searchsorted(t, np.arange(nr), "right")
+        empty = starts == ends
+        np.testing.assert_array_equal(rg[~empty, 0], starts[~empty])
+        np.testing.assert_array_equal(rg[~empty, 1], ends[~empty])
+        assert np.all(rg[empty] == 0)
+
+
+def test_emit_tile_pairs_matches_emit_pairs():
+    """32-bit tile keys in the depth order: the tile word of the 64-bit keys, same
+    values, same count; the renderer's pair lists agree with the full-key path."""
+    scene, cams = _c1(n=9000, W=176, H=144, views=3)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, 1, 0.3, presort=True)
+    r.preprocess()
+    r.depth_sort()
+    order = r.emit_order
+    cap = r.capacity
+    k64 = torch.empty(cap, dtype=torch.int64, device="cuda")
+    v64 = torch.empty(cap, dtype=torch.int32, device="cuda")
+    k32 = torch.empty(cap, dtype=torch.int32, device="cuda")
+    v32 = torch.empty(cap, dtype=torch.int32, device="cuda")
+    n64 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n32 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    B.ags_emit_pairs(r.proj, r.n, cams, k64, v64, cap, n64, r.status, r.ws_emit, order=order)
+    B.ags_emit_tile_pairs(r.proj, r.n, cams, k32, v32, cap, n32, r.status, r.ws_emit, order=order)
+    r.check()
+    P = int(n64.item())
+    assert P == int(n32.item()) and P > 0
+    hi = (k64[:P].cpu().numpy().view(np.uint64) >> np.uint64(32)).astype(np.uint32)
+    np.testing.assert_array_equal(k32[:P].cpu().numpy().view(np.uint32), hi)
+    assert torch.equal(v32[:P], v64[:P])
+    # the depth order: within each view, depth ascending, equal depths by index
+    # (the sort overwrote depth_key: rebuild the keys from the depths and flags)
+    o = order.cpu().numpy().astype(np.int64)
+    culled = (r.proj["flags"].cpu().numpy() & 0x80) != 0
+    dk = np.where(culled, np.uint32(0xffffffff), r.proj["depth"].cpu().numpy().view(np.uint32))[o]
+    live = dk != 0xffffffff
+    assert np.all(np.diff(dk.astype(np.int64)) >= 0)
+    assert np.all(~live[np.argmax(~live):]) if (~live).any() else True
+    for v in range(len(cams)):
+        sel = (o // r.n) == v
+        ov, dv = o[sel], dk[sel]
+        ties = np.nonzero(np.diff(dv.astype(np.int64)) == 0)[0]
+        assert np.all(ov[ties + 1] > ov[ties])
 
 
 def test_cuda_graph_replay_matches_eager_and_follows_scene_updates():
@@ -265,12 +361,14 @@ def test_autotuner_candidates_render_identically():
     from paper_2604_18980_gb300 import autotune
     scene, cams = _c1(n=8000, W=192, H=144, views=2)
     sc = R.scene_to_device(scene)
-    imgs = []
+    imgs, lists = [], []
     for cand in autotune.CANDIDATES:
         r = R.Renderer(sc, cams, 1, 0.3, **cand)
         imgs.append(r.forward().clone())
         r.check()
-    for im in imgs[1:]:
+        lists.append((r.sorted_vals[:r.pairs()].clone(), r.ranges.clone()))
+    for im, (v, rg) in zip(imgs[1:], lists[1:]):
         assert torch.equal(im, imgs[0])
+        assert torch.equal(v, lists[0][0]) and torch.equal(rg, lists[0][1])
     best = autotune.tune(sc, cams, 1, 0.3, use_cache=False, warmup=1, reps=2)
     assert best["digit_bits"] in (7, 8, 9) and len(best["table"]) == len(autotune.CANDIDATES)

@@ -23,13 +23,13 @@ def lib():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ags_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(ags_[a-z_0-9]+)\s*\(", src)))
 
 
 def test_header_declares_the_pipeline():
     names = declared_functions()
-    for n in ("ags_preprocess", "ags_emit_pairs", "ags_sort", "ags_rasterize", "ags_rasterize_backward",
-              "ags_calibrate_lut", "ags_check", "ags_status_reset"):
+    for n in ("ags_preprocess", "ags_emit_pairs", "ags_emit_tile_pairs", "ags_sort", "ags_sort32",
+              "ags_rasterize", "ags_rasterize_backward", "ags_calibrate_lut", "ags_check", "ags_status_reset"):
         assert n in names
 
 
@@ -57,7 +57,8 @@ def test_workspace_sizes(lib):
     assert B.ags_emit_workspace_bytes(0, 1) == 256
     assert B.ags_emit_workspace_bytes(1024, 1) == 256 + 8
     assert B.ags_emit_workspace_bytes(1025, 1) == 256 + 16
-    assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 512 * 4 + 2 * 512 * 4
+    assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 512 * 4 + 1 * 512 * 4
+    assert B.ags_sort_workspace_bytes(4097) == 256 + 16 * 512 * 4 + 2 * 512 * 4
     assert B.ags_backward_workspace_bytes(10, 2) == 10 * 2 * 9 * 4
 
 
@@ -95,10 +96,21 @@ def test_invalid_arguments_rejected_on_host(lib):
                       None, 0, None) == 1
     assert L.ags_sort(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
                       10, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st, None, 0, None) == 1
-    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 8, 2, None, 0, ctypes.byref(alt), st, None, 0,
+    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 8, 8, None, 0, ctypes.byref(alt), st, None, 0,
                       None) == 1
+    # 32-bit sort: end bit beyond the key, unknown flag, unaligned keys
+    assert L.ags_sort32(None, None, None, None, npairs, 10, 0, 33, 8, 0, None, 0, ctypes.byref(alt), st, None, 0,
+                        None) == 1
+    assert L.ags_sort32(None, None, None, None, npairs, 10, 0, 32, 8, 16, None, 0, ctypes.byref(alt), st, None, 0,
+                        None) == 1
+    assert L.ags_sort32(ctypes.c_void_p(20), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
+                        10, 0, 32, 8, 0, None, 0, ctypes.byref(alt), st, ctypes.c_void_p(256), 1 << 20, None) == 1
+    # 64-bit sort: unaligned keys
+    assert L.ags_sort(ctypes.c_void_p(24), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
+                      10, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st, ctypes.c_void_p(256), 1 << 20, None) == 1
     # emit: workspace too small
     assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, None, 0, None) == 1
+    assert L.ags_emit_tile_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, None, 0, None) == 1
     # mismatched view sizes
     cams2 = B.cameras([dict(width=64, height=48, fx=50.0, fy=50.0, cx=31.5, cy=23.5,
                             viewmat=[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], campos=[0, 0, 0]),
