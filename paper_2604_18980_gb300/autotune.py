@@ -59,7 +59,7 @@ def tune(scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_ADAGSCALE, K: fl
     table = []
     capacity = None
     for cand in candidates or CANDIDATES:
-        r = R.Renderer(scene, cams, scale_mode, K, lut, capacity=capacity, **cand)
+        r = R.Renderer(scene, cams, scale_mode, K, lut, capacity=capacity, keep_state=False, **cand)
         capacity = r.capacity
         ms = _time_forward(r, warmup, reps)
         table.append(dict(cand, ms=ms))

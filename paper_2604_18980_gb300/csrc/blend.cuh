@@ -8,9 +8,9 @@
 // Eq. 1 is alpha = min(alpha_max, tau 2^q); alpha >= tau is q >= 0 and p <= 0 is
 // q <= base, so the threshold test runs before the exponential.
 //
-// Each CTA blends one 16x16 tile with eight warps; warp w owns the 4x8 pixel
-// block rows 4*(w>>1).., columns 8*(w&1)...  For every staged splat the loading
-// thread also computes which of the eight blocks can hold a pixel with
+// The blend and its adjoint cover a 16x16 tile with four warps; warp w owns
+// the 8x8 pixel block rows 8*(w>>1).., columns 8*(w&1)...  For every staged
+// splat the loading thread also computes which of the blocks can hold a pixel with
 // alpha >= tau: its ellipse p >= ln(tau/opacity) must reach the block's
 // rectangle of pixel centres -- a bounding-box test (half-widths
 // sqrt(2 ln(opacity/tau) Sigma_xx), sqrt(2 ln(opacity/tau) Sigma_yy)) and then
@@ -26,7 +26,6 @@
 
 namespace ags {
 
-constexpr int kRasterThreads = kTile * kTile;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -104,13 +103,6 @@ __device__ __forceinline__ void stage_splat(const float4* rec, int tx0, int ty0,
         mask |= 1u << w;
     }
   }
-}
-
-// Pixel of thread `tid` within its tile: warp w covers a 4x8 block.
-__device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
-  const int w = tid >> 5, lane = tid & 31;
-  lx = 8 * (w & 1) + (lane & 7);
-  ly = 4 * (w >> 1) + (lane >> 3);
 }
 
 // q = log2(opacity e^p / tau) at pixel offset (dx, dy); explicit roundings.

@@ -19,13 +19,35 @@ namespace ags {
 
 // 128 threads per tile, four warps of 8x8 pixels; lane l blends the two
 // pixels (8*(w&1) + (l&7), 8*(w>>1) + (l>>3)) and the one 4 rows below, which
-// share dx.  kStats: count evaluations and blends; kMaxT: calibration output.
-// The benchmark's kernel is the <false, false> instance.
+// share dx.  kStats: count evaluations and blends; kMaxT: calibration output;
+// kState: track each pixel's last blended position (n_contrib, for the
+// backward).  The benchmark's kernel is the <false, false, false> instance.
 constexpr int kBlendThreads = 128;
 constexpr int kBlendWarps = kBlendThreads / 32;
 
-template <bool kStats, bool kMaxT>
-__global__ void __launch_bounds__(kBlendThreads)
+// One pixel's step over one splat, without branches: the accept test, the
+// stop test T (1 - alpha) < t_min and the blend are predicates, and a pixel
+// that does not blend adds exact zeros.  Returns whether it blended.
+__device__ __forceinline__ bool blend_pixel(const Staged& s, float cb, float P, float Bx, float dy,
+                                            const BlendConst& bc, bool& done, float& T, float& r, float& g,
+                                            float& b) {
+  const float q = splat_qy(s, P, Bx, dy);
+  const bool ok = !done && splat_accept(q, s.b.y);
+  const float alpha = fminf(bc.alpha_max, __fmul_rn(bc.tau, fast_exp2(q)));
+  const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+  const bool stop = ok && test_T < bc.t_min;
+  const bool blend = ok && !stop;
+  done = done || stop;
+  const float w = blend ? __fmul_rn(alpha, T) : 0.f;
+  r = __fmaf_rn(s.b.z, w, r);
+  g = __fmaf_rn(s.b.w, w, g);
+  b = __fmaf_rn(cb, w, b);
+  T = blend ? test_T : T;
+  return blend;
+}
+
+template <bool kStats, bool kMaxT, bool kState>
+__global__ void __launch_bounds__(kBlendThreads, kState ? 8 : 9)
 raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
               int W, int H, int gx, int tiles_per_view, BlendConst bc, float* __restrict__ image,
               float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ max_T_bits,
@@ -102,48 +124,16 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
         const float dx = __fsub_rn(s.a.x, fpx);
         float P, Bx;
         splat_qx(s, dx, P, Bx);
-        const uint32_t pos1 = bb - start + j + 1;
-        bool bl0 = false, bl1 = false;
+        const float cb = s_c[j];
         const float Tb0 = T0, Tb1 = T1;
-        if (!done0) {
-          if (kStats) evals += (j != kPad);
-          const float q = splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy0));
-          if (splat_accept(q, s.b.y)) {
-            const float alpha = fminf(bc.alpha_max, __fmul_rn(bc.tau, fast_exp2(q)));
-            const float test_T = __fmul_rn(T0, __fsub_rn(1.f, alpha));
-            if (test_T < bc.t_min) {
-              done0 = true;
-            } else {
-              const float w = __fmul_rn(alpha, T0);
-              r0 = __fmaf_rn(s.b.z, w, r0);
-              g0 = __fmaf_rn(s.b.w, w, g0);
-              b0c = __fmaf_rn(s_c[j], w, b0c);
-              T0 = test_T;
-              last0 = pos1;
-              bl0 = true;
-              if (kStats) blends++;
-            }
-          }
-        }
-        if (!done1) {
-          if (kStats) evals += (j != kPad);
-          const float q = splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy1));
-          if (splat_accept(q, s.b.y)) {
-            const float alpha = fminf(bc.alpha_max, __fmul_rn(bc.tau, fast_exp2(q)));
-            const float test_T = __fmul_rn(T1, __fsub_rn(1.f, alpha));
-            if (test_T < bc.t_min) {
-              done1 = true;
-            } else {
-              const float w = __fmul_rn(alpha, T1);
-              r1 = __fmaf_rn(s.b.z, w, r1);
-              g1 = __fmaf_rn(s.b.w, w, g1);
-              b1c = __fmaf_rn(s_c[j], w, b1c);
-              T1 = test_T;
-              last1 = pos1;
-              bl1 = true;
-              if (kStats) blends++;
-            }
-          }
+        if (kStats) evals += (j != kPad) * ((done0 ? 0u : 1u) + (done1 ? 0u : 1u));
+        const bool bl0 = blend_pixel(s, cb, P, Bx, __fsub_rn(s.a.y, fpy0), bc, done0, T0, r0, g0, b0c);
+        const bool bl1 = blend_pixel(s, cb, P, Bx, __fsub_rn(s.a.y, fpy1), bc, done1, T1, r1, g1, b1c);
+        if (kStats) blends += (bl0 ? 1u : 0u) + (bl1 ? 1u : 0u);
+        if (kState) {
+          const uint32_t pos1 = bb - start + j + 1;
+          last0 = bl0 ? pos1 : last0;
+          last1 = bl1 ? pos1 : last1;
         }
         if (kMaxT) {   // calibration: per-Gaussian max T before blending (warp max, one atomic)
           const uint32_t mine = max(bl0 ? __float_as_uint(Tb0) : 0u, bl1 ? __float_as_uint(Tb1) : 0u);
@@ -162,7 +152,7 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
     image[o + 2 * hw] = b0c + T0 * bc.bg[2];
     const size_t op = (size_t)view * hw + (size_t)py0 * W + px;
     if (final_T) final_T[op] = T0;
-    if (n_contrib) n_contrib[op] = last0;
+    if (kState) n_contrib[op] = last0;
   }
   if (in1) {
     const size_t o = (size_t)view * 3 * hw + (size_t)py1 * W + px;
@@ -171,7 +161,7 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
     image[o + 2 * hw] = b1c + T1 * bc.bg[2];
     const size_t op = (size_t)view * hw + (size_t)py1 * W + px;
     if (final_T) final_T[op] = T1;
-    if (n_contrib) n_contrib[op] = last1;
+    if (kState) n_contrib[op] = last1;
   }
   if (kStats) {
     unsigned long long e1 = warp_sum((unsigned long long)evals), e2 = warp_sum((unsigned long long)blends);
@@ -221,8 +211,10 @@ extern "C" ags_status ags_rasterize(const ags_projected* proj, int64_t n, const 
   if ((uintptr_t)proj->splat & 15u) return AGS_ERR_INVALID_ARG;
   const int tiles_per_view = cb.c[0].gx * cb.c[0].gy;
   BlendConst bc = make_blend_const(dp);
-  auto kern = stats ? (max_T ? raster_kernel<true, true> : raster_kernel<true, false>)
-                    : (max_T ? raster_kernel<false, true> : raster_kernel<false, false>);
+  auto kern = n_contrib ? (stats ? (max_T ? raster_kernel<true, true, true> : raster_kernel<true, false, true>)
+                                 : (max_T ? raster_kernel<false, true, true> : raster_kernel<false, false, true>))
+                       : (stats ? (max_T ? raster_kernel<true, true, false> : raster_kernel<true, false, false>)
+                                : (max_T ? raster_kernel<false, true, false> : raster_kernel<false, false, false>));
   kern<<<(unsigned)(tiles_per_view * views), kBlendThreads, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const float4*>(proj->splat), sorted_vals, reinterpret_cast<const uint2*>(ranges),
       cb.c[0].W, cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, image, final_T, n_contrib,

@@ -50,7 +50,7 @@ class Renderer:
     def __init__(self, scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_PLAIN, K: float = 0.0, lut=None,
                  sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 9,
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
-                 presort: bool = True, pair_rank_or: bool = True):
+                 presort: bool = True, pair_rank_or: bool = True, keep_state: bool = True):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -61,6 +61,7 @@ class Renderer:
         self.digit_bits = digit_bits
         self.presort = presort
         self.pair_rank_or = pair_rank_or
+        self.keep_state = keep_state or want_backward   # final_T / n_contrib for the backward
         self.set_params(scale_mode, K, lut, sh_degree, bg)
         dev, V, n = self.device, self.V, self.n
         self.proj = dict(splat=torch.empty(V * n * 12, dtype=torch.float32, device=dev),
@@ -83,8 +84,8 @@ class Renderer:
         self.ws_emit = torch.empty(max(B.ags_emit_workspace_bytes(n, V), 16), dtype=torch.uint8, device=dev)
         self.ranges = torch.empty(V * self.T * 2, dtype=torch.int32, device=dev)
         self.image = torch.empty(V, 3, self.H, self.W, dtype=torch.float32, device=dev)
-        self.final_T = torch.empty(V, self.H, self.W, dtype=torch.float32, device=dev)
-        self.n_contrib = torch.empty(V, self.H, self.W, dtype=torch.int32, device=dev)
+        self.final_T = torch.empty(V, self.H, self.W, dtype=torch.float32, device=dev) if self.keep_state else None
+        self.n_contrib = torch.empty(V, self.H, self.W, dtype=torch.int32, device=dev) if self.keep_state else None
         self.stats = torch.zeros(2, dtype=torch.int64, device=dev) if want_stats else None
         if capacity is None:
             capacity = max(1024, int(math.ceil(self.count_pairs() * headroom)))
@@ -205,6 +206,8 @@ class Renderer:
         return graph
 
     def backward(self, dL_dimage: torch.Tensor, grads: dict | None = None) -> dict:
+        if not self.keep_state:
+            raise RuntimeError("this renderer was built with keep_state=False: its forward keeps no blend state")
         if self.ws_bwd is None:
             self.ws_bwd = torch.empty(B.ags_backward_workspace_bytes(self.n, self.V), dtype=torch.uint8,
                                       device=self.device)
