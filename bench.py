@@ -42,12 +42,12 @@ FALLBACK_HBM_GBS = 6800.0
 # 1 - alpha and the transmittance product (2); the three colour FMAs and
 # alpha*T (4) = 18.  The exponential itself runs on the SFU.
 RASTER_OPS_PER_EVAL = 18
-# DRAM bytes (read + write) of one raster_kernel<false,false> launch per view of
-# this workload, from the ncu capture summarised in
-# profiles/raster_kernel_c2_clusters1m_1080p_1view.md (1 view; the kernel's
-# traffic grows with the number of views it renders).  Set to None whenever the
-# kernel changes until it is captured again.
-RASTER_TRAFFIC_PER_VIEW = 16.785664e6 + 0.7872e6
+# DRAM bytes (read + write) of one raster_kernel<false,false,false> launch per
+# view of this workload, from the ncu capture summarised in
+# profiles/raster_kernel_c2_clusters1m_1080p_6views.md ((108.18 + 108.41) MB over
+# 6 views; the kernel's traffic grows with the number of views it renders).  Set
+# to None whenever the kernel changes until it is captured again.
+RASTER_TRAFFIC_PER_VIEW = (108.179456e6 + 108.414976e6) / 6
 
 
 def parse():
@@ -499,7 +499,7 @@ def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):
         traffic = None if RASTER_TRAFFIC_PER_VIEW is None else RASTER_TRAFFIC_PER_VIEW * V
         return {"kernel": "raster_kernel", "bound": "alu", "achieved": achieved, "peak": peak_ops,
                 "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read+write of a 1-view capture x views",
+                "traffic_source": "ncu dram__bytes_read+write of a 6-view capture / 6 x views",
                 "work": "%d pixel-pair evaluations x %d FP32 ops" % (evals, RASTER_OPS_PER_EVAL),
                 "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (%s)" % (sms, sm_mhz, pk_src)}
     hbm = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
