@@ -34,6 +34,15 @@ if ROOT not in sys.path:
 
 WORKLOAD = "c2_clusters1m_1080p"
 METRIC = "FPS (AdaGScale, 1M Gaussians, 1920x1080, 10 poses)"
+# K values of the sweep reported beside the calibrated K (plus K itself)
+K_SWEEP = (0.0, 0.1, 0.3, 1.0, 3.0, 10.0)
+
+
+def metric_for(workload: str, n: int, W: int, H: int, V: int) -> str:
+    if workload == WORKLOAD:
+        return METRIC
+    return "FPS (AdaGScale, %s Gaussians, %dx%d, %d views)" % (
+        ("%dM" % (n >> 20)) if n >= 1 << 20 else ("%dK" % (n >> 10)), W, H, V)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP32 work per pixel-pair evaluation of Eq. 1-2 counted as the FP32-pipe
@@ -58,7 +67,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/backward legs")
-    ap.add_argument("--views", type=int, default=10, help="views per step (profiling cases use fewer)")
+    ap.add_argument("--views", type=int, default=None, help="views per step (default: all of the workload's poses)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="named workload (default: the benchmark configuration); the other configurations "
+                         "give lines for the results table")
     ap.add_argument("--profile", action="store_true",
                     help="no timing: run one forward (with one view, also one forward + backward) inside a "
                          "profiler range for `ncu --profile-from-start off`, then exit")
@@ -128,7 +140,7 @@ def device_uuid():
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(scene, cam, par_kwargs, frames: int = 1) -> dict:
+def cpu_baseline(scene, cam, par_kwargs, workload=WORKLOAD, frames: int = 1) -> dict:
     """The FP64 oracle on the host cores: `frames` full frames of the workload."""
     import oracle
     par = oracle.params(cam, **par_kwargs)
@@ -137,7 +149,8 @@ def cpu_baseline(scene, cam, par_kwargs, frames: int = 1) -> dict:
         oracle.render(scene, cam, par)
     dt = time.perf_counter() - t0
     return {"value": frames / dt, "unit": "FPS", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "%d full frame(s) (pose 0, 1920x1080, 1,048,576 Gaussians), FP64, OpenMP over tiles" % frames,
+            "sample": "%d full frame(s) of %s (pose 0, %dx%d, %d Gaussians), FP64, OpenMP over tiles" % (
+                frames, workload, cam["width"], cam["height"], scene["opacity_logit"].shape[0]),
             "seconds": dt}
 
 
@@ -147,13 +160,14 @@ def oracle_kwargs(wp):
                 tau=float(np.float32(1 / 255)), t_min=float(np.float32(1e-4)), alpha_max=float(np.float32(0.99)))
 
 
-def workload_params(sc, calib):
+def workload_params(sc, calib, workload=WORKLOAD):
     from paper_2604_18980_gb300 import calibrate as C
-    wp = C.load_params(WORKLOAD)
+    wp = C.load_params(workload)
     if wp is None:
         lut = C.calibrate_lut(sc, calib)
-        K, p = C.search_K(sc, calib, lut, C.TARGET_PSNR["c2"])
-        wp = dict(K=float(K), lut=[float(x) for x in lut], target_psnr=C.TARGET_PSNR["c2"], calib_psnr=p,
+        target = C.TARGET_PSNR[workload[:2]]
+        K, p = C.search_K(sc, calib, lut, target)
+        wp = dict(K=float(K), lut=[float(x) for x in lut], target_psnr=target, calib_psnr=p,
                   source="calibrated in this run")
     else:
         wp = dict(wp, source="workload_params.json")
@@ -169,11 +183,13 @@ def run_reference(args, world, rank):
     from paper_2604_18980_gb300 import calibrate as C
     from paper_2604_18980_gb300 import synth
     import oracle
-    wp = C.load_params(WORKLOAD)
+    workload = args.workload
+    wp = C.load_params(workload)
     if wp is None:
         print(json.dumps({"impl": "reference", "unavailable": "workload_params.json (K, T_up) not present"}))
         return 0
-    scene, cams, _ = synth.workload(WORKLOAD)
+    scene, cams, _ = synth.workload(workload)
+    cams = cams[:args.views] if args.views else cams
     kw = oracle_kwargs(wp)
     times = []
     for s in range(args.warmup + args.steps):
@@ -185,13 +201,16 @@ def run_reference(args, world, rank):
             times.append(time.perf_counter() - t0)
     tot = sum(times)
     fps = len(times) / tot
-    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "FPS", "n_gpus": args.gpus,
+    n = int(scene["opacity_logit"].shape[0])
+    W, H = cams[0]["width"], cams[0]["height"]
+    line = {"impl": "reference", "metric": metric_for(workload, n, W, H, len(cams)), "value": fps, "unit": "FPS",
+            "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "gaussians": 1048576, "width": 1920, "height": 1080,
-                       "views": 10, "scale_mode": "adagscale", "K": wp["K"], "step": "one frame per step"},
+            "config": {"workload": workload, "gaussians": n, "width": W, "height": H,
+                       "views": len(cams), "scale_mode": "adagscale", "K": wp["K"], "step": "one frame per step"},
             "cpu_baseline": {"value": fps, "unit": "FPS", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": "one full 1920x1080 frame per step, poses cycled"},
+                             "sample": "one full %dx%d frame per step, poses cycled" % (W, H)},
             "e2e": {"value": fps, "unit": "FPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -213,10 +232,11 @@ def run_ours(args, world, rank, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     cuda_build.build()
-    scene_np, cams, calib = synth.workload(WORKLOAD)
-    cams = cams[:args.views]
+    workload = args.workload
+    scene_np, cams, calib = synth.workload(workload)
+    cams = cams[:args.views] if args.views else cams
     sc = R.scene_to_device(scene_np)
-    wp = workload_params(sc, calib)
+    wp = workload_params(sc, calib, workload)
     V = len(cams)
     # launch parameters from the autotuner (untimed set-up; identical results for every candidate)
     from paper_2604_18980_gb300 import autotune
@@ -224,7 +244,6 @@ def run_ours(args, world, rank, local):
     knobs = dict(digit_bits=tuned["digit_bits"], presort=tuned["presort"], pair_rank_or=tuned["pair_rank_or"])
     ada = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_stats=True, keep_state=False,
                      **knobs)
-    plain = R.Renderer(sc, cams, B.AGS_SCALE_PLAIN, keep_state=False, **knobs)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -314,24 +333,57 @@ def run_ours(args, world, rank, local):
 
     extras = {}
     if not args.no_extras:
-        # plain 3-sigma on the same GPU
+        # plain 3-sigma on the same GPU (view by view when the batch exceeds one sort's pair limit)
+        try:
+            plains = [R.Renderer(sc, cams, B.AGS_SCALE_PLAIN, keep_state=False, **knobs)]
+        except ValueError:
+            plains = [R.Renderer(sc, [c], B.AGS_SCALE_PLAIN, keep_state=False, **knobs) for c in cams]
         for _ in range(args.warmup):
-            plain.forward()
+            for pr in plains:
+                pr.forward()
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(args.steps):
-            plain.forward()
+            for pr in plains:
+                pr.forward()
         b.record(stream)
         barrier()
-        plain.check()
+        for pr in plains:
+            pr.check()
         plain_ms = max_over_ranks(a.elapsed_time(b)) / args.steps
+        plain_pairs = sum(pr.pairs() for pr in plains)
         extras["plain"] = {"fps": world * V * 1000.0 / plain_ms, "ms_per_step": plain_ms,
-                           "pairs_per_frame": plain.pairs() / V}
+                           "pairs_per_frame": plain_pairs / V, "batches": len(plains)}
         img_a = ada.forward().clone()
-        img_p = plain.forward().clone()
+        img_p = torch.cat([pr.forward().clone() for pr in plains])
         extras["psnr_adagscale_vs_plain_db"] = C.psnr(img_a, img_p)
-        del img_a, img_p
+        del img_a, plains
+
+        # K sweep: pairs per frame, PSNR against plain and FPS at each K (same LUT)
+        sweep = []
+        for k in sorted(set(K_SWEEP) | {float(wp["K"])}):
+            try:
+                rk = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, k, wp["lut"], keep_state=False, **knobs)
+            except ValueError:
+                sweep.append({"K": k, "skipped": "more pairs than one sort call takes"})
+                continue
+            img_k = rk.forward().clone()
+            for _ in range(2):
+                rk.forward()
+            barrier()
+            a.record(stream)
+            for _ in range(max(3, args.steps // 4)):
+                rk.forward()
+            b.record(stream)
+            barrier()
+            rk.check()
+            ms_k = max_over_ranks(a.elapsed_time(b)) / max(3, args.steps // 4)
+            sweep.append({"K": k, "pairs_per_frame": rk.pairs() / V, "psnr_vs_plain_db": C.psnr(img_k, img_p),
+                          "fps_eager": world * V * 1000.0 / ms_k})
+            del rk, img_k
+        extras["k_sweep"] = sweep
+        del img_p
 
         # end to end through host buffers: params H2D, render, images D2H, every step
         host = {k: v.cpu().pin_memory() for k, v in sc.items()}
@@ -392,10 +444,10 @@ def run_ours(args, world, rank, local):
     dom = max(stage_ms, key=stage_ms.get)
     roof = roofline(dom, stage_ms[dom], ada, evals_per_step, pk, pk_src, passes, clk)
     line = {
-        "metric": METRIC, "value": fps, "unit": "FPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": metric_for(workload, ada.n, ada.W, ada.H, V), "value": fps, "unit": "FPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; stands in for the paper's trained scenes)",
-        "config": {"workload": WORKLOAD, "gaussians": ada.n, "width": ada.W, "height": ada.H, "views_per_step": V,
+        "config": {"workload": workload, "gaussians": ada.n, "width": ada.W, "height": ada.H, "views_per_step": V,
                    "scale_mode": "adagscale", "K": wp["K"], "lut_source": wp.get("source"),
                    "pairs_per_frame": ada_pairs / V, "sort_passes": passes,
                    "l2": "inputs larger than L2 (params 236 MB, pair keys and values %.2f GB per sort pass)" % (
@@ -417,7 +469,7 @@ def run_ours(args, world, rank, local):
         line["e2e"] = extras["e2e"]
     if not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline(scene_np, cams[0], oracle_kwargs(wp))
+            line["cpu_baseline"] = cpu_baseline(scene_np, cams[0], oracle_kwargs(wp), workload)
         except Exception as exc:   # report, never fail the benchmark line
             line["cpu_baseline"] = {"value": None, "unit": "FPS", "kind": "oracle", "error": str(exc)}
     print(json.dumps(line))
