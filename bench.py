@@ -241,7 +241,8 @@ def run_ours(args, world, rank, local):
     # launch parameters from the autotuner (untimed set-up; identical results for every candidate)
     from paper_2604_18980_gb300 import autotune
     tuned = autotune.tune(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"])
-    knobs = dict(digit_bits=tuned["digit_bits"], presort=tuned["presort"], pair_rank_or=tuned["pair_rank_or"])
+    knobs = dict(digit_bits=tuned["digit_bits"], presort=tuned["presort"], pair_rank_or=tuned["pair_rank_or"],
+                 emit_two_pass=tuned.get("emit_two_pass", True))
     ada = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_stats=True, keep_state=False,
                      **knobs)
     stream = torch.cuda.current_stream()
@@ -455,8 +456,7 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
         "timing": "CUDA-graph replay of the whole forward per step; stage_ms from the same steps launched "
                   "eagerly with events between stages (eager %.3f ms/step)" % eager_ms,
-        "tuned": {"digit_bits": knobs["digit_bits"], "presort": knobs["presort"],
-                  "pair_rank_or": knobs["pair_rank_or"]},
+        "tuned": dict(knobs),
         "stage_ms": stage_ms,
         "stage_hbm": stage_frac,
         "roofline": roof,
@@ -523,13 +523,16 @@ def stage_bytes(stage, r, passes):
     if stage == "depth_sort":
         from paper_2604_18980_gb300.render import digit_plan
         dp = digit_plan(r.dsort_end, r.digit_bits)[0] if r.presort else 0
-        # 32-bit depth keys: histogram 4 B, each pass 16 B, minus the values the first
-        # pass does not read (identity) and the keys the last pass does not write
-        return (G * 4 + dp * G * 16 - G * 8) if dp else 0, "onesweep_kernel (depth keys, identity values)"
+        if not dp:
+            return 0, "onesweep_kernel (depth keys)"
+        # compaction: flags (1 B) and depth (4 B) of every Gaussian-view read, key and
+        # index (8 B) of the visible ones written; the sort of the visible ones:
+        # histogram 4 B, each pass 16 B, minus the keys the last pass does not write
+        return G * 5 + live * 8 + live * 4 + dp * live * 16 - live * 4, "visible_kernel + onesweep_kernel (depth keys)"
     if stage == "emit":
         if r.presort:
-            # order (4 B) and rectangle (8 B) per Gaussian; 8 B per pair (tile key, value)
-            return G * 12 + P * 8, "emit_kernel"
+            # order (4 B) and rectangle (8 B) per visible Gaussian-view; 8 B per pair (tile key, value)
+            return live * 12 + P * 8, "emit_kernel"
         # rectangle (8 B) per Gaussian, depth (4 B) per survivor; 12 B per pair
         return G * 8 + live * 4 + P * 12, "emit_kernel"
     # preprocess: 44 B geometry per Gaussian and 192 B SH per Gaussian that survives

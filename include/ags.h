@@ -174,19 +174,47 @@ ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32_t views,
                           int64_t* d_num_pairs, int64_t* d_status,
                           void* ws, size_t ws_bytes, void* stream);
 
+/* Scratch bytes needed by ags_emit_tile_pairs for views*n Gaussian-views
+ * (the look-back state and a 16-byte record per visited Gaussian-view). */
+size_t ags_emit_tile_workspace_bytes(int64_t n, int32_t views);
+
 /* Pair emission with 32-bit tile keys (Sec. 2.1, Sec. 3.3): ags_emit_pairs
  * with key = view * tiles_per_view + tile and no depth bits.  Pairs come out
  * in the order of `order`; when `order` is the stable depth order (a sort of
- * depth_key, see ags_projected), a stable sort of these keys (ags_sort32 over
- * their bits) yields exactly the per-tile lists that sorting the 64-bit
- * (tile | depth) keys of ags_emit_pairs yields: the tile, then the depth, then
- * the Gaussian index.  `proj->depth` is not read.  Workspace: as
- * ags_emit_pairs (ags_emit_workspace_bytes). */
+ * depth_key, or of the compacted keys of ags_compact_visible), a stable sort of
+ * these keys (ags_sort32 over their bits) yields exactly the per-tile lists
+ * that sorting the 64-bit (tile | depth) keys of ags_emit_pairs yields: the
+ * tile, then the depth, then the Gaussian index.  d_order_count (device int64,
+ * nullable; used only with `order`) is the number of entries of `order` to
+ * visit, at most views*n (default views*n).  `proj->depth` is not read.
+ * Two passes by default: counts, offsets and one record per visited
+ * Gaussian-view, then the pairs in blocks of a fixed number of pairs (balanced
+ * however the tile counts cluster in depth order); flags AGS_EMIT_SINGLE_PASS
+ * selects the single fused pass of ags_emit_pairs instead.  Same pairs either
+ * way.  Workspace: ags_emit_tile_workspace_bytes, 16-byte aligned. */
+#define AGS_EMIT_SINGLE_PASS 1  /* ags_emit_tile_pairs flag: one fused scan-and-emit pass over
+                                   partitions of Gaussian-views (faster when the tile counts
+                                   are spread evenly along the order) */
 ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, int32_t views,
                                const ags_camera* cams, const uint32_t* order,
-                               uint32_t* keys, uint32_t* vals, int64_t capacity,
-                               int64_t* d_num_pairs, int64_t* d_status,
-                               void* ws, size_t ws_bytes, void* stream);
+                               const int64_t* d_order_count, uint32_t* keys, uint32_t* vals,
+                               int64_t capacity, int64_t* d_num_pairs, int64_t* d_status,
+                               int32_t flags, void* ws, size_t ws_bytes, void* stream);
+
+/* Scratch bytes needed by ags_compact_visible for views*n Gaussian-views. */
+size_t ags_compact_workspace_bytes(int64_t n, int32_t views);
+
+/* The Gaussian-views with pairs (flags bit 7 clear), in increasing index
+ * e = view*n + i, with their depth keys: keys[k] = float_bits(depth[e]),
+ * ids[k] = e for k < *d_count (device int64, written).  Culled views never
+ * reach a tile list (Sec. 2.1 frustum cull, Sec. 3.3 Th > opacity cull), so the
+ * depth pre-sort (ags_sort32 of keys with ids as values, count d_count) needs
+ * only these.  Reads proj->flags and proj->depth (both 16-byte aligned);
+ * keys and ids hold up to views*n entries.  Single pass with a decoupled
+ * look-back (bounded spin). */
+ags_status ags_compact_visible(const ags_projected* proj, int64_t n, int32_t views, uint32_t* keys,
+                               uint32_t* ids, int64_t* d_count, int64_t* d_status, void* ws,
+                               size_t ws_bytes, void* stream);
 
 /* Largest views*n that ags_emit_pairs_noalloc accepts (2^24). */
 int64_t ags_emit_pairs_noalloc_max_gaussians(void);

@@ -3,8 +3,9 @@
 The knobs are the digit width of the radix sorts (7, 8 or 9 bits: fewer,
 wider passes against more contention and larger look-back tables), whether
 the Gaussians are depth-sorted before emission (the pair sort then runs only
-the tile digits, on 32-bit keys) and how the pair sort ranks a warp's equal
-digits (warp match, or atomic-OR peer masks in shared memory).  Every candidate renders the same frames through
+the tile digits, on 32-bit keys), how the pair sort ranks a warp's equal
+digits (warp match, or atomic-OR peer masks in shared memory) and whether the
+tile-key emission runs as one fused pass or as two passes balanced by pairs.  Every candidate renders the same frames through
 the same kernels -- results are identical -- and the fastest one (CUDA-event
 time of a whole forward, after warm-up) is kept.  Results are cached in a JSON
 file keyed by GPU name and workload shape.
@@ -20,8 +21,9 @@ from . import binding as B
 from . import render as R
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
-CANDIDATES = [dict(digit_bits=d, presort=p, pair_rank_or=o) for p in (True, False) for o in (True, False)
-              for d in (9, 8, 7)]
+CANDIDATES = ([dict(digit_bits=d, presort=True, pair_rank_or=o, emit_two_pass=t) for t in (True, False)
+               for o in (True, False) for d in (9, 8, 7)]
+              + [dict(digit_bits=d, presort=False, pair_rank_or=o) for o in (True, False) for d in (9, 8, 7)])
 
 
 def workload_key(scene: dict, cams: list, scale_mode: int) -> str:
@@ -66,7 +68,7 @@ def tune(scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_ADAGSCALE, K: fl
         del r
     best = min(table, key=lambda t: t["ms"])
     out = dict(digit_bits=best["digit_bits"], presort=best["presort"], pair_rank_or=best["pair_rank_or"],
-               ms=best["ms"], table=table)
+               emit_two_pass=best.get("emit_two_pass", True), ms=best["ms"], table=table)
     if use_cache:
         cache[key] = out
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)

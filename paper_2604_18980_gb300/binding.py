@@ -68,7 +68,11 @@ EXPORTS = {
     "ags_preprocess": ([_P, _P, _I32, _P, _P, _P, _P], _I32),
     "ags_emit_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
     "ags_emit_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P], _I32),
-    "ags_emit_tile_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P], _I32),
+    "ags_emit_tile_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _P, _I64, _P, _P, _I32, _P, ctypes.c_size_t, _P],
+                            _I32),
+    "ags_compact_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
+    "ags_emit_tile_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
+    "ags_compact_visible": ([_P, _I64, _I32, _P, _P, _P, _P, _P, ctypes.c_size_t, _P], _I32),
     "ags_emit_pairs_noalloc_max_gaussians": ([], _I64),
     "ags_emit_pairs_noalloc": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P], _I32),
     "ags_sort_workspace_bytes": ([_I64], ctypes.c_size_t),
@@ -225,14 +229,36 @@ def ags_emit_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, w
         "ags_emit_pairs")
 
 
-def ags_emit_tile_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, ws, order=None, stream=None):
-    """Pairs with 32-bit tile keys, emitted in `order` (normally the depth order)."""
+AGS_EMIT_SINGLE_PASS = 1
+
+
+def ags_emit_tile_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, ws, order=None,
+                        order_count=None, flags=0, stream=None):
+    """Pairs with 32-bit tile keys, emitted in `order` (normally the depth order);
+    `order_count` (device int64) limits the entries of `order` visited."""
     pr = projected(proj)
     cs = cameras(cams)
-    _ok(lib().ags_emit_tile_pairs(ctypes.byref(pr), int(n), len(cams), cs, ptr(order), ptr(keys), ptr(vals),
-                                  int(capacity), ptr(d_num_pairs), ptr(d_status), ptr(ws),
+    _ok(lib().ags_emit_tile_pairs(ctypes.byref(pr), int(n), len(cams), cs, ptr(order), ptr(order_count),
+                                  ptr(keys), ptr(vals),
+                                  int(capacity), ptr(d_num_pairs), ptr(d_status), int(flags), ptr(ws),
                                   ws.numel() * ws.element_size() if ws is not None else 0, stream_handle(stream)),
         "ags_emit_tile_pairs")
+
+
+def ags_emit_tile_workspace_bytes(n: int, views: int) -> int:
+    return int(lib().ags_emit_tile_workspace_bytes(int(n), int(views)))
+
+
+def ags_compact_workspace_bytes(n: int, views: int) -> int:
+    return int(lib().ags_compact_workspace_bytes(int(n), int(views)))
+
+
+def ags_compact_visible(proj, n, views, keys, ids, d_count, d_status, ws, stream=None):
+    """Depth keys and indices of the Gaussian-views with pairs, in index order; count in d_count."""
+    pr = projected(proj)
+    _ok(lib().ags_compact_visible(ctypes.byref(pr), int(n), int(views), ptr(keys), ptr(ids), ptr(d_count),
+                                  ptr(d_status), ptr(ws), ws.numel() * ws.element_size(), stream_handle(stream)),
+        "ags_compact_visible")
 
 
 def ags_emit_pairs_noalloc(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, order=None, stream=None):

@@ -15,7 +15,7 @@ constexpr uint8_t kFlagCulled = 0x80;
 constexpr uint64_t kWaitLimitNs = 200ull * 1000ull * 1000ull;   // bounded spin: 200 ms
 
 // Stage ids reported as the detail word of AGS_ERR_TIMEOUT.
-enum : int64_t { kStageEmit = 1, kStageSort = 2 };
+enum : int64_t { kStageEmit = 1, kStageSort = 2, kStageVisible = 3 };
 
 // ---------------------------------------------------------------------------
 // Camera and parameter blocks passed by value (__grid_constant__).

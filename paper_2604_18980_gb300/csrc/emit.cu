@@ -15,6 +15,7 @@
 //
 // The look-back spins are bounded (globaltimer); on expiry the status block
 // records AGS_ERR_TIMEOUT and every store stays inside `capacity`.
+#include <algorithm>
 #include <mutex>
 
 #include "ags_internal.cuh"
@@ -30,6 +31,8 @@ constexpr int kEmitStride = kEmitRun + 1;                 // padded staging row 
 constexpr uint64_t kAgg = 1ull << 62;
 constexpr uint64_t kInc = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
+constexpr int kTileChunk = 2048;                          // pairs per block of the two-pass emission
+constexpr int64_t kTileChunksMax = ((int64_t)AGS_MAX_PAIRS + kTileChunk - 1) / kTileChunk + 1;
 
 // Pair key of a tile: 64-bit keys append the depth bits, 32-bit keys are the tile alone.
 __device__ __forceinline__ void make_key(uint32_t tile, uint32_t dbits, uint64_t& k) {
@@ -40,9 +43,11 @@ __device__ __forceinline__ void make_key(uint32_t tile, uint32_t, uint32_t& k) {
 template <typename K>
 __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, const uint32_t* __restrict__ order,
-            int64_t total, uint32_t n, uint32_t tiles_per_view, uint32_t gx, K* __restrict__ keys,
+            int64_t total_bound, const int64_t* d_total, uint32_t n, uint32_t tiles_per_view, uint32_t gx,
+            K* __restrict__ keys,
             uint32_t* __restrict__ vals, int64_t capacity, int64_t* d_num_pairs, int64_t* status,
-            uint64_t* part_status, uint32_t* counter, uint32_t num_parts) {
+            uint64_t* part_status, uint32_t* counter, uint4* __restrict__ recs,
+            uint32_t* __restrict__ chunk_start) {
   __shared__ uint32_t s_base[kEmitPart];   // key high word of the rectangle's first tile
   __shared__ uint32_t s_w[kEmitPart];      // rectangle width in tiles
   __shared__ uint32_t s_dbits[kEmitPart];  // depth bits
@@ -56,6 +61,17 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
   if (tid == 0) s_part = atomicAdd(counter, 1u);
   __syncthreads();
   const uint32_t part = s_part;
+  // entries to visit: all views*n, or the count the device holds (a compacted order)
+  int64_t total = total_bound;
+  if (d_total) {
+    const int64_t t = *d_total;
+    total = t < 0 ? 0 : (t > total_bound ? total_bound : t);
+  }
+  const uint32_t nparts = (uint32_t)((total + kEmitPart - 1) / kEmitPart);
+  if (part >= nparts) {                       // beyond the entries: no pairs, nobody waits on it
+    if (part == 0 && tid == 0) *d_num_pairs = 0;
+    return;
+  }
   const int64_t base = (int64_t)part * kEmitPart;
 
   // 1. coalesced loads of the rectangles (striped), counts staged in s_off
@@ -150,6 +166,29 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
   __syncthreads();
   const uint64_t prefix = s_prefix;
 
+  if (recs) {
+    // two-phase emission: only the per-entry records {first pair, splat index,
+    // first tile key, width}; the pairs come from tile_emit_kernel
+#pragma unroll
+    for (int k = 0; k < kEmitItems; k++) {
+      const int li = k * kEmitThreads + tid;
+      if (base + li < total) {
+        const uint64_t off = prefix + s_off[li], end = prefix + s_off[li + 1];
+        recs[base + li] = make_uint4((uint32_t)off, s_idx[li], s_base[li], s_w[li]);
+        // this entry holds the first pair of every pair block starting inside it
+        const uint64_t lim = end < (uint64_t)capacity ? end : (uint64_t)capacity;
+        for (uint64_t c = (off + kTileChunk - 1) / kTileChunk * kTileChunk; c < lim; c += kTileChunk)
+          chunk_start[c / kTileChunk] = (uint32_t)(base + li);
+      }
+    }
+    if (part == nparts - 1 && tid == 0) {
+      const int64_t tot = (int64_t)(prefix + agg);
+      *d_num_pairs = tot;
+      if (tot > capacity) set_status(status, AGS_ERR_CAPACITY, tot);
+    }
+    return;
+  }
+
   // 4. load-balanced emission: warps take chunks of 256 consecutive pairs; each
   //    lane generates 8 consecutive pairs (one binary search, then walking the
   //    rectangle row by row) into a warp-private staging row, and the warp
@@ -195,10 +234,114 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
     }
     __syncwarp();
   }
-  if (part == num_parts - 1 && tid == 0) {
+  if (part == nparts - 1 && tid == 0) {
     int64_t tot = (int64_t)(prefix + agg);
     *d_num_pairs = tot;
     if (tot > capacity) set_status(status, AGS_ERR_CAPACITY, tot);
+  }
+}
+
+// Second phase of the tile-key emission: blocks over fixed ranges of 2048
+// pairs, whatever the pairs per Gaussian.  In depth order the large
+// Gaussians near the camera come together, and a fused scan-and-emit over
+// Gaussian partitions would leave a few blocks with most of the pairs.  The
+// first pass recorded which entry holds the first pair of each block; a block
+// stages the records its range touches, and its warps emit chunks of 256 pairs
+// (8 per lane, one shared-memory binary search each) with coalesced stores,
+// as the fused kernel does.  Entries without pairs (an order that lists culled
+// views) can push the records of a block past the staging area: the block then
+// continues with further windows, found by a 32-way search of the records'
+// first-pair offsets.
+struct TileEmitSmem {
+  uint4 rec[kTileChunk + 2];
+  uint32_t key[kEmitThreads / 32][32 * kEmitStride];
+  uint32_t val[kEmitThreads / 32][32 * kEmitStride];
+  uint32_t k0;
+};
+
+__global__ void __launch_bounds__(kEmitThreads)
+tile_emit_kernel(const uint4* __restrict__ recs, const uint32_t* __restrict__ chunk_start, const int64_t* d_entries,
+                 int64_t entries_bound, const int64_t* d_num_pairs, int64_t capacity, uint32_t gx,
+                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileEmitSmem& S = *reinterpret_cast<TileEmitSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int64_t ne = d_entries ? *d_entries : entries_bound;
+  ne = ne < 0 ? 0 : (ne > entries_bound ? entries_bound : ne);
+  int64_t np = *d_num_pairs;
+  np = np < 0 ? 0 : (np > capacity ? capacity : np);
+  const uint32_t nent = (uint32_t)ne, total = (uint32_t)np;
+  for (uint32_t b = blockIdx.x; (uint64_t)b * kTileChunk < total; b += gridDim.x) {
+    const uint32_t c0 = b * (uint32_t)kTileChunk;
+    const uint32_t cend = min(c0 + (uint32_t)kTileChunk, total);
+    uint32_t cs = c0;
+    bool first = true;
+    while (cs < cend) {
+      if (first) {
+        if (tid == 0) S.k0 = min(__ldg(chunk_start + b), nent - 1u);
+      } else if (warp == 0) {   // the last record whose first pair is <= cs
+        uint32_t lo = 0, hi = nent;                // answer in [lo, hi); record 0 starts at pair 0
+        while (hi - lo > 32) {
+          const uint32_t step = (hi - lo + 31) / 32;
+          const uint32_t idx = lo + (uint32_t)lane * step;
+          const unsigned bal = __ballot_sync(0xffffffffu, idx < hi && __ldg(&recs[idx].x) <= cs);
+          lo = lo + (uint32_t)(31 - __clz(bal)) * step;   // lane 0 probes lo itself, so bal != 0
+          hi = min(hi, lo + step);
+        }
+        const uint32_t idx = lo + (uint32_t)lane;
+        const unsigned bal = __ballot_sync(0xffffffffu, idx < hi && __ldg(&recs[idx].x) <= cs);
+        if (lane == 0) S.k0 = lo + (uint32_t)(31 - __clz(bal));
+      }
+      first = false;
+      __syncthreads();
+      const uint32_t k0 = S.k0;
+      const uint32_t m = min((uint32_t)kTileChunk + 1u, nent - k0);
+      for (uint32_t q = tid; q <= m; q += kEmitThreads)
+        S.rec[q] = (k0 + q < nent) ? __ldg(&recs[k0 + q]) : make_uint4(total, 0u, 0u, 1u);
+      __syncthreads();
+      const uint32_t wend = min(cend, S.rec[m].x);   // pairs this window covers: [cs, wend)
+      const uint32_t cn = wend > cs ? wend - cs : 0u;
+      for (uint32_t w0 = (uint32_t)warp * kEmitChunk; w0 < cn; w0 += (kEmitThreads / 32) * kEmitChunk) {
+        const uint32_t j0 = cs + w0 + (uint32_t)lane * kEmitRun;
+        if (j0 < wend) {
+          int lo = 0, hi = (int)m;                 // invariant: rec[lo].x <= j0 < rec[hi].x
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (S.rec[mid].x <= j0) lo = mid; else hi = mid;
+          }
+          uint4 rc = S.rec[lo];
+          uint32_t nxt = S.rec[lo + 1].x;
+          const uint32_t r = j0 - rc.x;
+          uint32_t ry = r / rc.w, rx = r - ry * rc.w;
+#pragma unroll
+          for (int k = 0; k < kEmitRun; k++) {
+            const uint32_t j = j0 + k;
+            if (j >= wend) break;
+            while (j >= nxt) {                     // next record with pairs (j < wend <= rec[m].x)
+              lo++;
+              rc = S.rec[lo];
+              nxt = S.rec[lo + 1].x;
+              rx = 0;
+              ry = 0;
+            }
+            S.key[warp][lane * kEmitStride + k] = rc.z + ry * gx + rx;
+            S.val[warp][lane * kEmitStride + k] = rc.y;
+            if (++rx == rc.w) { rx = 0; ry++; }
+          }
+        }
+        __syncwarp();
+        const uint32_t nval = min((uint32_t)kEmitChunk, cn - w0);
+        for (uint32_t q = lane; q < nval; q += 32) {
+          const uint32_t pos = cs + w0 + q;
+          const uint32_t si = (q / kEmitRun) * kEmitStride + (q % kEmitRun);
+          keys[pos] = S.key[warp][si];
+          vals[pos] = S.val[warp][si];
+        }
+        __syncwarp();
+      }
+      cs = wend > cs ? wend : cend;                    // always progresses on consistent records
+      __syncthreads();
+    }
   }
 }
 
@@ -235,15 +378,22 @@ extern "C" ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
   uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
   emit_kernel<uint64_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
-      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, (uint32_t)n, tiles_per_view,
-      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, (uint32_t)parts);
+      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, nullptr, (uint32_t)n, tiles_per_view,
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr);
   return launch_status(cudaGetLastError());
 }
 
+extern "C" size_t ags_emit_tile_workspace_bytes(int64_t n, int32_t views) {
+  if (n < 0 || views < 1) return 0;
+  const int64_t total = n * (int64_t)views;
+  return (256 + 8 * ags::emit_parts(total) + 15) / 16 * 16 + 16 * (size_t)total + 4 * (size_t)ags::kTileChunksMax;
+}
+
 extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, int32_t views,
-                                          const ags_camera* cams, const uint32_t* order, uint32_t* keys,
-                                          uint32_t* vals, int64_t capacity, int64_t* d_num_pairs, int64_t* d_status,
-                                          void* ws, size_t ws_bytes, void* stream) {
+                                          const ags_camera* cams, const uint32_t* order,
+                                          const int64_t* d_order_count, uint32_t* keys, uint32_t* vals,
+                                          int64_t capacity, int64_t* d_num_pairs, int64_t* d_status,
+                                          int32_t flags, void* ws, size_t ws_bytes, void* stream) {
   using namespace ags;
   if (!proj || !d_num_pairs || !d_status || n < 0 || capacity < 0 || capacity > AGS_MAX_PAIRS)
     return AGS_ERR_INVALID_ARG;
@@ -255,7 +405,8 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
   cudaStream_t st = (cudaStream_t)stream;
   if (total == 0) return launch_status(cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st));
   if (!proj->rect || (capacity > 0 && (!keys || !vals))) return AGS_ERR_INVALID_ARG;
-  if (!ws || ws_bytes < ags_emit_workspace_bytes(n, views) || ((uintptr_t)ws & 7u)) return AGS_ERR_INVALID_ARG;
+  if (flags & ~AGS_EMIT_SINGLE_PASS) return AGS_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < ags_emit_tile_workspace_bytes(n, views) || ((uintptr_t)ws & 15u)) return AGS_ERR_INVALID_ARG;
   const size_t parts = emit_parts(total);
   uint32_t tiles_per_view = (uint32_t)cb.c[0].gx * (uint32_t)cb.c[0].gy;
   if ((uint64_t)tiles_per_view * (uint64_t)views >= (1ull << 32)) return AGS_ERR_INVALID_ARG;
@@ -263,9 +414,33 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
   uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
+  uint4* recs = reinterpret_cast<uint4*>(reinterpret_cast<char*>(ws) + (256 + 8 * parts + 15) / 16 * 16);
+  uint32_t* chunk_start = reinterpret_cast<uint32_t*>(recs + total);
+  const int64_t* d_entries = order ? d_order_count : nullptr;
+  if (flags & AGS_EMIT_SINGLE_PASS) {   // fused scan and emission over partitions of Gaussians
+    emit_kernel<uint32_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
+        reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, d_entries, (uint32_t)n,
+        tiles_per_view, (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter,
+        nullptr, nullptr);
+    return launch_status(cudaGetLastError());
+  }
+  // phase 1: per-entry records and the pair count
   emit_kernel<uint32_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
-      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, (uint32_t)n, tiles_per_view,
-      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, (uint32_t)parts);
+      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, d_entries, (uint32_t)n, tiles_per_view,
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, recs, chunk_start);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || capacity == 0) return launch_status(e);
+  // phase 2: the pairs, in blocks of 1024 (grid-stride over the device count)
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t chunks = (capacity + kTileChunk - 1) / kTileChunk;
+  const unsigned grid = (unsigned)std::min<int64_t>(chunks, (int64_t)sms * 8);
+  const int smem = (int)sizeof(TileEmitSmem);
+  e = cudaFuncSetAttribute(tile_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return AGS_ERR_CUDA;
+  tile_emit_kernel<<<grid, kEmitThreads, smem, st>>>(recs, chunk_start, d_entries, total, d_num_pairs, capacity,
+                                                     (uint32_t)cb.c[0].gx, keys, vals);
   return launch_status(cudaGetLastError());
 }
 
@@ -331,7 +506,7 @@ extern "C" ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t 
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
   uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
   emit_kernel<uint64_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
-      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, (uint32_t)n, tiles_per_view,
-      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, (uint32_t)parts);
+      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, nullptr, (uint32_t)n, tiles_per_view,
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr);
   return launch_status(cudaGetLastError());
 }

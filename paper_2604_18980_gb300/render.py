@@ -50,7 +50,8 @@ class Renderer:
     def __init__(self, scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_PLAIN, K: float = 0.0, lut=None,
                  sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 9,
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
-                 presort: bool = True, pair_rank_or: bool = True, keep_state: bool = True):
+                 presort: bool = True, pair_rank_or: bool = True, emit_two_pass: bool = True,
+                 keep_state: bool = True):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -61,6 +62,7 @@ class Renderer:
         self.digit_bits = digit_bits
         self.presort = presort
         self.pair_rank_or = pair_rank_or
+        self.emit_two_pass = emit_two_pass
         self.keep_state = keep_state or want_backward   # final_T / n_contrib for the backward
         self.set_params(scale_mode, K, lut, sh_degree, bg)
         dev, V, n = self.device, self.V, self.n
@@ -70,18 +72,21 @@ class Renderer:
                          tiles_touched=torch.empty(V * n, dtype=torch.int32, device=dev),
                          flags=torch.empty(V * n, dtype=torch.uint8, device=dev))
         if presort:
-            # depth pre-sort of the Gaussians (32-bit depth keys); pairs then carry
-            # 32-bit tile keys and the pair sort needs only the tile digits
-            self.proj["depth_key"] = torch.empty(V * n, dtype=torch.int32, device=dev)
+            # depth pre-sort of the Gaussian-views that have pairs (32-bit depth
+            # keys, compacted first); pairs then carry 32-bit tile keys and the
+            # pair sort needs only the tile digits
+            self.dkey = torch.empty(V * n, dtype=torch.int32, device=dev)
             self.dkey_alt = torch.empty(V * n, dtype=torch.int32, device=dev)
             self.order = torch.empty(V * n, dtype=torch.int32, device=dev)
             self.order_alt = torch.empty(V * n, dtype=torch.int32, device=dev)
-            self.n_total = torch.tensor([V * n], dtype=torch.int64, device=dev)
+            self.n_visible = torch.zeros(1, dtype=torch.int64, device=dev)
+            self.ws_vis = torch.empty(B.ags_compact_workspace_bytes(n, V), dtype=torch.uint8, device=dev)
             self.ws_dsort = torch.empty(B.ags_sort_workspace_bytes(V * n), dtype=torch.uint8, device=dev)
             self.dsort_end = 32
         self.status = torch.zeros(4, dtype=torch.int64, device=dev)
         self.num_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.ws_emit = torch.empty(max(B.ags_emit_workspace_bytes(n, V), 16), dtype=torch.uint8, device=dev)
+        ews = B.ags_emit_tile_workspace_bytes(n, V) if presort else B.ags_emit_workspace_bytes(n, V)
+        self.ws_emit = torch.empty(max(ews, 16), dtype=torch.uint8, device=dev)
         self.ranges = torch.empty(V * self.T * 2, dtype=torch.int32, device=dev)
         self.image = torch.empty(V, 3, self.H, self.W, dtype=torch.float32, device=dev)
         self.final_T = torch.empty(V, self.H, self.W, dtype=torch.float32, device=dev) if self.keep_state else None
@@ -139,8 +144,8 @@ class Renderer:
     def launches_per_forward(self) -> int:
         # preprocess, emit, (histogram, digit scan, passes, ranges fix-up), blend
         n = 1 + 1 + (2 + self.sort_plan()[0] + 1) + 1
-        if self.presort:
-            n += 2 + digit_plan(self.dsort_end, self.digit_bits)[0]
+        if self.presort:       # compaction, then (histogram, digit scan, passes)
+            n += 1 + 2 + digit_plan(self.dsort_end, self.digit_bits)[0]
         return n
 
     # -- stages ---------------------------------------------------------------
@@ -148,19 +153,23 @@ class Renderer:
         B.ags_preprocess(self.scene, self.cams, self.params, self.proj, self.status)
 
     def depth_sort(self):
-        """Stable sort of the Gaussians by depth: the emission order (each view's
-        Gaussians in depth order, equal depths in index order)."""
+        """Stable sort of the Gaussian-views with pairs by depth: the emission
+        order (each view's Gaussians in depth order, equal depths in index order)."""
         if self.presort:
+            B.ags_compact_visible(self.proj, self.n, self.V, self.dkey, self.order, self.n_visible, self.status,
+                                  self.ws_vis)
             passes, db = digit_plan(self.dsort_end, self.digit_bits)
-            alt = B.ags_sort32(self.proj["depth_key"], self.order, self.dkey_alt, self.order_alt, self.n_total,
+            alt = B.ags_sort32(self.dkey, self.order, self.dkey_alt, self.order_alt, self.n_visible,
                                self.V * self.n, 0, self.dsort_end, db, None, 0, self.status, self.ws_dsort,
-                               flags=B.AGS_SORT_IDENTITY_VALUES | B.AGS_SORT_DISCARD_KEYS)
+                               flags=B.AGS_SORT_DISCARD_KEYS)
             self.emit_order = self.order_alt if alt else self.order
 
     def emit(self):
         if self.presort:
             B.ags_emit_tile_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity,
-                                  self.num_pairs, self.status, self.ws_emit, order=self.emit_order)
+                                  self.num_pairs, self.status, self.ws_emit, order=self.emit_order,
+                                  order_count=self.n_visible,
+                                  flags=0 if self.emit_two_pass else B.AGS_EMIT_SINGLE_PASS)
         else:
             B.ags_emit_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity, self.num_pairs,
                              self.status, self.ws_emit)

@@ -297,14 +297,32 @@ def test_sort32_random_keys_stable(count, bits, digit, flags, rank_or):
 
 
 def test_emit_tile_pairs_matches_emit_pairs():
-    """32-bit tile keys in the depth order: the tile word of the 64-bit keys, same
-    values, same count; the renderer's pair lists agree with the full-key path."""
+    """32-bit tile keys in the depth order of the compacted visible views: the
+    tile word of the 64-bit keys emitted in that order, same values, same count;
+    the order holds every visible view once, each view by depth then index."""
     scene, cams = _c1(n=9000, W=176, H=144, views=3)
     sc = R.scene_to_device(scene)
     r = R.Renderer(sc, cams, 1, 0.3, presort=True)
     r.preprocess()
     r.depth_sort()
-    order = r.emit_order
+    r.check()
+    nvis = int(r.n_visible.item())
+    flags = r.proj["flags"].cpu().numpy()
+    visible = np.nonzero((flags & 0x80) == 0)[0]
+    assert nvis == len(visible) and 0 < nvis < r.V * r.n
+    o = r.emit_order[:nvis].cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(np.sort(o), visible)
+    dk = r.proj["depth"].cpu().numpy().view(np.uint32)[o]
+    v_of = o // r.n
+    for v in range(len(cams)):
+        sel = v_of == v
+        ov, dv = o[sel], dk[sel].astype(np.int64)
+        assert np.all(np.diff(dv) >= 0)
+        ties = np.nonzero(np.diff(dv) == 0)[0]
+        assert np.all(ov[ties + 1] > ov[ties])
+    # pairs: 64-bit emission over the same order (a full-length copy whose tail
+    # lists the culled views, which emit nothing) against the tile-key emission
+    full = torch.from_numpy(np.concatenate([o, np.setdiff1d(np.arange(r.V * r.n), visible)]).astype(np.int32)).cuda()
     cap = r.capacity
     k64 = torch.empty(cap, dtype=torch.int64, device="cuda")
     v64 = torch.empty(cap, dtype=torch.int32, device="cuda")
@@ -312,27 +330,69 @@ def test_emit_tile_pairs_matches_emit_pairs():
     v32 = torch.empty(cap, dtype=torch.int32, device="cuda")
     n64 = torch.zeros(1, dtype=torch.int64, device="cuda")
     n32 = torch.zeros(1, dtype=torch.int64, device="cuda")
-    B.ags_emit_pairs(r.proj, r.n, cams, k64, v64, cap, n64, r.status, r.ws_emit, order=order)
-    B.ags_emit_tile_pairs(r.proj, r.n, cams, k32, v32, cap, n32, r.status, r.ws_emit, order=order)
+    B.ags_emit_pairs(r.proj, r.n, cams, k64, v64, cap, n64, r.status, r.ws_emit, order=full)
+    B.ags_emit_tile_pairs(r.proj, r.n, cams, k32, v32, cap, n32, r.status, r.ws_emit, order=r.emit_order,
+                          order_count=r.n_visible)
     r.check()
     P = int(n64.item())
     assert P == int(n32.item()) and P > 0
     hi = (k64[:P].cpu().numpy().view(np.uint64) >> np.uint64(32)).astype(np.uint32)
     np.testing.assert_array_equal(k32[:P].cpu().numpy().view(np.uint32), hi)
     assert torch.equal(v32[:P], v64[:P])
-    # the depth order: within each view, depth ascending, equal depths by index
-    # (the sort overwrote depth_key: rebuild the keys from the depths and flags)
-    o = order.cpu().numpy().astype(np.int64)
-    culled = (r.proj["flags"].cpu().numpy() & 0x80) != 0
-    dk = np.where(culled, np.uint32(0xffffffff), r.proj["depth"].cpu().numpy().view(np.uint32))[o]
-    live = dk != 0xffffffff
-    assert np.all(np.diff(dk.astype(np.int64)) >= 0)
-    assert np.all(~live[np.argmax(~live):]) if (~live).any() else True
-    for v in range(len(cams)):
-        sel = (o // r.n) == v
-        ov, dv = o[sel], dk[sel]
-        ties = np.nonzero(np.diff(dv.astype(np.int64)) == 0)[0]
-        assert np.all(ov[ties + 1] > ov[ties])
+
+
+def test_emit_tile_pairs_balanced_blocks():
+    """The two-pass tile-key emission over orders with culled entries (no pairs)
+    and with Gaussians whose pairs span many 1024-pair blocks: identical to the
+    64-bit emission's tile words and values."""
+    scene, cams = _c1(n=6000, W=1280, H=960, views=2)
+    scene["log_scale"][:, :40] = -0.3            # a few Gaussians covering thousands of tiles
+    scene["mean"][:, -300:] = np.nan             # culled: entries without pairs
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, 0, 0.0, presort=True)
+    r.preprocess()
+    cap = r.capacity
+    for order, flags in ((None, 0), (torch.randperm(r.V * r.n, device="cuda").to(torch.int32), 0),
+                         (None, B.AGS_EMIT_SINGLE_PASS)):
+        k64 = torch.empty(cap, dtype=torch.int64, device="cuda")
+        v64 = torch.empty(cap, dtype=torch.int32, device="cuda")
+        k32 = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+        v32 = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+        n64 = torch.zeros(1, dtype=torch.int64, device="cuda")
+        n32 = torch.zeros(1, dtype=torch.int64, device="cuda")
+        B.ags_emit_pairs(r.proj, r.n, cams, k64, v64, cap, n64, r.status, r.ws_emit, order=order)
+        B.ags_emit_tile_pairs(r.proj, r.n, cams, k32, v32, cap, n32, r.status, r.ws_emit, order=order, flags=flags)
+        r.check()
+        P = int(n64.item())
+        assert P == int(n32.item()) and P > 4096
+        touched = r.proj["tiles_touched"].cpu().numpy()
+        assert touched.max() > 2 * 2048 and (touched == 0).any()
+        hi = (k64[:P].cpu().numpy().view(np.uint64) >> np.uint64(32)).astype(np.uint32)
+        np.testing.assert_array_equal(k32[:P].cpu().numpy().view(np.uint32), hi)
+        assert torch.equal(v32[:P], v64[:P])
+        assert torch.all(k32[P:] == -1)
+
+
+def test_compact_visible_edges():
+    """Compaction of ragged counts (not a multiple of the partition), all-culled
+    and none-culled inputs, against numpy."""
+    for total, p_cull in ((1, 0.0), (4095, 0.5), (4097, 0.3), (3 * 4096 + 17, 1.0), (70001, 0.0), (70001, 0.9)):
+        rng = np.random.default_rng(total + int(10 * p_cull))
+        flags = np.where(rng.random(total) < p_cull, 0x80, rng.integers(0, 0x20, total)).astype(np.uint8)
+        depth = rng.uniform(0.2, 50.0, total).astype(np.float32)
+        proj = dict(splat=None, depth=torch.from_numpy(depth).cuda(), rect=None, flags=torch.from_numpy(flags).cuda())
+        keys = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+        ids = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st = torch.zeros(4, dtype=torch.int64, device="cuda")
+        ws = torch.empty(B.ags_compact_workspace_bytes(total, 1), dtype=torch.uint8, device="cuda")
+        B.ags_compact_visible(proj, total, 1, keys, ids, cnt, st, ws)
+        B.ags_check(st)
+        vis = np.nonzero((flags & 0x80) == 0)[0]
+        assert int(cnt.item()) == len(vis)
+        np.testing.assert_array_equal(ids[:len(vis)].cpu().numpy(), vis)
+        np.testing.assert_array_equal(keys[:len(vis)].cpu().numpy().view(np.uint32), depth.view(np.uint32)[vis])
+        assert torch.all(ids[len(vis):] == -1)
 
 
 def test_cuda_graph_replay_matches_eager_and_follows_scene_updates():

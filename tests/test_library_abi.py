@@ -60,6 +60,11 @@ def test_workspace_sizes(lib):
     assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 512 * 4 + 1 * 512 * 4
     assert B.ags_sort_workspace_bytes(4097) == 256 + 16 * 512 * 4 + 2 * 512 * 4
     assert B.ags_backward_workspace_bytes(10, 2) == 10 * 2 * 9 * 4
+    assert B.ags_compact_workspace_bytes(4096, 1) == 256 + 8
+    chunks = 4 * ((B.AGS_MAX_PAIRS + 2047) // 2048 + 1)
+    assert B.ags_emit_tile_workspace_bytes(1024, 1) == 256 + 16 + 16 * 1024 + chunks
+    assert B.ags_emit_tile_workspace_bytes(1025, 2) == 256 + 32 + 16 * 2050 + chunks
+    assert B.ags_compact_workspace_bytes(4097, 2) == 256 + 8 * 3
 
 
 def test_invalid_arguments_rejected_on_host(lib):
@@ -110,7 +115,16 @@ def test_invalid_arguments_rejected_on_host(lib):
                       10, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st, ctypes.c_void_p(256), 1 << 20, None) == 1
     # emit: workspace too small
     assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, None, 0, None) == 1
-    assert L.ags_emit_tile_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, None, 0, None) == 1
+    assert L.ags_emit_tile_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, None, 0, npairs, st, 0, None, 0,
+                                 None) == 1
+    # compaction: zero views, missing workspace, unaligned flags
+    assert L.ags_compact_visible(ctypes.byref(pr), 10, 0, None, None, npairs, st, None, 0, None) == 1
+    pr2 = B.AgsProjected()
+    pr2.flags, pr2.depth = ctypes.c_void_p(17), ctypes.c_void_p(32)
+    assert L.ags_compact_visible(ctypes.byref(pr2), 10, 1, ctypes.c_void_p(16), ctypes.c_void_p(16), npairs, st,
+                                 ctypes.c_void_p(256), 1 << 20, None) == 1
+    assert L.ags_compact_visible(ctypes.byref(pr), 10, 1, ctypes.c_void_p(16), ctypes.c_void_p(16), npairs, st,
+                                 None, 0, None) == 1
     # mismatched view sizes
     cams2 = B.cameras([dict(width=64, height=48, fx=50.0, fy=50.0, cx=31.5, cy=23.5,
                             viewmat=[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], campos=[0, 0, 0]),

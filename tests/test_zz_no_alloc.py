@@ -36,16 +36,22 @@ def test_noalloc_emit_matches_workspace_emit_twice():
     r = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, 0.3)
     r.preprocess()
     r.depth_sort()
+    # a full permutation of the Gaussian-views: the depth order of the visible
+    # ones (the renderer's compacted order), then the culled ones
+    nvis = int(r.n_visible.item())
+    culled = torch.nonzero((r.proj["flags"] & 0x80) != 0).flatten().to(torch.int32)
+    order_full = torch.cat([r.emit_order[:nvis], culled]).contiguous()
+    assert order_full.numel() == r.V * r.n
     cap = r.capacity
     keys_ref = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
     vals_ref = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
     np_ref = torch.zeros(1, dtype=torch.int64, device="cuda")
     st = torch.zeros(4, dtype=torch.int64, device="cuda")
-    B.ags_emit_pairs(r.proj, r.n, r.cams, keys_ref, vals_ref, cap, np_ref, st, r.ws_emit, order=r.emit_order)
+    B.ags_emit_pairs(r.proj, r.n, r.cams, keys_ref, vals_ref, cap, np_ref, st, r.ws_emit, order=order_full)
     B.ags_check(st)
     n_ref = int(np_ref.item())
     assert n_ref > 0
-    for order in (r.emit_order, None, r.emit_order):   # several calls in a row share the scratch array
+    for order in (order_full, None, order_full):   # several calls in a row share the scratch array
         keys = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
         vals = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
         npairs = torch.zeros(1, dtype=torch.int64, device="cuda")
