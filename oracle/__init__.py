@@ -30,13 +30,14 @@ _LIB = os.path.join(_HERE, "_build", "libags_oracle.so")
 
 # per-Gaussian double fields
 (F_U, F_V, F_A, F_B, F_C, F_OPAC, F_R, F_G, F_BL, F_DEPTH, F_TH, F_DET, F_LAMBDA,
- F_COVA, F_COVB, F_COVC, F_DEPTH32, F_RARG) = range(18)
-NF = 18
+ F_COVA, F_COVB, F_COVC, F_DEPTH32, F_RARG, F_QELL) = range(19)
+NF = 19
 # per-Gaussian integer fields
 I_RADIUS, I_X0, I_Y0, I_X1, I_Y1, I_TOUCHED, I_CULL, I_EDGE, I_CLAMP = range(9)
 NI = 9
 CULL_NONE, CULL_NEAR, CULL_DET, CULL_TH, CULL_TUP, CULL_NONFINITE, CULL_EMPTY = range(7)
-EDGE_NEAR, EDGE_DET, EDGE_TH, EDGE_CEIL, EDGE_RECT, EDGE_LUT = 1, 2, 4, 8, 16, 32
+EDGE_NEAR, EDGE_DET, EDGE_TH, EDGE_CEIL, EDGE_RECT, EDGE_LUT, EDGE_ELLIPSE = 1, 2, 4, 8, 16, 32, 64
+TILE_SQUARE, TILE_ELLIPSE = 0, 1     # tile test: square footprint, or square and ellipse
 TILE = 16
 
 TAU = 1.0 / 255.0        # Sec. 2.1 / Sec. 3.1
@@ -63,7 +64,7 @@ class OcCamera(ctypes.Structure):
 
 class OcParams(ctypes.Structure):
     _fields_ = [("scale_mode", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
-                ("lut_bins", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("lut_bins", ctypes.c_int32), ("tile_test", ctypes.c_int32),
                 ("K", ctypes.c_double), ("tau", ctypes.c_double), ("t_min", ctypes.c_double),
                 ("alpha_max", ctypes.c_double), ("lut_depth_max", ctypes.c_double),
                 ("lut", ctypes.c_double * 32), ("bg", ctypes.c_double * 3),
@@ -110,11 +111,12 @@ def params(cam: dict | None = None, scale_mode: int = 0, K: float = 0.0, lut=Non
            sh_degree: int = 3, bg=(0.0, 0.0, 0.0), tau: float = TAU, t_min: float = T_MIN,
            alpha_max: float = ALPHA_MAX, lut_bins: int = LUT_BINS,
            lut_depth_max: float = LUT_DEPTH_MAX, edge_rel: float = 1e-5,
-           pos_err: float | None = None) -> OcParams:
+           pos_err: float | None = None, tile_test: int = TILE_SQUARE) -> OcParams:
     """Render parameters.  `pos_err` defaults to 8 fp32 ulps of the image extent
     (the rounding of a float32 pixel position); it only widens edge classes."""
     p = OcParams()
     p.scale_mode, p.sh_degree, p.lut_bins = int(scale_mode), int(sh_degree), int(lut_bins)
+    p.tile_test = int(tile_test)
     p.K, p.tau, p.t_min, p.alpha_max = float(K), float(tau), float(t_min), float(alpha_max)
     p.lut_depth_max = float(lut_depth_max)
     lut = np.ones(lut_bins) if lut is None else np.asarray(lut, dtype=np.float64)

@@ -10,7 +10,9 @@
  *   preprocess  (Sec. 2.1: cull, project to 2D mean/covariance, colour, depth)
  *   AdaGScale   (Eq. 9-10 threshold Th, Sec. 3.3 cull when Th > opacity,
  *                adjusted intersection test; Sec. 3.4 T_up look-up table)
- *   tile lists  (Sec. 2.1 pair generation + sort by tile, then depth)
+ *   tile lists  (Sec. 2.1 pair generation + sort by tile, then depth); the
+ *                tiles are those of the square footprint, or (tile_test 1)
+ *                those of it that the alpha >= Th ellipse reaches
  *   blending    (Eq. 1 alpha, Eq. 2 front-to-back accumulation with tau and the
  *                1e-4 transmittance stop; always with the original covariance,
  *                Sec. 3.3 "dual-size strategy")
@@ -54,7 +56,7 @@ typedef struct {
   int32_t scale_mode;     /* 0 plain 3-sigma, 1 AdaGScale */
   int32_t sh_degree;      /* 0..3 */
   int32_t lut_bins;       /* <= 32 */
-  int32_t pad0;
+  int32_t tile_test;      /* 0 square footprint, 1 square and ellipse */
   double K, tau, t_min, alpha_max;
   double lut_depth_max;
   double lut[32];
@@ -66,7 +68,9 @@ typedef struct {
 /* Per-Gaussian double outputs. */
 enum {
   F_U = 0, F_V, F_A, F_B, F_C, F_OPAC, F_R, F_G, F_BL, F_DEPTH, F_TH, F_DET, F_LAMBDA,
-  F_COVA, F_COVB, F_COVC, F_DEPTH32, F_RARG, OC_NF
+  F_COVA, F_COVB, F_COVC, F_DEPTH32, F_RARG,
+  F_QELL,   /* ellipse level Q = 2 ln(opacity / Th) of the tile test, NaN for the square test */
+  OC_NF
 };
 /* Per-Gaussian integer outputs. */
 enum { I_RADIUS = 0, I_X0, I_Y0, I_X1, I_Y1, I_TOUCHED, I_CULL, I_EDGE, I_CLAMP, OC_NI };
@@ -87,6 +91,7 @@ enum { I_RADIUS = 0, I_X0, I_Y0, I_X1, I_Y1, I_TOUCHED, I_CULL, I_EDGE, I_CLAMP,
 #define EDGE_CEIL 8
 #define EDGE_RECT 16
 #define EDGE_LUT 32
+#define EDGE_ELLIPSE 64
 
 /* ------------------------------------------------------------------------ */
 /* Jets: value plus NJ partial derivatives.                                   */
@@ -208,6 +213,45 @@ static int span_tiles(double lo, double hi, int len, double slack, int* t0, int*
 /* edge test: is |a - b| within rel * scale ? */
 static int near_edge(double a, double b, double rel, double scale) {
   return fabs(a - b) <= rel * scale;
+}
+
+/* Minimum of the conic's quadratic form q(x, y) = A x^2 + 2 B x y + C y^2
+ * (positive definite) over the rectangle [xl, xh] x [yl, yh] of offsets from
+ * the Gaussian's centre.  Zero when the rectangle holds the centre; otherwise
+ * the minimum of a convex function over a rectangle lies on its boundary, and
+ * along each edge q is a parabola in the free coordinate whose vertex, clamped
+ * to the edge, gives that edge's minimum. */
+static double rect_min_form(double A, double B, double C, double xl, double xh, double yl, double yh) {
+  if (xl <= 0.0 && xh >= 0.0 && yl <= 0.0 && yh >= 0.0) return 0.0;
+  double best = INFINITY;
+  const double xs[2] = {xl, xh}, ys[2] = {yl, yh};
+  for (int k = 0; k < 2; k++) {
+    double x = xs[k];
+    double y = fmin(fmax(-B * x / C, yl), yh);          /* vertex of q(x, .) */
+    best = fmin(best, A * x * x + 2.0 * B * x * y + C * y * y);
+    y = ys[k];
+    x = fmin(fmax(-B * y / A, xl), xh);                 /* vertex of q(., y) */
+    best = fmin(best, A * x * x + 2.0 * B * x * y + C * y * y);
+  }
+  return best;
+}
+
+/* Ellipse tile test (the exact footprint-tile intersection the paper's
+ * implementation builds on; our reading for tile_test 1): tile (tx, ty) is kept
+ * when some point of the rectangle spanned by its pixel centres (clipped to
+ * the image) has alpha >= Th with the blending conic, i.e. q <= Q with
+ * Q = 2 ln(opacity / Th), Th = tau in plain mode.  Returns the minimum of q
+ * over that rectangle. */
+static double tile_min_form(const double* g, int tx, int ty, int width, int height) {
+  double xl = OC_TILE * tx - g[F_U], xh = fmin(OC_TILE * tx + OC_TILE - 1, width - 1) - g[F_U];
+  double yl = OC_TILE * ty - g[F_V], yh = fmin(OC_TILE * ty + OC_TILE - 1, height - 1) - g[F_V];
+  return rect_min_form(g[F_A], g[F_B], g[F_C], xl, xh, yl, yh);
+}
+
+static int tile_kept(const double* g, int tx, int ty, int width, int height) {
+  double Q = g[F_QELL];
+  if (isnan(Q)) return 1;
+  return tile_min_form(g, tx, ty, width, height) <= Q;
 }
 
 /* Returns cull reason; fills dbl[OC_NF], irec[OC_NI] and (optionally) the jets. */
@@ -393,6 +437,25 @@ static int preprocess_one(const double* mean, const double* log_scale, const dou
     for (int k = 0; k < nc; k++) gj->Y[k] = Y[k];
   }
   int64_t area = (int64_t)(x1 - x0) * (y1 - y0);
+  dbl[F_QELL] = NAN;
+  if (par->tile_test == 1 && radius > 0 && area > 0) {
+    /* keep the tiles of the square that the alpha >= Th ellipse reaches; a
+     * decision within the edge width of Q marks the Gaussian an edge case
+     * (its conic and position carry fp32 rounding on the GPU: Q's relative
+     * width plus the position error times |grad q| = 2 sqrt(q * lambda)) */
+    double Q = 2.0 * log(opac.v / th);
+    dbl[F_QELL] = Q;
+    int64_t kept = 0;
+    for (int ty = y0; ty < y1; ty++)
+      for (int tx = x0; tx < x1; tx++) {
+        double m = tile_min_form(dbl, tx, ty, cam->width, cam->height);
+        if (m <= Q) kept++;
+        double tol = eps * fmax(Q, 1.0) + 2.0 * par->pos_err * sqrt((A.v + C.v) * fmax(fmax(Q, m), 0.0));
+        if (fabs(m - Q) <= tol) edge |= EDGE_ELLIPSE;
+      }
+    irec[I_EDGE] = edge;
+    area = kept;
+  }
   if (radius <= 0 || area <= 0) { irec[I_CULL] = CULL_EMPTY; return CULL_EMPTY; }
   irec[I_TOUCHED] = (int32_t)area;
   return CULL_NONE;
@@ -435,7 +498,7 @@ int64_t oracle_tile_lists(int64_t n, const double* dbl, const int32_t* irec, int
     for (int ty = r[I_Y0]; ty < r[I_Y1]; ty++)
       for (int tx = r[I_X0]; tx < r[I_X1]; tx++) {
         int64_t t = (int64_t)ty * gx + tx;
-        if (!tile_mask || tile_mask[t]) cnt[t]++;
+        if ((!tile_mask || tile_mask[t]) && tile_kept(dbl + i * OC_NF, tx, ty, width, height)) cnt[t]++;
       }
   }
   tile_start[0] = 0;
@@ -452,6 +515,7 @@ int64_t oracle_tile_lists(int64_t n, const double* dbl, const int32_t* irec, int
         for (int tx = r[I_X0]; tx < r[I_X1]; tx++) {
           int64_t t = (int64_t)ty * gx + tx;
           if (tile_mask && !tile_mask[t]) continue;
+          if (!tile_kept(dbl + i * OC_NF, tx, ty, width, height)) continue;
           oc_pair* p = &pairs[tile_start[t] + cnt[t]++];
           p->depth = d;
           p->id = (int32_t)i;
@@ -565,8 +629,8 @@ void oracle_rasterize(int64_t n, const double* dbl, const int64_t* tile_start, c
 }
 
 /* Brute force: no tile lists and no key sort.  Every pixel takes every
- * Gaussian whose rectangle holds the pixel's tile, orders them globally by
- * (fp32 depth, id) and blends. */
+ * Gaussian whose rectangle holds the pixel's tile (and whose ellipse reaches
+ * it, with tile_test 1), orders them globally by (fp32 depth, id) and blends. */
 void oracle_render_bruteforce(int64_t n, const double* dbl, const int32_t* irec, int32_t width,
                               int32_t height, const oc_params* par, double* image) {
   oc_pair* all = (oc_pair*)malloc(sizeof(oc_pair) * (n > 0 ? n : 1));
@@ -588,7 +652,9 @@ void oracle_render_bruteforce(int64_t n, const double* dbl, const int32_t* irec,
       int64_t len = 0;
       for (int64_t k = 0; k < m; k++) {
         const int32_t* r = irec + (int64_t)all[k].id * OC_NI;
-        if (tx >= r[I_X0] && tx < r[I_X1] && ty >= r[I_Y0] && ty < r[I_Y1]) list[len++] = all[k].id;
+        if (tx >= r[I_X0] && tx < r[I_X1] && ty >= r[I_Y0] && ty < r[I_Y1] &&
+            tile_kept(dbl + (int64_t)all[k].id * OC_NF, tx, ty, width, height))
+          list[len++] = all[k].id;
       }
       oc_pix pix;
       blend_pixel((double)x, (double)y, list, len, dbl, par, cmax, NULL, &pix);

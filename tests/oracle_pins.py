@@ -10,6 +10,9 @@ AssertionError when the oracle disagrees with:
     their orthonormality on the sphere,
   * brute-force enumeration (pixel coverage of the tile rectangle, untiled
     rendering, and an ideal render with no footprint at all),
+  * the ellipse tile test against the closed form of an axis-aligned conic and
+    a dense sampling of every tile (and plain mode with it rendering exactly
+    the square-footprint image),
   * invariants stated by the paper (Th >= tau, Th > sigma culls, larger K drops
     pairs, the blend always uses the unscaled covariance),
   * FP64 central finite differences of the forward (backward pin).
@@ -520,6 +523,116 @@ def pin_backward_fd(orc, n_check=None, seed=5):
     return checked, skipped
 
 
+# --------------------------------------------------------------------------
+# Ellipse tile test (tile_test 1)
+# --------------------------------------------------------------------------
+def _interval_dist(lo, hi):
+    """Distance from 0 to the interval [lo, hi]."""
+    return 0.0 if lo <= 0.0 <= hi else min(abs(lo), abs(hi))
+
+
+def pin_ellipse_tiles(orc):
+    """The kept tiles against (a) the closed form of an axis-aligned conic, whose
+    minimum over a rectangle is A dx^2 + C dy^2 with dx, dy the distances from
+    the centre to the rectangle's x and y ranges, and (b) a dense sampling of
+    each tile's pixel-centre rectangle for rotated conics: a tile is kept iff the
+    sampled minimum reaches Q, up to the sampling error."""
+    # (a) axis-aligned Gaussians (on the y = 0 plane, so B = 0): one stretched
+    # along x, one thin in x just beyond the last pixel column of a ragged
+    # image, whose square reaches the clipped last tile column but whose
+    # ellipse misses its pixel centres
+    W, H = 100, 64
+    cam = axis_camera(W, H, 80.0)
+    scene = concat(one_gaussian((0.31, 0.0, 2.0), (0.35, 0.1, 0.1), opacity=0.9),
+                   one_gaussian((1.3375, 0.0, 2.0), (0.01, 0.2, 0.01), opacity=0.9))
+    par = oracle.params(cam, tile_test=oracle.TILE_ELLIPSE)
+    dbl, irec = orc.preprocess(scene, cam, par)
+    total = 0
+    for i in range(2):
+        g = dbl[i]
+        assert g[oracle.F_B] == 0.0
+        Q = 2 * math.log(g[oracle.F_OPAC] / TAU)
+        assert abs(g[oracle.F_QELL] - Q) < 1e-12
+        x0, y0, x1, y1 = (irec[i, k] for k in (oracle.I_X0, oracle.I_Y0, oracle.I_X1, oracle.I_Y1))
+        kept_cf = 0
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                dx = _interval_dist(16 * tx - g[oracle.F_U], min(16 * tx + 15, W - 1) - g[oracle.F_U])
+                dy = _interval_dist(16 * ty - g[oracle.F_V], min(16 * ty + 15, H - 1) - g[oracle.F_V])
+                kept_cf += g[oracle.F_A] * dx * dx + g[oracle.F_C] * dy * dy <= Q
+        assert irec[i, oracle.I_TOUCHED] == kept_cf and 0 <= kept_cf < (x1 - x0) * (y1 - y0)
+        total += kept_cf
+    assert irec[0, oracle.I_TOUCHED] > 0 and dbl[1, oracle.F_U] - W + 1 > 1.0 and irec[1, oracle.I_X1] == 7
+    out = orc.render(scene, cam, par)
+    assert len(out["ids"]) == total
+    # (b) rotated conics, both modes: dense sampling of every tile of the square
+    for mode, K in ((0, 0.0), (1, 0.1)):
+        scene, cam = tiny_scene(60, 71, W=70, H=52)
+        W, H = cam["width"], cam["height"]
+        par = oracle.params(cam, scale_mode=mode, K=K, tile_test=oracle.TILE_ELLIPSE)
+        dbl, irec = orc.preprocess(scene, cam, par)
+        _, irq = orc.preprocess(scene, cam, oracle.params(cam, scale_mode=mode, K=K))
+        ts, ids = orc.tile_lists(dbl, irec, W, H)
+        gx = (W + 15) // 16
+        kept_tiles = {(int(t), int(i)) for t, i in zip(np.repeat(np.arange(len(ts) - 1), np.diff(ts)), ids)}
+        s = np.linspace(0.0, 1.0, 121)
+        checked = 0
+        for i in range(len(dbl)):
+            if irq[i, oracle.I_TOUCHED] <= 0:
+                continue
+            g = dbl[i]
+            Q = g[oracle.F_QELL]
+            x0, y0, x1, y1 = (irq[i, k] for k in (oracle.I_X0, oracle.I_Y0, oracle.I_X1, oracle.I_Y1))
+            for ty in range(y0, y1):
+                for tx in range(x0, x1):
+                    xs = 16 * tx + s * (min(16 * tx + 15, W - 1) - 16 * tx) - g[oracle.F_U]
+                    ys = 16 * ty + s * (min(16 * ty + 15, H - 1) - 16 * ty) - g[oracle.F_V]
+                    X, Y = np.meshgrid(xs, ys)
+                    q = g[oracle.F_A] * X * X + 2 * g[oracle.F_B] * X * Y + g[oracle.F_C] * Y * Y
+                    qmin = q.min()
+                    # sampling error bound: |grad q| * half the sample spacing (diagonal)
+                    step = 15.0 / 120.0
+                    grad = 2.0 * math.sqrt((g[oracle.F_A] + g[oracle.F_C]) * max(qmin, 0.0) + 1e-300)
+                    slack = grad * step + (g[oracle.F_A] + g[oracle.F_C]) * step * step
+                    kept = ((ty * gx + tx), i) in kept_tiles
+                    if qmin <= Q - 1e-12:
+                        assert kept, (i, tx, ty, qmin, Q)
+                    elif qmin - slack > Q:
+                        assert not kept, (i, tx, ty, qmin, Q)
+                    checked += 1
+        assert checked > 50
+
+
+def pin_ellipse_lossless_plain(orc):
+    """Plain mode with the ellipse test renders exactly the square-footprint
+    image (a dropped tile holds only pixels with alpha < tau), with a subset of
+    its pairs; with AdaGScale every pixel centre of a dropped tile has
+    alpha < Th; brute force and tiled agree."""
+    scene, cam = tiny_scene(220, 81, W=80, H=64)
+    W, H = cam["width"], cam["height"]
+    sq = orc.render(scene, cam, oracle.params(cam))
+    el = orc.render(scene, cam, oracle.params(cam, tile_test=oracle.TILE_ELLIPSE))
+    np.testing.assert_array_equal(el["image"], sq["image"])
+    Ps, Pe = _pairs(sq, W), _pairs(el, W)
+    assert Pe <= Ps and len(Pe) < len(Ps)
+    par = oracle.params(cam, scale_mode=1, K=0.2, tile_test=oracle.TILE_ELLIPSE)
+    ada = orc.render(scene, cam, par)
+    ada_sq = orc.render(scene, cam, oracle.params(cam, scale_mode=1, K=0.2))
+    Pa, Pas = _pairs(ada, W), _pairs(ada_sq, W)
+    assert Pa <= Pas
+    gx = (W + 15) // 16
+    px, py = np.meshgrid(np.arange(W), np.arange(H))
+    for (t, i) in Pas - Pa:
+        g = ada["dbl"][i]
+        tx, ty = t % gx, t // gx
+        sel = (px // 16 == tx) & (py // 16 == ty)
+        dx, dy = px[sel] - g[oracle.F_U], py[sel] - g[oracle.F_V]
+        q = g[oracle.F_A] * dx * dx + 2 * g[oracle.F_B] * dx * dy + g[oracle.F_C] * dy * dy
+        assert np.all(g[oracle.F_OPAC] * np.exp(-0.5 * q) < g[oracle.F_TH] * (1 + 1e-12))
+    np.testing.assert_array_equal(ada["image"], orc.render_bruteforce(scene, cam, par))
+
+
 ALL_PINS = [pin_isotropic_on_axis, pin_off_axis_jacobian, pin_rotation_conventions, pin_eq9_quadrature,
             pin_eq8_riemann_pixels, pin_sh_basis, pin_sh_colour, pin_rect_enumeration, pin_bruteforce,
-            pin_ideal_render, pin_invariants, pin_low_opacity_invisible, pin_max_T, pin_backward_fd]
+            pin_ideal_render, pin_invariants, pin_low_opacity_invisible, pin_max_T, pin_backward_fd,
+            pin_ellipse_tiles, pin_ellipse_lossless_plain]

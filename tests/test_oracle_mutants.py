@@ -51,6 +51,13 @@ MUTANTS = [
     ("backward_mean_sign", "atomic_add_double(&G[who[j] * 9 + 0], dLdp * (-(f[F_A] * dx + f[F_B] * dy)));",
      "atomic_add_double(&G[who[j] * 9 + 0], dLdp * (f[F_A] * dx + f[F_B] * dy));", ["pin_backward_fd"]),
     ("backward_ignores_alpha_clamp", "if (clampa[j]) continue;", "", ["pin_backward_fd"]),
+    ("ellipse_level_missing_2", "double Q = 2.0 * log(opac.v / th);", "double Q = log(opac.v / th);",
+     ["pin_ellipse_tiles", "pin_ellipse_lossless_plain"]),
+    ("ellipse_cross_term_sign", "best = fmin(best, A * x * x + 2.0 * B * x * y + C * y * y);\n    y = ys[k];",
+     "best = fmin(best, A * x * x - 2.0 * B * x * y + C * y * y);\n    y = ys[k];",
+     ["pin_ellipse_tiles", "pin_ellipse_lossless_plain"]),
+    ("ellipse_tile_unclipped", "xh = fmin(OC_TILE * tx + OC_TILE - 1, width - 1) - g[F_U];",
+     "xh = OC_TILE * tx + OC_TILE - 1 - g[F_U];", ["pin_ellipse_tiles"]),
 ]
 
 
