@@ -71,6 +71,16 @@ typedef enum {
 
 typedef enum { AGS_SCALE_PLAIN = 0, AGS_SCALE_ADAGSCALE = 1 } ags_scale_mode;
 
+/* Which tiles of a Gaussian's footprint get a pair.  SQUARE: every tile of the
+ * square [u-r, u+r]^2 (3D-GS; the paper's baseline).  ELLIPSE: those of them
+ * that the ellipse alpha >= Th meets -- with the blending conic, q <= Q =
+ * 2 ln(opacity / Th), Th = tau in plain mode and Eq. 10 in AdaGScale mode --
+ * tested against the rectangle spanned by the tile's pixel centres: the exact
+ * footprint-tile intersection of the FlashGS-style renderer the paper's
+ * implementation builds on.  In plain mode it drops only tiles whose pixels all
+ * have alpha < tau, so the image is unchanged. */
+typedef enum { AGS_TILE_SQUARE = 0, AGS_TILE_ELLIPSE = 1 } ags_tile_test;
+
 /* Pinhole camera (host struct).  viewmat is the row-major 3x4 world->camera
  * transform (+x right, +y down, +z forward): t = R m + t_cam.  The EWA
  * frustum clamp uses tan(fov/2) = 0.5*width/fx and 0.5*height/fy. */
@@ -94,6 +104,7 @@ typedef struct {
   float lut_depth_max;      /* depth range [0, lut_depth_max] of the LUT; 100 (Sec. 3.4) */
   float lut[AGS_MAX_LUT_BINS]; /* T_up per depth bin (Sec. 3.2 Eq. 7, Sec. 3.4) */
   float bg[3];              /* background colour added with the final transmittance */
+  int32_t tile_test;        /* ags_tile_test */
 } ags_params;
 
 /* Gaussian parameters (pointers to device memory, SoA fp32). */
@@ -167,11 +178,15 @@ size_t ags_emit_workspace_bytes(int64_t n, int32_t views);
  * `order` (nullable, [views*n]) visits the Gaussians in that order instead
  * (a permutation of 0..views*n-1).  *d_num_pairs (device int64) receives the
  * total.  Pairs beyond `capacity` are not written; the status block then
- * holds AGS_ERR_CAPACITY and the total needed. */
+ * holds AGS_ERR_CAPACITY and the total needed.  flags: AGS_EMIT_ELLIPSE (the
+ * kept tiles of each square, row-major, instead of all of them). */
+#define AGS_EMIT_ELLIPSE 2       /* emission flag: the tiles of the ellipse test (the
+                                    preprocess ran with tile_test AGS_TILE_ELLIPSE; reads
+                                    splat records and tiles_touched) instead of whole squares */
 ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32_t views,
                           const ags_camera* cams, const uint32_t* order,
                           uint64_t* keys, uint32_t* vals, int64_t capacity,
-                          int64_t* d_num_pairs, int64_t* d_status,
+                          int64_t* d_num_pairs, int64_t* d_status, int32_t flags,
                           void* ws, size_t ws_bytes, void* stream);
 
 /* Scratch bytes needed by ags_emit_tile_pairs for views*n Gaussian-views
@@ -191,7 +206,8 @@ size_t ags_emit_tile_workspace_bytes(int64_t n, int32_t views);
  * Gaussian-view, then the pairs in blocks of a fixed number of pairs (balanced
  * however the tile counts cluster in depth order); flags AGS_EMIT_SINGLE_PASS
  * selects the single fused pass of ags_emit_pairs instead.  Same pairs either
- * way.  Workspace: ags_emit_tile_workspace_bytes, 16-byte aligned. */
+ * way.  AGS_EMIT_ELLIPSE as for ags_emit_pairs.  Workspace:
+ * ags_emit_tile_workspace_bytes, 16-byte aligned. */
 #define AGS_EMIT_SINGLE_PASS 1  /* ags_emit_tile_pairs flag: one fused scan-and-emit pass over
                                    partitions of Gaussian-views (faster when the tile counts
                                    are spread evenly along the order) */
@@ -225,7 +241,8 @@ int64_t ags_emit_pairs_noalloc_max_gaussians(void);
  * and forbids it to allocate, or code calling this C ABI from a language with
  * no CUDA allocator binding -- and so cannot provide the workspace that
  * ags_emit_pairs needs.  Arguments and results are those of ags_emit_pairs
- * without `ws`/`ws_bytes`; the caller still passes every input and output.
+ * without `flags` (whole squares) and `ws`/`ws_bytes`; the caller still
+ * passes every input and output.
  * The look-back scratch is a library-owned static device array of
  * 256 + 8 * (2^24 / 1024) bytes (about 128 KiB), held by every GPU that loads
  * the library until the process exits; views*n above

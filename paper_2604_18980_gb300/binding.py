@@ -21,6 +21,7 @@ AGS_MAX_VIEWS = 32
 AGS_MAX_LUT_BINS = 32
 AGS_MAX_PAIRS = 1 << 30
 AGS_SCALE_PLAIN, AGS_SCALE_ADAGSCALE = 0, 1
+AGS_TILE_SQUARE, AGS_TILE_ELLIPSE = 0, 1
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "pair capacity exceeded", 3: "bounded device wait timed out",
                 4: "CUDA error", 5: "non-finite Gaussian parameters culled"}
 AGS_OK, AGS_ERR_INVALID_ARG, AGS_ERR_CAPACITY, AGS_ERR_TIMEOUT, AGS_ERR_CUDA, AGS_ERR_NUMERIC = range(6)
@@ -49,7 +50,7 @@ class AgsCamera(ctypes.Structure):
 class AgsParams(ctypes.Structure):
     _fields_ = [("scale_mode", _I32), ("sh_degree", _I32), ("lut_bins", _I32), ("K", _F), ("tau", _F),
                 ("t_min", _F), ("alpha_max", _F), ("lut_depth_max", _F), ("lut", _F * AGS_MAX_LUT_BINS),
-                ("bg", _F * 3)]
+                ("bg", _F * 3), ("tile_test", _I32)]
 
 
 class AgsGaussians(ctypes.Structure):
@@ -67,7 +68,7 @@ EXPORTS = {
     "ags_status_string": ([_I32], ctypes.c_char_p),
     "ags_preprocess": ([_P, _P, _I32, _P, _P, _P, _P], _I32),
     "ags_emit_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
-    "ags_emit_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P], _I32),
+    "ags_emit_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _I64, _P, _P, _I32, _P, ctypes.c_size_t, _P], _I32),
     "ags_emit_tile_pairs": ([_P, _I64, _I32, _P, _P, _P, _P, _P, _I64, _P, _P, _I32, _P, ctypes.c_size_t, _P],
                             _I32),
     "ags_compact_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
@@ -150,9 +151,10 @@ def cameras(cams) -> ctypes.Array:
 
 def params(scale_mode: int = AGS_SCALE_PLAIN, K: float = 0.0, lut=None, sh_degree: int = 3, bg=(0.0, 0.0, 0.0),
            tau: float = 1.0 / 255.0, t_min: float = 1e-4, alpha_max: float = 0.99, lut_bins: int = 20,
-           lut_depth_max: float = 100.0) -> AgsParams:
+           lut_depth_max: float = 100.0, tile_test: int = AGS_TILE_SQUARE) -> AgsParams:
     p = AgsParams()
     p.scale_mode, p.sh_degree, p.lut_bins = int(scale_mode), int(sh_degree), int(lut_bins)
+    p.tile_test = int(tile_test)
     p.K, p.tau, p.t_min, p.alpha_max, p.lut_depth_max = float(K), float(tau), float(t_min), float(alpha_max), \
         float(lut_depth_max)
     lut = np.ones(lut_bins, dtype=np.float32) if lut is None else np.asarray(lut, dtype=np.float32)
@@ -220,11 +222,15 @@ def ags_emit_workspace_bytes(n: int, views: int) -> int:
     return int(lib().ags_emit_workspace_bytes(int(n), int(views)))
 
 
-def ags_emit_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, ws, order=None, stream=None):
+AGS_EMIT_ELLIPSE = 2
+
+
+def ags_emit_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, ws, order=None, flags=0,
+                   stream=None):
     pr = projected(proj)
     cs = cameras(cams)
     _ok(lib().ags_emit_pairs(ctypes.byref(pr), int(n), len(cams), cs, ptr(order), ptr(keys), ptr(vals),
-                             int(capacity), ptr(d_num_pairs), ptr(d_status), ptr(ws),
+                             int(capacity), ptr(d_num_pairs), ptr(d_status), int(flags), ptr(ws),
                              ws.numel() * ws.element_size() if ws is not None else 0, stream_handle(stream)),
         "ags_emit_pairs")
 

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "ags_internal.cuh"
+#include "ellipse.cuh"
 
 namespace ags {
 
@@ -34,6 +35,14 @@ constexpr uint64_t kValMask = (1ull << 62) - 1;
 constexpr int kTileChunk = 2048;                          // pairs per block of the two-pass emission
 constexpr int64_t kTileChunksMax = ((int64_t)AGS_MAX_PAIRS + kTileChunk - 1) / kTileChunk + 1;
 
+// Inputs of the ellipse tile test's enumeration; splat == nullptr means whole
+// squares (the rectangle records alone decide the tiles).
+struct EllipseSrc {
+  const float4* splat;       // splat records (centre, conic, opacity, Th)
+  const uint32_t* touched;   // kept tiles per Gaussian-view (from the preprocess)
+  int W, H;
+};
+
 // Pair key of a tile: 64-bit keys append the depth bits, 32-bit keys are the tile alone.
 __device__ __forceinline__ void make_key(uint32_t tile, uint32_t dbits, uint64_t& k) {
   k = ((uint64_t)tile << 32) | dbits;
@@ -47,7 +56,7 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
             K* __restrict__ keys,
             uint32_t* __restrict__ vals, int64_t capacity, int64_t* d_num_pairs, int64_t* status,
             uint64_t* part_status, uint32_t* counter, uint4* __restrict__ recs,
-            uint32_t* __restrict__ chunk_start) {
+            uint32_t* __restrict__ chunk_start, EllipseSrc ell) {
   __shared__ uint32_t s_base[kEmitPart];   // key high word of the rectangle's first tile
   __shared__ uint32_t s_w[kEmitPart];      // rectangle width in tiles
   __shared__ uint32_t s_dbits[kEmitPart];  // depth bits
@@ -85,7 +94,7 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
       uint2 r = __ldg(rect + e);
       uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
       uint32_t w = x1 - x0;
-      c = w * (y1 - y0);
+      c = ell.splat ? __ldg(ell.touched + e) : w * (y1 - y0);
       uint32_t view = e / n;
       s_base[li] = view * tiles_per_view + y0 * gx + x0;
       s_w[li] = w;
@@ -204,22 +213,39 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
         if (s_off[mid] <= j0) lo = mid; else hi = mid;
       }
       uint32_t r = j0 - s_off[lo];
-      uint32_t w = s_w[lo];
-      uint32_t ry = r / w, rx = r - ry * w;
-#pragma unroll
-      for (int k = 0; k < kEmitRun; k++) {
-        const uint32_t j = j0 + k;
-        if (j >= agg) break;
-        while (j >= s_off[lo + 1]) {          // next Gaussian with pairs
-          lo++;
-          w = s_w[lo];
-          rx = 0;
-          ry = 0;
+      if (ell.splat) {                        // the ellipse test's tiles, row by row
+        EllipseWalk wk;
+        wk.start(ell.splat, rect, s_idx[lo], n, tiles_per_view, ell.W, ell.H, r);
+#pragma unroll 1
+        for (int k = 0; k < kEmitRun; k++) {
+          const uint32_t j = j0 + k;
+          if (j >= agg) break;
+          if (j >= s_off[lo + 1]) {           // next Gaussian with pairs
+            do lo++; while (j >= s_off[lo + 1]);
+            wk.start(ell.splat, rect, s_idx[lo], n, tiles_per_view, ell.W, ell.H, j - s_off[lo]);
+          }
+          make_key(wk.tile(gx), sizeof(K) == 8 ? s_dbits[lo] : 0u, s_key[warp][lane * kEmitStride + k]);
+          s_val[warp][lane * kEmitStride + k] = s_idx[lo];
+          wk.next();
         }
-        const uint32_t tile = s_base[lo] + ry * gx + rx;
-        make_key(tile, sizeof(K) == 8 ? s_dbits[lo] : 0u, s_key[warp][lane * kEmitStride + k]);
-        s_val[warp][lane * kEmitStride + k] = s_idx[lo];
-        if (++rx == w) { rx = 0; ry++; }
+      } else {
+        uint32_t w = s_w[lo];
+        uint32_t ry = r / w, rx = r - ry * w;
+#pragma unroll
+        for (int k = 0; k < kEmitRun; k++) {
+          const uint32_t j = j0 + k;
+          if (j >= agg) break;
+          while (j >= s_off[lo + 1]) {          // next Gaussian with pairs
+            lo++;
+            w = s_w[lo];
+            rx = 0;
+            ry = 0;
+          }
+          const uint32_t tile = s_base[lo] + ry * gx + rx;
+          make_key(tile, sizeof(K) == 8 ? s_dbits[lo] : 0u, s_key[warp][lane * kEmitStride + k]);
+          s_val[warp][lane * kEmitStride + k] = s_idx[lo];
+          if (++rx == w) { rx = 0; ry++; }
+        }
       }
     }
     __syncwarp();
@@ -262,7 +288,8 @@ struct TileEmitSmem {
 __global__ void __launch_bounds__(kEmitThreads)
 tile_emit_kernel(const uint4* __restrict__ recs, const uint32_t* __restrict__ chunk_start, const int64_t* d_entries,
                  int64_t entries_bound, const int64_t* d_num_pairs, int64_t capacity, uint32_t gx,
-                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const uint2* __restrict__ rect, uint32_t n,
+                 uint32_t tiles_per_view, EllipseSrc ell) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileEmitSmem& S = *reinterpret_cast<TileEmitSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -312,21 +339,42 @@ tile_emit_kernel(const uint4* __restrict__ recs, const uint32_t* __restrict__ ch
           uint4 rc = S.rec[lo];
           uint32_t nxt = S.rec[lo + 1].x;
           const uint32_t r = j0 - rc.x;
-          uint32_t ry = r / rc.w, rx = r - ry * rc.w;
-#pragma unroll
-          for (int k = 0; k < kEmitRun; k++) {
-            const uint32_t j = j0 + k;
-            if (j >= wend) break;
-            while (j >= nxt) {                     // next record with pairs (j < wend <= rec[m].x)
-              lo++;
-              rc = S.rec[lo];
-              nxt = S.rec[lo + 1].x;
-              rx = 0;
-              ry = 0;
+          if (ell.splat) {                         // the ellipse test's tiles, row by row
+            EllipseWalk wk;
+            wk.start(ell.splat, rect, rc.y, n, tiles_per_view, ell.W, ell.H, r);
+#pragma unroll 1
+            for (int k = 0; k < kEmitRun; k++) {
+              const uint32_t j = j0 + k;
+              if (j >= wend) break;
+              if (j >= nxt) {                      // next record with pairs (j < wend <= rec[m].x)
+                do {
+                  lo++;
+                  nxt = S.rec[lo + 1].x;
+                } while (j >= nxt);
+                rc = S.rec[lo];
+                wk.start(ell.splat, rect, rc.y, n, tiles_per_view, ell.W, ell.H, j - rc.x);
+              }
+              S.key[warp][lane * kEmitStride + k] = wk.tile(gx);
+              S.val[warp][lane * kEmitStride + k] = rc.y;
+              wk.next();
             }
-            S.key[warp][lane * kEmitStride + k] = rc.z + ry * gx + rx;
-            S.val[warp][lane * kEmitStride + k] = rc.y;
-            if (++rx == rc.w) { rx = 0; ry++; }
+          } else {
+            uint32_t ry = r / rc.w, rx = r - ry * rc.w;
+#pragma unroll
+            for (int k = 0; k < kEmitRun; k++) {
+              const uint32_t j = j0 + k;
+              if (j >= wend) break;
+              while (j >= nxt) {                     // next record with pairs (j < wend <= rec[m].x)
+                lo++;
+                rc = S.rec[lo];
+                nxt = S.rec[lo + 1].x;
+                rx = 0;
+                ry = 0;
+              }
+              S.key[warp][lane * kEmitStride + k] = rc.z + ry * gx + rx;
+              S.val[warp][lane * kEmitStride + k] = rc.y;
+              if (++rx == rc.w) { rx = 0; ry++; }
+            }
           }
         }
         __syncwarp();
@@ -347,6 +395,16 @@ tile_emit_kernel(const uint4* __restrict__ recs, const uint32_t* __restrict__ ch
 
 static size_t emit_parts(int64_t total) { return (size_t)((total + kEmitPart - 1) / kEmitPart); }
 
+// The ellipse enumeration's inputs for AGS_EMIT_ELLIPSE (or whole squares).
+static ags_status ellipse_src(const ags_projected* proj, const CamBatch& cb, int32_t flags, EllipseSrc* out) {
+  *out = EllipseSrc{nullptr, nullptr, cb.c[0].W, cb.c[0].H};
+  if (!(flags & AGS_EMIT_ELLIPSE)) return AGS_OK;
+  if (!proj->splat || !proj->tiles_touched || ((uintptr_t)proj->splat & 15u)) return AGS_ERR_INVALID_ARG;
+  out->splat = reinterpret_cast<const float4*>(proj->splat);
+  out->touched = proj->tiles_touched;
+  return AGS_OK;
+}
+
 }  // namespace ags
 
 extern "C" size_t ags_emit_workspace_bytes(int64_t n, int32_t views) {
@@ -356,8 +414,8 @@ extern "C" size_t ags_emit_workspace_bytes(int64_t n, int32_t views) {
 
 extern "C" ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32_t views, const ags_camera* cams,
                                      const uint32_t* order, uint64_t* keys, uint32_t* vals, int64_t capacity,
-                                     int64_t* d_num_pairs, int64_t* d_status, void* ws, size_t ws_bytes,
-                                     void* stream) {
+                                     int64_t* d_num_pairs, int64_t* d_status, int32_t flags, void* ws,
+                                     size_t ws_bytes, void* stream) {
   using namespace ags;
   if (!proj || !d_num_pairs || !d_status || n < 0 || capacity < 0 || capacity > AGS_MAX_PAIRS)
     return AGS_ERR_INVALID_ARG;
@@ -369,6 +427,10 @@ extern "C" ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32
   cudaStream_t st = (cudaStream_t)stream;
   if (total == 0) return launch_status(cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st));
   if (!proj->rect || !proj->depth || (capacity > 0 && (!keys || !vals))) return AGS_ERR_INVALID_ARG;
+  if (flags & ~AGS_EMIT_ELLIPSE) return AGS_ERR_INVALID_ARG;
+  EllipseSrc ell;
+  s = ellipse_src(proj, cb, flags, &ell);
+  if (s != AGS_OK) return s;
   if (!ws || ws_bytes < ags_emit_workspace_bytes(n, views) || ((uintptr_t)ws & 7u)) return AGS_ERR_INVALID_ARG;
   const size_t parts = emit_parts(total);
   uint32_t tiles_per_view = (uint32_t)cb.c[0].gx * (uint32_t)cb.c[0].gy;
@@ -379,7 +441,7 @@ extern "C" ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32
   uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
   emit_kernel<uint64_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
       reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, nullptr, (uint32_t)n, tiles_per_view,
-      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr);
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr, ell);
   return launch_status(cudaGetLastError());
 }
 
@@ -405,7 +467,10 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
   cudaStream_t st = (cudaStream_t)stream;
   if (total == 0) return launch_status(cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st));
   if (!proj->rect || (capacity > 0 && (!keys || !vals))) return AGS_ERR_INVALID_ARG;
-  if (flags & ~AGS_EMIT_SINGLE_PASS) return AGS_ERR_INVALID_ARG;
+  if (flags & ~(AGS_EMIT_SINGLE_PASS | AGS_EMIT_ELLIPSE)) return AGS_ERR_INVALID_ARG;
+  EllipseSrc ell;
+  s = ellipse_src(proj, cb, flags, &ell);
+  if (s != AGS_OK) return s;
   if (!ws || ws_bytes < ags_emit_tile_workspace_bytes(n, views) || ((uintptr_t)ws & 15u)) return AGS_ERR_INVALID_ARG;
   const size_t parts = emit_parts(total);
   uint32_t tiles_per_view = (uint32_t)cb.c[0].gx * (uint32_t)cb.c[0].gy;
@@ -421,16 +486,17 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
     emit_kernel<uint32_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
         reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, d_entries, (uint32_t)n,
         tiles_per_view, (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter,
-        nullptr, nullptr);
+        nullptr, nullptr, ell);
     return launch_status(cudaGetLastError());
   }
   // phase 1: per-entry records and the pair count
   emit_kernel<uint32_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
       reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, d_entries, (uint32_t)n, tiles_per_view,
-      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, recs, chunk_start);
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, recs, chunk_start,
+      ell);
   e = cudaGetLastError();
   if (e != cudaSuccess || capacity == 0) return launch_status(e);
-  // phase 2: the pairs, in blocks of 1024 (grid-stride over the device count)
+  // phase 2: the pairs, in blocks of kTileChunk (grid-stride over the device count)
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -440,7 +506,9 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
   e = cudaFuncSetAttribute(tile_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   tile_emit_kernel<<<grid, kEmitThreads, smem, st>>>(recs, chunk_start, d_entries, total, d_num_pairs, capacity,
-                                                     (uint32_t)cb.c[0].gx, keys, vals);
+                                                     (uint32_t)cb.c[0].gx, keys, vals,
+                                                     reinterpret_cast<const uint2*>(proj->rect), (uint32_t)n,
+                                                     tiles_per_view, ell);
   return launch_status(cudaGetLastError());
 }
 
@@ -507,6 +575,7 @@ extern "C" ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t 
   uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
   emit_kernel<uint64_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
       reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, nullptr, (uint32_t)n, tiles_per_view,
-      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr);
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr,
+      EllipseSrc{nullptr, nullptr, cb.c[0].W, cb.c[0].H});
   return launch_status(cudaGetLastError());
 }

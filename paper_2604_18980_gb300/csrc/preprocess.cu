@@ -11,6 +11,7 @@
 // survives and touches a tile (from DRAM the first time, then from cache).  Outputs per view and
 // survivor: a 48-byte splat record (three 16-byte stores), depth, the tile
 // rectangle (one 8-byte store), the tile count, a flag byte and the depth key.
+#include "ellipse.cuh"
 #include "project.cuh"
 
 namespace ags {
@@ -107,7 +108,17 @@ __global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn
       tile_span(pj.u - rf, pj.u + rf, C.W, x0, x1);
       tile_span(pj.v - rf, pj.v + rf, C.H, y0, y1);
     }
-    const uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+    uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+    if (P.tile_test == AGS_TILE_ELLIPSE && touched) {
+      // the tiles of the square that the alpha >= Th ellipse reaches
+      const EllipseTiles E{pj.u, pj.v, pj.A, pj.B, pj.C, ellipse_level(F.opac, th), x0, x1, C.W, C.H};
+      touched = 0u;
+      for (int ty = y0; ty < y1; ty++) {
+        int lo, hi;
+        ellipse_row_span(E, ty, lo, hi);
+        if (lo <= hi) touched += (uint32_t)(hi - lo + 1);
+      }
+    }
     if (touched == 0u) { write_culled(out, e); continue; }
 
     // colour: SH at the world-space direction from the camera centre (the

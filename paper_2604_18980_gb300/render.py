@@ -51,7 +51,7 @@ class Renderer:
                  sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 9,
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
                  presort: bool = True, pair_rank_or: bool = True, emit_two_pass: bool = True,
-                 keep_state: bool = True):
+                 keep_state: bool = True, tile_test: int = B.AGS_TILE_SQUARE):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -63,6 +63,8 @@ class Renderer:
         self.presort = presort
         self.pair_rank_or = pair_rank_or
         self.emit_two_pass = emit_two_pass
+        self.tile_test = tile_test
+        self.emit_flags = B.AGS_EMIT_ELLIPSE if tile_test == B.AGS_TILE_ELLIPSE else 0
         self.keep_state = keep_state or want_backward   # final_T / n_contrib for the backward
         self.set_params(scale_mode, K, lut, sh_degree, bg)
         dev, V, n = self.device, self.V, self.n
@@ -102,11 +104,11 @@ class Renderer:
     # -- configuration -------------------------------------------------------
     def set_params(self, scale_mode=None, K=None, lut=None, sh_degree=None, bg=None):
         prev = getattr(self, "_pargs", dict(scale_mode=B.AGS_SCALE_PLAIN, K=0.0, lut=None, sh_degree=3,
-                                            bg=(0.0, 0.0, 0.0)))
+                                            bg=(0.0, 0.0, 0.0), tile_test=getattr(self, "tile_test", 0)))
         args = dict(scale_mode=prev["scale_mode"] if scale_mode is None else scale_mode,
                     K=prev["K"] if K is None else K, lut=prev["lut"] if lut is None else lut,
                     sh_degree=prev["sh_degree"] if sh_degree is None else sh_degree,
-                    bg=prev["bg"] if bg is None else bg)
+                    bg=prev["bg"] if bg is None else bg, tile_test=prev["tile_test"])
         self._pargs = args
         self.params = B.params(**args)
 
@@ -126,7 +128,8 @@ class Renderer:
         """Preprocess + emission with zero capacity; returns the pair count (synchronises)."""
         B.ags_status_reset(self.status)
         B.ags_preprocess(self.scene, self.cams, self.params, self.proj, self.status)
-        B.ags_emit_pairs(self.proj, self.n, self.cams, None, None, 0, self.num_pairs, self.status, self.ws_emit)
+        B.ags_emit_pairs(self.proj, self.n, self.cams, None, None, 0, self.num_pairs, self.status, self.ws_emit,
+                         flags=self.emit_flags)
         B.ags_status_reset(self.status)
         return int(self.num_pairs.item())
 
@@ -169,10 +172,10 @@ class Renderer:
             B.ags_emit_tile_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity,
                                   self.num_pairs, self.status, self.ws_emit, order=self.emit_order,
                                   order_count=self.n_visible,
-                                  flags=0 if self.emit_two_pass else B.AGS_EMIT_SINGLE_PASS)
+                                  flags=self.emit_flags | (0 if self.emit_two_pass else B.AGS_EMIT_SINGLE_PASS))
         else:
             B.ags_emit_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity, self.num_pairs,
-                             self.status, self.ws_emit)
+                             self.status, self.ws_emit, flags=self.emit_flags)
 
     def sort(self):
         """Stable sort of the pairs by tile (and depth); only the values and the

@@ -15,20 +15,20 @@ PSNR_MIN = 60.0         # dB, over all pixels
 
 
 def gpu_render(scene_np, cams, scale_mode=0, K=0.0, lut=None, bg=(0.0, 0.0, 0.0), sh_degree=3, capacity=None,
-               digit_bits=8, want_stats=False):
+               digit_bits=8, want_stats=False, tile_test=0, **knobs):
     scene = R.scene_to_device(scene_np)
     r = R.Renderer(scene, cams, scale_mode, K, lut, sh_degree, bg, capacity=capacity, digit_bits=digit_bits,
-                   want_stats=want_stats)
+                   want_stats=want_stats, tile_test=tile_test, **knobs)
     r.forward()
     r.check()
     return r
 
 
-def oracle_params(cam, scale_mode=0, K=0.0, lut=None, bg=(0.0, 0.0, 0.0), sh_degree=3):
+def oracle_params(cam, scale_mode=0, K=0.0, lut=None, bg=(0.0, 0.0, 0.0), sh_degree=3, tile_test=0):
     lut32 = None if lut is None else np.asarray(lut, dtype=np.float32).astype(np.float64)
     return oracle.params(cam, scale_mode=scale_mode, K=float(np.float32(K)), lut=lut32, sh_degree=sh_degree,
                          bg=tuple(float(np.float32(b)) for b in bg), tau=float(np.float32(1.0 / 255.0)),
-                         t_min=float(np.float32(1e-4)), alpha_max=float(np.float32(0.99)))
+                         t_min=float(np.float32(1e-4)), alpha_max=float(np.float32(0.99)), tile_test=tile_test)
 
 
 def gpu_features(r, view=0):
@@ -53,6 +53,9 @@ def compare_features(r, orc_out, view=0):
     o_rect = irec[:, [oracle.I_X0, oracle.I_Y0, oracle.I_X1, oracle.I_Y1]].astype(np.int64)
     bad = both & np.any(o_rect != rect, axis=1)
     assert not bad.any(), "rect mismatch: %s" % np.nonzero(bad)[0][:10]
+    touched = r.proj["tiles_touched"].view(r.V, r.n)[view].cpu().numpy().astype(np.int64)
+    bad = both & (touched != irec[:, oracle.I_TOUCHED])
+    assert not bad.any(), "tile count mismatch: %s" % np.nonzero(bad)[0][:10]
     W = r.W
     du = np.abs(sp[both, 0] - dbl[both, oracle.F_U])
     dv = np.abs(sp[both, 1] - dbl[both, oracle.F_V])

@@ -28,11 +28,11 @@ def _c1(n=16384, W=256, H=256, views=1):
     return scene, cams
 
 
-def _full_check(scene, cams, mode, K, lut=None, bg=(0.0, 0.0, 0.0)):
-    r = gpu_render(scene, cams, mode, K, lut, bg)
+def _full_check(scene, cams, mode, K, lut=None, bg=(0.0, 0.0, 0.0), tile_test=0, **knobs):
+    r = gpu_render(scene, cams, mode, K, lut, bg, tile_test=tile_test, **knobs)
     outs, stats = [], []
     for v, cam in enumerate(cams):
-        par = oracle_params(cam, mode, K, lut, bg)
+        par = oracle_params(cam, mode, K, lut, bg, tile_test=tile_test)
         oo = oracle.render(scene, cam, par)
         outs.append(oo)
         stats.append(compare_features(r, oo, v))
@@ -48,6 +48,34 @@ def test_c1_parity(mode, K):
     lut = np.linspace(1.0, 0.4, 20).astype(np.float32)
     r, outs, stats, ties = _full_check(scene, cams, mode, K, lut)
     assert r.pairs() > 0
+
+
+@pytest.mark.parametrize("mode,K,knobs", [(0, 0.0, {}), (1, 0.3, {}), (1, 0.3, dict(presort=False)),
+                                          (1, 3.0, dict(emit_two_pass=False))])
+def test_c1_parity_ellipse_tiles(mode, K, knobs):
+    """The ellipse tile test: per-Gaussian kept-tile counts, per-tile lists and
+    images against the oracle's exact per-tile minimum, on every emission path."""
+    scene, cams = _c1(n=12000, W=256, H=200, views=2)
+    lut = np.linspace(1.0, 0.4, 20).astype(np.float32)
+    r, outs, stats, ties = _full_check(scene, cams, mode, K, lut, tile_test=B.AGS_TILE_ELLIPSE, **knobs)
+    sq = gpu_render(scene, cams, mode, K, lut, tile_test=B.AGS_TILE_SQUARE, **knobs)
+    assert 0 < r.pairs() < sq.pairs()
+
+
+def test_plain_ellipse_tiles_render_the_square_image():
+    """Plain mode: the ellipse test drops only tiles whose pixels all have
+    alpha < tau, so the image is bit-identical with fewer pairs (ragged size,
+    background)."""
+    scene, cams = _c1(n=6000, W=173, H=94, views=2)
+    a = gpu_render(scene, cams, 0, 0.0, bg=(0.1, 0.3, 0.7))
+    b = gpu_render(scene, cams, 0, 0.0, bg=(0.1, 0.3, 0.7), tile_test=B.AGS_TILE_ELLIPSE)
+    assert torch.equal(a.image, b.image)
+    assert b.pairs() < a.pairs()
+    ka, va = gpu_pairs(a)
+    kb, vb = gpu_pairs(b)
+    pa = set(zip((ka >> np.uint64(32)).tolist(), va.tolist()))
+    pb = set(zip((kb >> np.uint64(32)).tolist(), vb.tolist()))
+    assert pb <= pa
 
 
 def test_ragged_sizes_and_background():

@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_header(lib):
     # sizes implied by the header's field lists (all 4- or 8-byte fields)
     assert ctypes.sizeof(B.AgsCamera) == 4 * (2 + 4 + 12 + 3 + 1)
-    assert ctypes.sizeof(B.AgsParams) == 4 * (3 + 5 + 32 + 3)
+    assert ctypes.sizeof(B.AgsParams) == 4 * (3 + 5 + 32 + 3 + 1)
     assert ctypes.sizeof(B.AgsGaussians) == 8 * 6
     assert ctypes.sizeof(B.AgsProjected) == 8 * 6
 
@@ -90,6 +90,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
     bad = B.params(scale_mode=2)
     assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
+    bad = B.params(tile_test=2)
+    assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
     # null outputs
     assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(par), ctypes.byref(pr), st, None) == 1
     # sort: bad digit width, capacity beyond the limit, missing workspace
@@ -114,7 +116,12 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert L.ags_sort(ctypes.c_void_p(24), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
                       10, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st, ctypes.c_void_p(256), 1 << 20, None) == 1
     # emit: workspace too small
-    assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, None, 0, None) == 1
+    assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, 0, None, 0, None) == 1
+    # the ellipse flag needs the splat records and tile counts
+    assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, 2, ctypes.c_void_p(256),
+                            1 << 20, None) == 1
+    assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, 4, ctypes.c_void_p(256),
+                            1 << 20, None) == 1
     assert L.ags_emit_tile_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, None, 0, npairs, st, 0, None, 0,
                                  None) == 1
     # compaction: zero views, missing workspace, unaligned flags
