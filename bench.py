@@ -384,6 +384,34 @@ def run_ours(args, world, rank, local):
                           "fps_eager": world * V * 1000.0 / ms_k})
             del rk, img_k
         extras["k_sweep"] = sweep
+
+        # the ellipse tile test (tiles of the square that the alpha >= Th ellipse meets),
+        # AdaGScale at its own calibrated K and plain (the same image as plain 3-sigma)
+        if "K_ellipse" in wp:
+            ell = {}
+            for label, mode, k in (("adagscale", B.AGS_SCALE_ADAGSCALE, wp["K_ellipse"]), ("plain", B.AGS_SCALE_PLAIN, 0.0)):
+                try:
+                    re_ = R.Renderer(sc, cams, mode, k, wp["lut"] if mode else None, keep_state=False,
+                                     tile_test=B.AGS_TILE_ELLIPSE, **knobs)
+                except ValueError:
+                    ell[label] = {"skipped": "more pairs than one sort call takes"}
+                    continue
+                img_e = re_.forward().clone()
+                g = re_.capture()
+                for _ in range(args.warmup):
+                    g.replay()
+                barrier()
+                a.record(stream)
+                for _ in range(args.steps):
+                    g.replay()
+                b.record(stream)
+                barrier()
+                re_.check()
+                ms_e = max_over_ranks(a.elapsed_time(b)) / args.steps
+                ell[label] = {"fps": world * V * 1000.0 / ms_e, "ms_per_step": ms_e, "pairs_per_frame": re_.pairs() / V,
+                              "K": k, "psnr_vs_plain_db": C.psnr(img_e, img_p)}
+                del re_, g, img_e
+            extras["ellipse_tiles"] = ell
         del img_p
 
         # end to end through host buffers: params H2D, render, images D2H, every step

@@ -66,15 +66,17 @@ def calibrate_lut(scene: dict, calib_cams: list, sh_degree: int = 3, lut_bins: i
 
 
 def search_K(scene: dict, calib_cams: list, lut, target_psnr: float, sh_degree: int = 3, batch: int = 8,
-             k_lo: float = 0.0, k_hi: float = 4096.0, iters: int = 16) -> tuple:
-    """Largest K (geometric bisection) whose AdaGScale renders keep PSNR >= target vs plain."""
+             k_lo: float = 0.0, k_hi: float = 4096.0, iters: int = 16, tile_test: int = B.AGS_TILE_SQUARE) -> tuple:
+    """Largest K (geometric bisection) whose AdaGScale renders keep PSNR >= target vs plain
+    (with the given tile test; the plain reference is the same with either test)."""
     groups = [calib_cams[s:s + batch] for s in range(0, len(calib_cams), batch)]
     plains, rens = [], []
     for cams in groups:
         r = R.Renderer(scene, cams, B.AGS_SCALE_PLAIN, sh_degree=sh_degree)
         plains.append(r.forward().clone())
         r.check()
-        ra = R.Renderer(scene, cams, B.AGS_SCALE_ADAGSCALE, 0.0, lut, sh_degree, capacity=r.capacity)
+        ra = R.Renderer(scene, cams, B.AGS_SCALE_ADAGSCALE, 0.0, lut, sh_degree, capacity=r.capacity,
+                        tile_test=tile_test)
         rens.append(ra)
 
     def score(K):
@@ -105,8 +107,10 @@ def calibrate_workload(name: str, device="cuda") -> dict:
     lut = calibrate_lut(sc, calib)
     target = TARGET_PSNR[name[:2]]
     K, p = search_K(sc, calib, lut, target)
+    # the ellipse tile test drops more of each footprint: its own K for the same target
+    Ke, pe = search_K(sc, calib, lut, target, tile_test=B.AGS_TILE_ELLIPSE)
     return dict(K=float(np.float32(K)), lut=[float(x) for x in lut], target_psnr=target, calib_psnr=p,
-                calibration_views=len(calib))
+                calibration_views=len(calib), K_ellipse=float(np.float32(Ke)), calib_psnr_ellipse=pe)
 
 
 def load_params(name: str) -> dict | None:
@@ -119,8 +123,18 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c2_clusters1m_1080p")
     ap.add_argument("--write", action="store_true")
+    ap.add_argument("--ellipse-only", action="store_true",
+                    help="keep the stored LUT and K; add the K of the ellipse tile test")
     a = ap.parse_args()
-    out = calibrate_workload(a.workload)
+    if a.ellipse_only:
+        out = dict(load_params(a.workload))
+        scene, _, calib = synth.workload(a.workload)
+        sc = R.scene_to_device(scene)
+        Ke, pe = search_K(sc, calib, np.asarray(out["lut"], np.float32), out["target_psnr"],
+                          tile_test=B.AGS_TILE_ELLIPSE)
+        out.update(K_ellipse=float(np.float32(Ke)), calib_psnr_ellipse=pe)
+    else:
+        out = calibrate_workload(a.workload)
     print(json.dumps({a.workload: out}, indent=1))
     if a.write:
         data = json.load(open(PARAMS_FILE)) if os.path.exists(PARAMS_FILE) else {}

@@ -23,54 +23,106 @@ struct EllipseTiles {
 // Q from the stored opacity and threshold (the same expression everywhere).
 __device__ __forceinline__ float ellipse_level(float opacity, float th) { return 2.f * logf(opacity / th); }
 
+// A tile is kept when the minimum of q over its pixel-centre rectangle is at
+// most Q plus a relative 1e-5: a margin far above the fp32 rounding of the
+// blend's own alpha >= tau test, so that in plain mode no tile holding an
+// accepted pixel is ever dropped.
+__device__ __forceinline__ float ellipse_keep_level(float Q) { return Q + 1e-5f * fmaxf(Q, 1.f); }
+
 __device__ __forceinline__ float tile_min_q(const EllipseTiles& E, int tx, int ty) {
   const float xl = (float)(kTile * tx) - E.u, xh = (float)min(kTile * tx + kTile - 1, E.W - 1) - E.u;
   const float yl = (float)(kTile * ty) - E.v, yh = (float)min(kTile * ty + kTile - 1, E.H - 1) - E.v;
   return rect_min_quad(E.A, E.B, E.C, xl, xh, yl, yh);
 }
 
-__device__ __forceinline__ bool tile_kept(const EllipseTiles& E, int tx, int ty) { return tile_min_q(E, tx, ty) <= E.Q; }
+__device__ __forceinline__ bool tile_kept(const EllipseTiles& E, float Qk, int tx, int ty) {
+  return tile_min_q(E, tx, ty) <= Qk;
+}
+
+// First kept column in [a, b] when column b is kept (the kept columns of a row
+// are contiguous).  `guess` is tried first with short walks, then bisection.
+__device__ __forceinline__ int first_kept(const EllipseTiles& E, float Qk, int ty, int a, int b, int guess) {
+  int g = min(max(guess, a), b);
+  if (tile_kept(E, Qk, g, ty)) {
+    if (g == a || !tile_kept(E, Qk, g - 1, ty)) return g;
+    b = g - 1;                                  // kept; the first one is in [a, g - 1]
+  } else {
+    if (tile_kept(E, Qk, g + 1, ty)) return g + 1;
+    a = g + 2;                                  // [g + 2, b], b kept
+    if (a > b) return b;
+  }
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (tile_kept(E, Qk, mid, ty)) b = mid; else a = mid + 1;
+  }
+  return a;
+}
+
+// Last kept column in [a, b] when column a is kept.
+__device__ __forceinline__ int last_kept(const EllipseTiles& E, float Qk, int ty, int a, int b, int guess) {
+  int g = min(max(guess, a), b);
+  if (tile_kept(E, Qk, g, ty)) {
+    if (g == b || !tile_kept(E, Qk, g + 1, ty)) return g;
+    a = g + 1;
+  } else {
+    if (tile_kept(E, Qk, g - 1, ty)) return g - 1;
+    b = g - 2;
+    if (a > b) return a;
+  }
+  while (a < b) {
+    const int mid = (a + b + 1) >> 1;
+    if (tile_kept(E, Qk, mid, ty)) a = mid; else b = mid - 1;
+  }
+  return a;
+}
 
 // Kept tiles [lo, hi] of tile row ty (lo > hi when none).  The minimum of q
 // over a tile rectangle is a convex function of the tile's position, so the
 // kept tiles of a row are contiguous around the column where the row band's
-// minimum of q lies: that column (or a neighbour) is tested, then the two ends
-// are found by binary search with the per-tile test.
+// minimum of q lies; that column (or its neighbour across the gap between
+// tiles) decides whether the row has any.  The ends start from the closed-form
+// x-range of the ellipse over the band -- the section of a conic, whose
+// extreme points lie at dy = -+B sqrt(Q / (det C)) -- and are settled by the
+// per-tile test.
 __device__ __forceinline__ void ellipse_row_span(const EllipseTiles& E, int ty, int& lo, int& hi) {
   lo = 1;
   hi = 0;
   if (!(E.Q >= 0.f) || E.x0 >= E.x1) return;
-  // the band's lowest q: dy closest to 0, then dx = -B dy / A
+  const float Qk = ellipse_keep_level(E.Q);
   const float yl = (float)(kTile * ty) - E.v, yh = (float)min(kTile * ty + kTile - 1, E.H - 1) - E.v;
+  // the band's lowest q: dy closest to 0, then dx = -B dy / A
   const float dyc = fminf(fmaxf(0.f, yl), yh);
   const float xc = E.u - E.B * dyc / E.A;
-  int tc = (int)floorf(fminf(fmaxf(xc, -1e9f), 1e9f) / (float)kTile);
-  tc = min(max(tc, E.x0), E.x1 - 1);
-  // best of the column and its neighbours (the minimiser may sit in a gap between tiles)
+  const float fc = floorf(fminf(fmaxf(xc, -1e9f), 1e9f) / (float)kTile);
+  int tc = min(max((int)fc, E.x0), E.x1 - 1);
   int tb = tc;
   float mb = tile_min_q(E, tc, ty);
-  if (tc > E.x0) {
-    const float m = tile_min_q(E, tc - 1, ty);
-    if (m < mb) { mb = m; tb = tc - 1; }
-  }
-  if (tc + 1 < E.x1) {
+  if (xc - (float)(kTile * tc) > (float)(kTile - 1) && tc + 1 < E.x1) {   // minimiser in the gap after tc
     const float m = tile_min_q(E, tc + 1, ty);
     if (m < mb) { mb = m; tb = tc + 1; }
   }
-  if (!(mb <= E.Q)) return;
-  int a = E.x0, b = tb;                // first kept column in [x0, tb]
-  while (a < b) {
-    const int mid = (a + b) >> 1;
-    if (tile_kept(E, mid, ty)) b = mid; else a = mid + 1;
+  if (xc < (float)(kTile * tc) && tc > E.x0) {                              // clamped from the left
+    const float m = tile_min_q(E, tc - 1, ty);
+    if (m < mb) { mb = m; tb = tc - 1; }
   }
-  lo = a;
-  a = tb;
-  b = E.x1 - 1;                        // last kept column in [tb, x1 - 1]
-  while (a < b) {
-    const int mid = (a + b + 1) >> 1;
-    if (tile_kept(E, mid, ty)) a = mid; else b = mid - 1;
+  if (!(mb <= Qk)) return;
+  // closed-form x-range of the ellipse over the band (a guess: fp32, thin ellipses lose digits)
+  int gl = E.x0, gh = E.x1 - 1;
+  const float det = E.A * E.C - E.B * E.B;
+  if (det > 0.f) {
+    const float ymax = sqrtf(E.A * E.Q / det);
+    const float bl = fmaxf(yl, -ymax), bh = fminf(yh, ymax);
+    if (bl <= bh) {
+      const float ds = E.B * sqrtf(E.Q / (det * E.C));
+      const float d1 = fminf(fmaxf(ds, bl), bh), d2 = fminf(fmaxf(-ds, bl), bh);
+      const float xl = E.u + (-E.B * d1 - sqrtf(fmaxf(E.A * E.Q - det * d1 * d1, 0.f))) / E.A;
+      const float xr = E.u + (-E.B * d2 + sqrtf(fmaxf(E.A * E.Q - det * d2 * d2, 0.f))) / E.A;
+      gl = (int)fminf(fmaxf(ceilf((xl - (float)(kTile - 1)) / (float)kTile), -1e6f), 1e6f);
+      gh = (int)fminf(fmaxf(floorf(xr / (float)kTile), -1e6f), 1e6f);
+    }
   }
-  hi = a;
+  lo = first_kept(E, Qk, ty, E.x0, tb, gl);
+  hi = last_kept(E, Qk, ty, tb, E.x1 - 1, gh);
 }
 
 }  // namespace ags

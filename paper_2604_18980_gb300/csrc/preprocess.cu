@@ -51,7 +51,9 @@ __device__ __forceinline__ void tile_span(float lo, float hi, int len, int& t0, 
 
 // kCacheSH: keep the 48 SH coefficients in registers after the first view that
 // needs them (multi-view batches); otherwise re-read them through the caches.
-template <bool kCacheSH>
+// kEllipse: count the tiles of the ellipse tile test instead of whole squares
+// (a separate instance, so that the square path keeps its registers).
+template <bool kCacheSH, bool kEllipse>
 __global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn in, int64_t n, int views,
                                                          const __grid_constant__ CamBatch cams,
                                                          const __grid_constant__ DevParams P, PreOut out,
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn
       tile_span(pj.v - rf, pj.v + rf, C.H, y0, y1);
     }
     uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
-    if (P.tile_test == AGS_TILE_ELLIPSE && touched) {
+    if (kEllipse && touched) {
       // the tiles of the square that the alpha >= Th ellipse reaches
       const EllipseTiles E{pj.u, pj.v, pj.A, pj.B, pj.C, ellipse_level(F.opac, th), x0, x1, C.W, C.H};
       touched = 0u;
@@ -196,7 +198,9 @@ extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* c
   if (((uintptr_t)out->splat & 15u) || ((uintptr_t)out->rect & 7u)) return AGS_ERR_INVALID_ARG;
   PreIn in{g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
   PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags, out->depth_key};
-  auto kern = views > 1 ? preprocess_kernel<true> : preprocess_kernel<false>;
+  const bool ell = dp.tile_test == AGS_TILE_ELLIPSE;
+  auto kern = views > 1 ? (ell ? preprocess_kernel<true, true> : preprocess_kernel<true, false>)
+                        : (ell ? preprocess_kernel<false, true> : preprocess_kernel<false, false>);
   kern<<<(unsigned)((g->n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, g->n, views, cb, dp, po, d_status);
   return launch_status(cudaGetLastError());
 }
