@@ -278,8 +278,110 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
 // views) can push the records of a block past the staging area: the block then
 // continues with further windows, found by a 32-way search of the records'
 // first-pair offsets.
+// Pairs [p0, p1) of the ellipse tile test, enumerated by a whole warp from the
+// records rec[0..m] staged in shared memory (rec[m] a sentinel).  The records
+// that own these pairs are taken 32 at a time, one per lane; the rows of all
+// of them are spread over the lanes (one row per lane per step, the owner found
+// by bisection over the row prefix), so that every row's span is computed once
+// with all lanes busy whatever the Gaussians' sizes; a segmented scan places
+// each row's tiles, each lane stages its row's tiles that fall in [p0, p1)
+// (at most kEmitChunk pairs) in shared memory, and the warp writes them out
+// with coalesced stores.  k_run (32 words of shared memory per warp) carries
+// each record's kept tiles from one step of rows to the next.
+__device__ __forceinline__ void warp_emit_ellipse(const uint4* rec, int m, uint32_t p0, uint32_t p1,
+                                                  const EllipseSrc& ell, const uint2* __restrict__ rect, uint32_t n,
+                                                  uint32_t tiles_per_view, uint32_t gx, uint32_t* __restrict__ keys,
+                                                  uint32_t* __restrict__ vals, uint32_t* k_run, uint32_t* st_key,
+                                                  uint32_t* st_val, int lane) {
+  int lo = 0, hi = m;                              // rec[lo].x <= p0 < rec[hi].x
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (rec[mid].x <= p0) lo = mid; else hi = mid;
+  }
+  for (int eb = lo; eb < m && rec[eb].x < p1;) {
+    // this lane's record of the batch
+    const int ek = eb + lane;
+    const bool in = ek < m && rec[ek].x < p1;
+    const int nb = __popc(__ballot_sync(0xffffffffu, in));   // records start in order: a prefix of the lanes
+    uint32_t e = 0, off = 0, h = 0, vb = 0;
+    int y0 = 0;
+    EllipseTiles E{0.f, 0.f, 1.f, 0.f, 1.f, -1.f, 0, 0, ell.W, ell.H, 1.f, 1.f};
+    if (in && rec[ek + 1].x > rec[ek].x) {
+      e = rec[ek].y;
+      off = rec[ek].x;
+      const uint2 rr = __ldg(rect + e);
+      y0 = (int)(rr.x >> 16);
+      h = (rr.y >> 16) - (uint32_t)y0;
+      const float4 s0 = __ldg(ell.splat + (size_t)e * 3), s1 = __ldg(ell.splat + (size_t)e * 3 + 1);
+      const float th = __ldg(reinterpret_cast<const float*>(ell.splat + (size_t)e * 3 + 2) + 1);
+      E = EllipseTiles{s0.x, s0.y, s0.z, s0.w, s1.x, ellipse_level(s1.y, th), (int)(rr.x & 0xffffu),
+                       (int)(rr.y & 0xffffu), ell.W, ell.H, 0.f, 0.f};
+      ellipse_prepare(E);
+      vb = (e / n) * tiles_per_view;
+    }
+    uint32_t incl = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t rstart = incl - h, R = __shfl_sync(0xffffffffu, incl, 31);
+    k_run[lane] = 0u;
+    __syncwarp();
+    for (uint32_t k0 = 0; k0 < R; k0 += 32) {
+      const uint32_t k = k0 + (uint32_t)lane;
+      int own = 0;                                 // the last lane whose rows start at or before k
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const uint32_t s = __shfl_sync(0xffffffffu, rstart, own + step);
+        if (s <= k) own += step;
+      }
+      const EllipseTiles Eo{__shfl_sync(0xffffffffu, E.u, own), __shfl_sync(0xffffffffu, E.v, own),
+                            __shfl_sync(0xffffffffu, E.A, own), __shfl_sync(0xffffffffu, E.B, own),
+                            __shfl_sync(0xffffffffu, E.C, own), __shfl_sync(0xffffffffu, E.Q, own),
+                            __shfl_sync(0xffffffffu, E.x0, own), __shfl_sync(0xffffffffu, E.x1, own), ell.W, ell.H,
+                            __shfl_sync(0xffffffffu, E.iA, own), __shfl_sync(0xffffffffu, E.iC, own)};
+      const uint32_t rs_own = __shfl_sync(0xffffffffu, rstart, own);
+      const int ty = __shfl_sync(0xffffffffu, y0, own) + (int)(k - rs_own);
+      int slo = 1, shi = 0;
+      if (k < R) ellipse_row_span(Eo, ty, slo, shi);
+      const uint32_t c = slo <= shi ? (uint32_t)(shi - slo + 1) : 0u;
+      // kept index of this row's first tile within its record: the record's
+      // count from earlier steps plus its earlier rows in this step
+      uint32_t sc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, sc, o);
+        if (lane >= o) sc += y;
+      }
+      const uint32_t ex = sc - c;
+      const int first = (int)(max(rs_own, k0) - k0);   // first lane of this record in the step
+      const uint32_t kidx = k_run[own] + ex - __shfl_sync(0xffffffffu, ex, first);
+      const uint32_t pr = __shfl_sync(0xffffffffu, off, own) + kidx;   // pair index of the row's first tile
+      const uint32_t t0 = __shfl_sync(0xffffffffu, vb, own) + (uint32_t)ty * gx + (uint32_t)slo;
+      const uint32_t ev = __shfl_sync(0xffffffffu, e, own);
+      __syncwarp();
+      if (c) atomicAdd(&k_run[own], c);
+      // this lane's row: stage its tiles that fall in [p0, p1)
+      const uint32_t a = max(pr, p0), b = min(pr + c, p1);
+      for (uint32_t q = a; q < b; q++) {
+        st_key[q - p0] = t0 + (q - pr);
+        st_val[q - p0] = ev;
+      }
+      __syncwarp();
+    }
+    eb += nb;
+  }
+  for (uint32_t q = (uint32_t)lane; q < p1 - p0; q += 32) {   // coalesced stores of the staged pairs
+    keys[p0 + q] = st_key[q];
+    vals[p0 + q] = st_val[q];
+  }
+  __syncwarp();
+}
+
 struct TileEmitSmem {
   uint4 rec[kTileChunk + 2];
+  uint32_t k_run[kEmitThreads / 32][32];
   uint32_t key[kEmitThreads / 32][32 * kEmitStride];
   uint32_t val[kEmitThreads / 32][32 * kEmitStride];
   uint32_t k0;
@@ -329,6 +431,11 @@ tile_emit_kernel(const uint4* __restrict__ recs, const uint32_t* __restrict__ ch
       const uint32_t wend = min(cend, S.rec[m].x);   // pairs this window covers: [cs, wend)
       const uint32_t cn = wend > cs ? wend - cs : 0u;
       for (uint32_t w0 = (uint32_t)warp * kEmitChunk; w0 < cn; w0 += (kEmitThreads / 32) * kEmitChunk) {
+        if (ell.splat) {                           // ellipse tiles: the whole warp enumerates rows
+          warp_emit_ellipse(S.rec, (int)m, cs + w0, min(cs + w0 + (uint32_t)kEmitChunk, wend), ell, rect, n,
+                            tiles_per_view, gx, keys, vals, S.k_run[warp], S.key[warp], S.val[warp], lane);
+          continue;
+        }
         const uint32_t j0 = cs + w0 + (uint32_t)lane * kEmitRun;
         if (j0 < wend) {
           int lo = 0, hi = (int)m;                 // invariant: rec[lo].x <= j0 < rec[hi].x
@@ -339,26 +446,7 @@ tile_emit_kernel(const uint4* __restrict__ recs, const uint32_t* __restrict__ ch
           uint4 rc = S.rec[lo];
           uint32_t nxt = S.rec[lo + 1].x;
           const uint32_t r = j0 - rc.x;
-          if (ell.splat) {                         // the ellipse test's tiles, row by row
-            EllipseWalk wk;
-            wk.start(ell.splat, rect, rc.y, n, tiles_per_view, ell.W, ell.H, r);
-#pragma unroll 1
-            for (int k = 0; k < kEmitRun; k++) {
-              const uint32_t j = j0 + k;
-              if (j >= wend) break;
-              if (j >= nxt) {                      // next record with pairs (j < wend <= rec[m].x)
-                do {
-                  lo++;
-                  nxt = S.rec[lo + 1].x;
-                } while (j >= nxt);
-                rc = S.rec[lo];
-                wk.start(ell.splat, rect, rc.y, n, tiles_per_view, ell.W, ell.H, j - rc.x);
-              }
-              S.key[warp][lane * kEmitStride + k] = wk.tile(gx);
-              S.val[warp][lane * kEmitStride + k] = rc.y;
-              wk.next();
-            }
-          } else {
+          {
             uint32_t ry = r / rc.w, rx = r - ry * rc.w;
 #pragma unroll
             for (int k = 0; k < kEmitRun; k++) {

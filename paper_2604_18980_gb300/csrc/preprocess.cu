@@ -51,9 +51,7 @@ __device__ __forceinline__ void tile_span(float lo, float hi, int len, int& t0, 
 
 // kCacheSH: keep the 48 SH coefficients in registers after the first view that
 // needs them (multi-view batches); otherwise re-read them through the caches.
-// kEllipse: count the tiles of the ellipse tile test instead of whole squares
-// (a separate instance, so that the square path keeps its registers).
-template <bool kCacheSH, bool kEllipse>
+template <bool kCacheSH>
 __global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn in, int64_t n, int views,
                                                          const __grid_constant__ CamBatch cams,
                                                          const __grid_constant__ DevParams P, PreOut out,
@@ -110,17 +108,7 @@ __global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn
       tile_span(pj.u - rf, pj.u + rf, C.W, x0, x1);
       tile_span(pj.v - rf, pj.v + rf, C.H, y0, y1);
     }
-    uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
-    if (kEllipse && touched) {
-      // the tiles of the square that the alpha >= Th ellipse reaches
-      const EllipseTiles E{pj.u, pj.v, pj.A, pj.B, pj.C, ellipse_level(F.opac, th), x0, x1, C.W, C.H};
-      touched = 0u;
-      for (int ty = y0; ty < y1; ty++) {
-        int lo, hi;
-        ellipse_row_span(E, ty, lo, hi);
-        if (lo <= hi) touched += (uint32_t)(hi - lo + 1);
-      }
-    }
+    const uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
     if (touched == 0u) { write_culled(out, e); continue; }
 
     // colour: SH at the world-space direction from the camera centre (the
@@ -177,6 +165,39 @@ __global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn
   }
 }
 
+// Ellipse tile test (tile_test AGS_TILE_ELLIPSE): the kept tiles of every
+// surviving Gaussian-view, from its splat record and square, by the same
+// functions the emission enumerates them with.  One warp per 32 consecutive
+// Gaussian-views (Gaussian order, so the sizes within a warp are mixed); the
+// rows of the 32 are spread over the lanes.  A Gaussian-view without a kept
+// tile is culled.
+__global__ void __launch_bounds__(256) ellipse_count_kernel(const float4* __restrict__ splat,
+                                                            const uint2* __restrict__ rect, int64_t total, int W,
+                                                            int H, PreOut out) {
+  __shared__ uint32_t s_run[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  EllipseTiles E{0.f, 0.f, 1.f, 0.f, 1.f, -1.f, 0, 0, W, H, 1.f, 1.f};
+  int y0 = 0;
+  uint32_t h = 0;
+  const bool live = e < total && !(out.flags[e] & kFlagCulled);
+  if (live) {
+    const uint2 r = __ldg(rect + e);
+    const float4 s0 = __ldg(splat + e * 3), s1 = __ldg(splat + e * 3 + 1);
+    const float th = __ldg(reinterpret_cast<const float*>(splat + e * 3 + 2) + 1);
+    E = EllipseTiles{s0.x, s0.y, s0.z, s0.w, s1.x, ellipse_level(s1.y, th), (int)(r.x & 0xffffu),
+                     (int)(r.y & 0xffffu), W, H, 0.f, 0.f};
+    ellipse_prepare(E);
+    y0 = (int)(r.x >> 16);
+    h = (r.y >> 16) - (uint32_t)y0;
+  }
+  const uint32_t c = warp_ellipse_count(E, y0, h, lane, s_run[warp]);
+  if (live) {
+    if (c) out.touched[e] = c;
+    else write_culled(out, e);
+  }
+}
+
 }  // namespace ags
 
 extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* cams, int32_t views,
@@ -198,9 +219,16 @@ extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* c
   if (((uintptr_t)out->splat & 15u) || ((uintptr_t)out->rect & 7u)) return AGS_ERR_INVALID_ARG;
   PreIn in{g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
   PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags, out->depth_key};
-  const bool ell = dp.tile_test == AGS_TILE_ELLIPSE;
-  auto kern = views > 1 ? (ell ? preprocess_kernel<true, true> : preprocess_kernel<true, false>)
-                        : (ell ? preprocess_kernel<false, true> : preprocess_kernel<false, false>);
+  auto kern = views > 1 ? preprocess_kernel<true> : preprocess_kernel<false>;
   kern<<<(unsigned)((g->n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, g->n, views, cb, dp, po, d_status);
+  if (dp.tile_test == AGS_TILE_ELLIPSE) {
+    if (!out->tiles_touched) return AGS_ERR_INVALID_ARG;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return launch_status(e);
+    const int64_t total = (int64_t)views * g->n;
+    ellipse_count_kernel<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4*>(out->splat), reinterpret_cast<const uint2*>(out->rect), total, cb.c[0].W,
+        cb.c[0].H, po);
+  }
   return launch_status(cudaGetLastError());
 }
