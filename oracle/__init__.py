@@ -13,6 +13,11 @@ What each function follows (paper: AdaGScale, arXiv 2604.18980):
   rasterize       Eq. 1 and Eq. 2, tau = 1/255, early stop at T < 1e-4
   render_bruteforce  the same blend without tiles or key sort
   backward        exact adjoint of the blend with frozen lists (not in the paper)
+  peripheral      Eq. 3 contributions summed per Gaussian over tau <= alpha < x
+                  (Eq. 4), with max T and the pixel sum of alpha (Eq. 6-7)
+  peripheral_scores  Eq. 4 at each Gaussian's Th (Eq. 10) beside Eq. 6, 7, 9
+  render_skip     the blend with low-contribution blends skipped (Fig. 4a,
+                  Fig. 5: exact, max-T and T_up rankings)
   sh_basis        real spherical harmonics from the general formula
 """
 from __future__ import annotations
@@ -146,6 +151,12 @@ class Oracle:
         L.oracle_rasterize.restype = None
         L.oracle_render_bruteforce.argtypes = [ctypes.c_int64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
         L.oracle_render_bruteforce.restype = None
+        L.oracle_peripheral.argtypes = [ctypes.c_int64, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                        ctypes.c_double, _P, _P, _P, _P]
+        L.oracle_peripheral.restype = None
+        L.oracle_render_skip.argtypes = [ctypes.c_int64, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                         ctypes.c_int, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]
+        L.oracle_render_skip.restype = None
         L.oracle_backward.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P,
                                       _P, _P, _P, _P, _P, _P]
         L.oracle_backward.restype = None
@@ -241,6 +252,63 @@ class Oracle:
     def num_threads(self) -> int:
         return int(self.L.oracle_num_threads())
 
+    # -- peripheral-score diagnostics (Sec. 3.1 Eq. 4, Sec. 3.2 Eq. 6-9, Fig. 4a, Fig. 5) --
+    def peripheral(self, dbl, tile_start, ids, width: int, height: int, par: OcParams, level,
+                   level_rel: float = 1e-4) -> dict:
+        """Eq. 4 per Gaussian at the level x_i = level[i] over the blend of the
+        given lists: ps (sum of alpha T with alpha < x_i), sum_alpha (the same
+        pixels' alpha), max_T (over every pixel where it blends) and edge (the
+        alpha T of blends within the edge width of x_i or tau)."""
+        n = dbl.shape[0]
+        out = {k: np.zeros(n, dtype=np.float64) for k in ("ps", "sum_alpha", "max_T", "edge")}
+        ids = np.ascontiguousarray(ids, dtype=np.int32) if len(ids) else np.zeros(1, dtype=np.int32)
+        self.L.oracle_peripheral(n, _ptr(_d(dbl)), _ptr(np.ascontiguousarray(tile_start, dtype=np.int64)),
+                                 _ptr(ids), width, height, ctypes.byref(par), _ptr(_d(level)), float(level_rel),
+                                 _ptr(out["ps"]), _ptr(out["sum_alpha"]), _ptr(out["max_T"]), _ptr(out["edge"]))
+        return out
+
+    def render_skip(self, dbl, tile_start, ids, width: int, height: int, par: OcParams, rule: int, weight,
+                    thr: float, thr_rel: float = 1e-4) -> dict:
+        """The plain render's blends, each skipped when its contribution is below
+        thr (rule 0: alpha T, Eq. 3; rule 1/2: weight[i] alpha with weight max T_i
+        (Eq. 6) or T_up(depth_i) (Eq. 7)).  Returns image, budget, blends, skipped."""
+        n = dbl.shape[0]
+        img = np.zeros((3, height, width), dtype=np.float64)
+        bud = np.zeros((height, width), dtype=np.float64)
+        counts = np.zeros(2, dtype=np.int64)
+        w = _d(np.zeros(max(n, 1)) if weight is None else weight)
+        ids = np.ascontiguousarray(ids, dtype=np.int32) if len(ids) else np.zeros(1, dtype=np.int32)
+        self.L.oracle_render_skip(n, _ptr(_d(dbl)), _ptr(np.ascontiguousarray(tile_start, dtype=np.int64)),
+                                  _ptr(ids), width, height, ctypes.byref(par), int(rule), _ptr(w), float(thr),
+                                  float(thr_rel), _ptr(img), _ptr(counts), _ptr(bud))
+        return dict(image=img, budget=bud, blends=int(counts[0]), skipped=int(counts[1]))
+
+    def peripheral_scores(self, scene: dict, cam: dict, K: float, lut, sh_degree: int = 3,
+                          level_rel: float = 1e-4, **pkw) -> dict:
+        """The scores of every Gaussian at its AdaGScale level Th (Eq. 10 with K
+        and the T_up table lut), over the plain render (the alpha >= tau region
+        Eq. 4 sums over):
+          th   Eq. 10 (inf where T_up = 0),
+          eq4  exact peripheral score (sum of alpha T with tau <= alpha < Th),
+          eq6  max T_i times the pixel sum of alpha (Eq. 6),
+          eq7  T_up(depth_i) times the same sum (Eq. 7),
+          eq9  T_up 2 pi sqrt(det Sigma2D) (min(Th, opacity) - tau) (Eq. 9; alpha
+               never exceeds the opacity, so the band ends there),
+          max_T, sum_alpha, edge, and the plain and AdaGScale preprocess records."""
+        plain = params(cam, scale_mode=0, lut=lut, sh_degree=sh_degree, **pkw)
+        ada = params(cam, scale_mode=1, K=K, lut=lut, sh_degree=sh_degree, **pkw)
+        dbl, irec = self.preprocess(scene, cam, plain)
+        dbl_a, irec_a = self.preprocess(scene, cam, ada)
+        ts, ids = self.tile_lists(dbl, irec, cam["width"], cam["height"])
+        th = np.where(irec_a[:, I_CULL] == CULL_TUP, np.inf, dbl_a[:, F_TH])
+        pr = self.peripheral(dbl, ts, ids, cam["width"], cam["height"], plain, th, level_rel)
+        tup = lut_value(dbl[:, F_DEPTH], lut, ada.lut_bins, ada.lut_depth_max)
+        band = np.minimum(th, dbl[:, F_OPAC]) - ada.tau
+        return dict(th=th, eq4=pr["ps"], eq6=pr["max_T"] * pr["sum_alpha"], eq7=tup * pr["sum_alpha"],
+                    eq9=tup * 2.0 * math.pi * np.sqrt(np.maximum(dbl[:, F_DET], 0.0)) * band,
+                    max_T=pr["max_T"], sum_alpha=pr["sum_alpha"], edge=pr["edge"], dbl=dbl, irec=irec,
+                    dbl_ada=dbl_a, irec_ada=irec_a, tile_start=ts, ids=ids)
+
 
 _default = None
 
@@ -283,6 +351,27 @@ def sh_basis(*a, **k):
 
 def num_threads() -> int:
     return default().num_threads()
+
+
+def peripheral(*a, **k):
+    return default().peripheral(*a, **k)
+
+
+def render_skip(*a, **k):
+    return default().render_skip(*a, **k)
+
+
+def peripheral_scores(*a, **k):
+    return default().peripheral_scores(*a, **k)
+
+
+def lut_value(depth, lut, bins: int = LUT_BINS, depth_max: float = LUT_DEPTH_MAX):
+    """T_up of each depth (Sec. 3.4): bin floor(depth / (depth_max / bins)),
+    depths beyond the range in the last bin."""
+    lut = np.ones(bins) if lut is None else np.asarray(lut, dtype=np.float64)
+    b = np.floor(np.asarray(depth, dtype=np.float64) / (depth_max / bins))
+    b = np.clip(b, 0, bins - 1).astype(np.int64)
+    return lut[b]
 
 
 def psnr(a, b, peak: float = 1.0) -> float:

@@ -19,6 +19,9 @@
  *   backward    (not in the paper: exact adjoint of the blend with the pair
  *                lists frozen, chained to the raw parameters by forward-mode
  *                jets, i.e. derivatives carried alongside every value)
+ *   diagnostics (Eq. 3 contributions, the exact peripheral score of Eq. 4 with
+ *                the max-T statistic of Eq. 6, and the contribution-skip
+ *                render behind Fig. 4a and Fig. 5)
  *
  * Details the paper leaves to the original 3D-GS (near plane 0.2, EWA Jacobian
  * with the 1.3 tan(fov/2) clamp, +0.3 low-pass, eigenvalue guard 0.1, colour =
@@ -665,6 +668,133 @@ void oracle_render_bruteforce(int64_t n, const double* dbl, const int32_t* irec,
   free(all);
 }
 
+static void atomic_add_double(double* p, double v) {
+#pragma omp atomic
+  *p += v;
+}
+
+static void atomic_max_double(double* p, double v) {
+#pragma omp critical(oc_max)
+  if (v > *p) *p = v;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Peripheral-score diagnostics (Sec. 2.2 Eq. 3, Sec. 3.1 Eq. 4, Sec. 3.2     */
+/* Eq. 6-7, Fig. 4a and Fig. 5).                                              */
+/*                                                                            */
+/* Both functions replay the blend of the given (plain) tile lists pixel by   */
+/* pixel, with the decisions of blend_pixel: Gaussian i is blended at pixel k */
+/* when alpha >= tau and p <= 0, before the stop T (1 - alpha) < t_min.  Its  */
+/* contribution there is alpha * T (Eq. 3), T the transmittance before it.    */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 4 at the level x_i = level[i]: ps[i] = sum of alpha * T over the pixels
+ * where i is blended with alpha < level[i]; sum_alpha[i] = sum of alpha over
+ * the same pixels; max_T[i] = max of T over all pixels where i is blended.
+ * edge[i] collects the alpha * T of the blends whose alpha lies within the
+ * edge width (edge_rel + pos_err |grad ln alpha| + level_rel) of level[i], and
+ * 2 tau T for alpha within the edge width of tau: a fp32 evaluation may count
+ * them on the other side.  All arrays [n], zeroed by the caller. */
+void oracle_peripheral(int64_t n, const double* dbl, const int64_t* tile_start, const int32_t* ids,
+                       int32_t width, int32_t height, const oc_params* par, const double* level,
+                       double level_rel, double* ps, double* sum_alpha, double* max_T, double* edge) {
+  int gx = (width + OC_TILE - 1) / OC_TILE, gy = (height + OC_TILE - 1) / OC_TILE;
+  int64_t nt = (int64_t)gx * gy;
+  (void)n;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t t = 0; t < nt; t++) {
+    int tx = (int)(t % gx), ty = (int)(t / gx);
+    const int32_t* list = ids + tile_start[t];
+    int64_t len = tile_start[t + 1] - tile_start[t];
+    for (int y = ty * OC_TILE; y < ty * OC_TILE + OC_TILE && y < height; y++)
+      for (int x = tx * OC_TILE; x < tx * OC_TILE + OC_TILE && x < width; x++) {
+        double T = 1.0;
+        for (int64_t k = 0; k < len; k++) {
+          int32_t i = list[k];
+          const double* g = dbl + (int64_t)i * OC_NF;
+          double dx = g[F_U] - x, dy = g[F_V] - y;
+          double p = -0.5 * (g[F_A] * dx * dx + g[F_C] * dy * dy) - g[F_B] * dx * dy;
+          double araw = g[F_OPAC] * exp(p);
+          double alpha = fmin(par->alpha_max, araw);
+          double gl = fabs(g[F_A] * dx + g[F_B] * dy) + fabs(g[F_B] * dx + g[F_C] * dy);
+          double tol = par->edge_rel + par->pos_err * gl;
+          if (araw > 0.0 && fabs(log(araw / par->tau)) <= tol) atomic_add_double(&edge[i], 2.0 * par->tau * T);
+          if (p > 0.0 || alpha < par->tau) continue;
+          double test_T = T * (1.0 - alpha);
+          if (test_T < par->t_min) break;
+          double c = alpha * T;
+          if (alpha < level[i]) {
+            atomic_add_double(&ps[i], c);
+            atomic_add_double(&sum_alpha[i], alpha);
+          }
+          if (isfinite(level[i]) && fabs(log(alpha / level[i])) <= tol + level_rel) atomic_add_double(&edge[i], c);
+          atomic_max_double(&max_T[i], T);
+          T = test_T;
+        }
+      }
+  }
+}
+
+/* Contribution-skip render: the blends of the plain render, each skipped when
+ * its contribution c < thr, with c = alpha * T (rule 0, Eq. 3), or
+ * weight[i] * alpha (rule 1: weight = max T_i, Eq. 6; rule 2: weight =
+ * T_up(depth_i), Eq. 7).  A skipped blend adds no colour and leaves the
+ * image's transmittance Ts unchanged; T, which ranks rule 0 and decides the
+ * stop, advances as in the plain render, so every rule and threshold works on
+ * the same set of blends.  image [3][H][W] = colour + Ts bg; counts[0] =
+ * blends, counts[1] = skipped; budget [H][W] (nullable) bounds the change a
+ * near-threshold decision (alpha vs tau, p vs 0, c vs thr within thr_rel)
+ * can cause. */
+void oracle_render_skip(int64_t n, const double* dbl, const int64_t* tile_start, const int32_t* ids,
+                        int32_t width, int32_t height, const oc_params* par, int rule, const double* weight,
+                        double thr, double thr_rel, double* image, int64_t* counts, double* budget) {
+  int gx = (width + OC_TILE - 1) / OC_TILE, gy = (height + OC_TILE - 1) / OC_TILE;
+  int64_t nt = (int64_t)gx * gy, hw = (int64_t)width * height;
+  double cmax = color_max(n, dbl, par);
+  int64_t tot = 0, skipped = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : tot, skipped)
+  for (int64_t t = 0; t < nt; t++) {
+    int tx = (int)(t % gx), ty = (int)(t / gx);
+    const int32_t* list = ids + tile_start[t];
+    int64_t len = tile_start[t + 1] - tile_start[t];
+    for (int y = ty * OC_TILE; y < ty * OC_TILE + OC_TILE && y < height; y++)
+      for (int x = tx * OC_TILE; x < tx * OC_TILE + OC_TILE && x < width; x++) {
+        double T = 1.0, Ts = 1.0, col[3] = {0, 0, 0}, bud = 0.0;
+        for (int64_t k = 0; k < len; k++) {
+          const double* g = dbl + (int64_t)list[k] * OC_NF;
+          double dx = g[F_U] - x, dy = g[F_V] - y;
+          double p = -0.5 * (g[F_A] * dx * dx + g[F_C] * dy * dy) - g[F_B] * dx * dy;
+          double araw = g[F_OPAC] * exp(p);
+          double alpha = fmin(par->alpha_max, araw);
+          double gl = fabs(g[F_A] * dx + g[F_B] * dy) + fabs(g[F_B] * dx + g[F_C] * dy);
+          double tol = par->edge_rel + par->pos_err * gl;
+          if (araw > 0.0 && fabs(log(araw / par->tau)) <= tol) bud += 2.0 * par->tau * T * cmax;
+          if (fabs(p) <= par->edge_rel && g[F_OPAC] >= par->tau) bud += 2.0 * g[F_OPAC] * T * cmax;
+          if (p > 0.0 || alpha < par->tau) continue;
+          double test_T = T * (1.0 - alpha);
+          if (test_T < par->t_min) break;
+          double c = rule == 0 ? alpha * T : weight[list[k]] * alpha;
+          if (fabs(c - thr) <= (tol + thr_rel) * thr) bud += 2.0 * alpha * Ts * cmax;
+          tot++;
+          if (c < thr) {
+            skipped++;
+          } else {
+            col[0] += g[F_R] * alpha * Ts;
+            col[1] += g[F_G] * alpha * Ts;
+            col[2] += g[F_BL] * alpha * Ts;
+            Ts *= 1.0 - alpha;
+          }
+          T = test_T;
+        }
+        int64_t o = (int64_t)y * width + x;
+        for (int c = 0; c < 3; c++) image[c * hw + o] = col[c] + Ts * par->bg[c];
+        if (budget) budget[o] = bud;
+      }
+  }
+  counts[0] = tot;
+  counts[1] = skipped;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Backward with frozen tile lists.                                          */
 /* Per pixel: forward products give T_i; the colour behind entry i,         */
@@ -674,10 +804,6 @@ void oracle_render_bruteforce(int64_t n, const double* dbl, const int32_t* irec,
 /* without any division.  The feature gradients are chained to the raw       */
 /* parameters through the jets of the preprocess.                            */
 /* ------------------------------------------------------------------------ */
-static void atomic_add_double(double* p, double v) {
-#pragma omp atomic
-  *p += v;
-}
 
 void oracle_backward(const double* mean, const double* log_scale, const double* quat, const double* logit,
                      const double* sh, int64_t n, const oc_camera* cam, const oc_params* par,

@@ -632,7 +632,142 @@ def pin_ellipse_lossless_plain(orc):
     np.testing.assert_array_equal(ada["image"], orc.render_bruteforce(scene, cam, par))
 
 
+# --------------------------------------------------------------------------
+# Peripheral-score diagnostics: Eq. 3-4 contributions, Eq. 6-9 estimates and
+# the contribution-skip render of Fig. 4a / Fig. 5
+# --------------------------------------------------------------------------
+def _two_layers(back_px=0):
+    """A wide front Gaussian (opacity 0.5, depth 2, on the axis) over a small
+    back one (opacity 0.9, depth 3, back_px pixels right of the centre) seen by
+    a 65x65 camera, with the closed-form alpha of each at every pixel: an
+    isotropic Gaussian of scale s at (x, 0, z) projects to the diagonal
+    covariance ((f s/z)^2 (1 + x^2/z^2) + 0.3, (f s/z)^2 + 0.3).  Both
+    footprints cover their alpha >= tau pixels; the transmittance never
+    reaches the stop."""
+    W = H = 65
+    f = 80.0
+    cam = axis_camera(W, H, f)
+    lam_f = (f * 0.3 / 2.0) ** 2 + 0.3
+    s_b, z_b = 0.02, 3.0
+    x_b = back_px * z_b / f
+    lam_bx = (f * s_b / z_b) ** 2 * (1 + (x_b / z_b) ** 2) + 0.3
+    lam_by = (f * s_b / z_b) ** 2 + 0.3
+    sc = concat(one_gaussian((0, 0, 2.0), (0.3, 0.3, 0.3), opacity=0.5),
+                one_gaussian((x_b, 0, z_b), (s_b, s_b, s_b), opacity=0.9, dc=(0.9, 0.1, -0.4)))
+    k = np.arange(-32, 33)
+    dx, dy = np.meshgrid(k, k)
+    af = np.minimum(0.99, 0.5 * np.exp(-(dx * dx + dy * dy) / (2 * lam_f)))
+    ab = np.minimum(0.99, 0.9 * np.exp(-(dx - back_px) ** 2 / (2 * lam_bx) - dy * dy / (2 * lam_by)))
+    return cam, sc, af, ab
+
+
+def pin_peripheral_two_layers(orc):
+    """Eq. 4 per Gaussian against a direct per-pixel sum: the back Gaussian
+    sees T = 1 - alpha_front wherever the front one blends."""
+    cam, sc, af, ab = _two_layers()
+    par = oracle.params(cam)
+    dbl, irec = orc.preprocess(sc, cam, par)
+    ts, ids = orc.tile_lists(dbl, irec, cam["width"], cam["height"])
+    bf, bb = af >= TAU, ab >= TAU
+    Tb = np.where(bf, 1.0 - af, 1.0)
+    for x in (0.02, 0.3, 0.95, np.inf):
+        out = orc.peripheral(dbl, ts, ids, cam["width"], cam["height"], par, np.array([x, x]))
+        exp_ps = [af[bf & (af < x)].sum(), (ab * Tb)[bb & (ab < x)].sum()]
+        exp_sa = [af[bf & (af < x)].sum(), ab[bb & (ab < x)].sum()]
+        np.testing.assert_allclose(out["ps"], exp_ps, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(out["sum_alpha"], exp_sa, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(out["max_T"], [1.0, Tb[bb].max()], rtol=1e-12)
+    assert out["ps"][1] < out["sum_alpha"][1]
+
+
+def pin_peripheral_closed_form(orc):
+    """A lone large Gaussian (T = 1 everywhere): Eq. 4 equals the pixel sum of
+    alpha and lies within 1% of Eq. 9's annulus integral 2 pi sqrt(det) (x - tau),
+    the band ending at the opacity."""
+    W = H = 161
+    f, d, sig = 200.0, 2.0, 0.3
+    cam = axis_camera(W, H, f)
+    sc = one_gaussian((0.013, -0.007, d), (0.2, 0.11, 0.05), quat=(0.8, 0.0, 0.0, 0.6), opacity=sig)
+    par = oracle.params(cam)
+    dbl, irec = orc.preprocess(sc, cam, par)
+    ts, ids = orc.tile_lists(dbl, irec, W, H)
+    det = dbl[0, oracle.F_DET]
+    for x in (0.02, 0.1, 0.2, 0.5):
+        out = orc.peripheral(dbl, ts, ids, W, H, par, np.array([x]))
+        np.testing.assert_allclose(out["ps"], out["sum_alpha"], rtol=1e-13)
+        np.testing.assert_allclose(out["ps"][0], 2 * math.pi * math.sqrt(det) * (min(x, sig) - TAU), rtol=1e-2)
+        assert out["max_T"][0] == 1.0
+
+
+def pin_peripheral_invariants(orc):
+    """On a random scene: with no level the scores telescope to the covered
+    fraction of every pixel (sum_i alpha_i T_i = 1 - T_final); Eq. 6 bounds
+    Eq. 4 from above; Eq. 4 grows with the level; at each Gaussian's own Th
+    (Eq. 10), Eq. 9 returns K wherever Th <= opacity."""
+    scene, cams, _ = synth.workload("c1_cube16k_256", n=400, width=64, height=48, views=1)
+    cam = cams[0]
+    lut = np.linspace(1.0, 0.5, 20)
+    par = oracle.params(cam, lut=lut)
+    dbl, irec = orc.preprocess(scene, cam, par)
+    ts, ids = orc.tile_lists(dbl, irec, 64, 48)
+    n = dbl.shape[0]
+    full = orc.peripheral(dbl, ts, ids, 64, 48, par, np.full(n, np.inf))
+    ref = orc.rasterize(dbl, ts, ids, 64, 48, par)
+    np.testing.assert_allclose(full["ps"].sum(), (1.0 - ref["final_T"]).sum(), rtol=1e-10)
+    assert np.all(full["max_T"] * full["sum_alpha"] >= full["ps"] * (1 - 1e-12))
+    half = orc.peripheral(dbl, ts, ids, 64, 48, par, np.full(n, 0.2))
+    assert np.all(half["ps"] <= full["ps"] * (1 + 1e-12)) and half["ps"].sum() < full["ps"].sum()
+    K = 0.5
+    sc = orc.peripheral_scores(scene, cam, K, lut)
+    live = irec[:, oracle.I_TOUCHED] > 0
+    ok = live & np.isfinite(sc["th"]) & (sc["th"] <= dbl[:, oracle.F_OPAC])
+    assert ok.sum() > 20
+    np.testing.assert_allclose(sc["eq9"][ok], K, rtol=1e-9)
+    over = live & (sc["th"] > dbl[:, oracle.F_OPAC])
+    assert over.any() and np.all(sc["eq9"][over] < K)
+
+
+def pin_skip_render(orc):
+    """Contribution-skip render: no threshold gives the plain image bit for bit,
+    a threshold above every contribution leaves the background, and on two
+    layers each ranking skips exactly the blends a per-pixel restatement
+    predicts (rule 0 ranks by the unskipped T, the image uses the kept blends)."""
+    W = H = 65
+    bg = (0.2, 0.4, 0.6)
+    cases = ((0, 0, None, 0.05), (0, 0, None, 0.3), (0, 1, np.array([1.0, 0.5]), 0.2), (20, 0, None, 0.36),
+             (20, 2, np.array([0.7, 0.9]), 0.3))
+    for back_px, rule, weight, thr in cases:
+        cam, sc, af, ab = _two_layers(back_px)
+        par = oracle.params(cam, bg=bg)
+        dbl, irec = orc.preprocess(sc, cam, par)
+        ts, ids = orc.tile_lists(dbl, irec, W, H)
+        if thr == 0.05:
+            ref = orc.rasterize(dbl, ts, ids, W, H, par, want_state=True)
+            out = orc.render_skip(dbl, ts, ids, W, H, par, 0, None, 0.0)
+            np.testing.assert_array_equal(out["image"], ref["image"])
+            assert out["skipped"] == 0 and out["blends"] == int(ref["state"][..., 0].sum())
+            out = orc.render_skip(dbl, ts, ids, W, H, par, 0, None, 2.0)
+            np.testing.assert_allclose(out["image"], np.broadcast_to(np.array(bg)[:, None, None], (3, H, W)),
+                                       rtol=1e-15)
+            assert out["skipped"] == out["blends"]
+        bf, bb = af >= TAU, ab >= TAU
+        cf, cb = dbl[0, oracle.F_R:oracle.F_BL + 1], dbl[1, oracle.F_R:oracle.F_BL + 1]
+        w = np.ones(2) if weight is None else weight
+        kf = bf & (w[0] * af >= thr)
+        rank_b = ab * np.where(bf, 1.0 - af, 1.0) if rule == 0 else w[1] * ab
+        kb = bb & (rank_b >= thr)
+        Ts_b = np.where(kf, 1.0 - af, 1.0)
+        Ts = Ts_b * np.where(kb, 1.0 - ab, 1.0)
+        img = (cf[:, None, None] * np.where(kf, af, 0.0) + cb[:, None, None] * np.where(kb, ab * Ts_b, 0.0)
+               + np.array(bg)[:, None, None] * Ts)
+        out = orc.render_skip(dbl, ts, ids, W, H, par, rule, weight, thr)
+        np.testing.assert_allclose(out["image"], img, rtol=1e-12, atol=1e-15)
+        assert out["skipped"] == int((bf & ~kf).sum() + (bb & ~kb).sum())
+        assert 0 < out["skipped"] < out["blends"]
+
+
 ALL_PINS = [pin_isotropic_on_axis, pin_off_axis_jacobian, pin_rotation_conventions, pin_eq9_quadrature,
             pin_eq8_riemann_pixels, pin_sh_basis, pin_sh_colour, pin_rect_enumeration, pin_bruteforce,
             pin_ideal_render, pin_invariants, pin_low_opacity_invisible, pin_max_T, pin_backward_fd,
-            pin_ellipse_tiles, pin_ellipse_lossless_plain]
+            pin_ellipse_tiles, pin_ellipse_lossless_plain, pin_peripheral_two_layers, pin_peripheral_closed_form,
+            pin_peripheral_invariants, pin_skip_render]

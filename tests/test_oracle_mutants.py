@@ -58,6 +58,15 @@ MUTANTS = [
      ["pin_ellipse_tiles", "pin_ellipse_lossless_plain"]),
     ("ellipse_tile_unclipped", "xh = fmin(OC_TILE * tx + OC_TILE - 1, width - 1) - g[F_U];",
      "xh = OC_TILE * tx + OC_TILE - 1 - g[F_U];", ["pin_ellipse_tiles"]),
+    ("ps_after_transmittance_update", "double c = alpha * T;\n          if (alpha < level[i]) {",
+     "double c = alpha * test_T;\n          if (alpha < level[i]) {",
+     ["pin_peripheral_two_layers", "pin_peripheral_closed_form"]),
+    ("ps_ignores_level", "if (alpha < level[i]) {", "if (alpha >= par->tau) {",
+     ["pin_peripheral_two_layers", "pin_peripheral_closed_form", "pin_peripheral_invariants"]),
+    ("skip_ranked_by_image_transmittance", "double c = rule == 0 ? alpha * T : weight[list[k]] * alpha;",
+     "double c = rule == 0 ? alpha * Ts : weight[list[k]] * alpha;", ["pin_skip_render"]),
+    ("skipped_blend_still_occludes", "            Ts *= 1.0 - alpha;\n          }\n",
+     "          }\n          Ts *= 1.0 - alpha;\n", ["pin_skip_render"]),
 ]
 
 
