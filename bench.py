@@ -225,6 +225,7 @@ def run_ours(args, world, rank, local):
     from paper_2604_18980_gb300 import binding as B
     from paper_2604_18980_gb300 import build as cuda_build
     from paper_2604_18980_gb300 import calibrate as C
+    from paper_2604_18980_gb300 import diagnostics as D
     from paper_2604_18980_gb300 import render as R
     from paper_2604_18980_gb300 import synth
 
@@ -391,8 +392,9 @@ def run_ours(args, world, rank, local):
             ell = {}
             for label, mode, k in (("adagscale", B.AGS_SCALE_ADAGSCALE, wp["K_ellipse"]), ("plain", B.AGS_SCALE_PLAIN, 0.0)):
                 try:
+                    # the ellipse rows are enumerated warp-wide only by the two-pass emission
                     re_ = R.Renderer(sc, cams, mode, k, wp["lut"] if mode else None, keep_state=False,
-                                     tile_test=B.AGS_TILE_ELLIPSE, **knobs)
+                                     tile_test=B.AGS_TILE_ELLIPSE, **dict(knobs, emit_two_pass=True))
                 except ValueError:
                     ell[label] = {"skipped": "more pairs than one sort call takes"}
                     continue
@@ -413,6 +415,30 @@ def run_ours(args, world, rank, local):
                 del re_, g, img_e
             extras["ellipse_tiles"] = ell
         del img_p
+
+        # peripheral-score diagnostics on the first view's plain render: the exact
+        # score (Eq. 4) at each Gaussian's Th against its estimates (Eq. 6, 7, 9),
+        # PSNR when the lowest-contribution blends are skipped (Fig. 4a, Fig. 5)
+        # and the max-T statistic by depth (Fig. 6)
+        try:
+            pd = R.Renderer(sc, cams[:1], B.AGS_SCALE_PLAIN, keep_state=False, want_stats=True, **knobs)
+            pd.forward()
+            pd.check()
+            dg = D.Diagnostics(pd, wp["K"], wp["lut"])
+            dg.scores()
+            a.record(stream)
+            scs = dg.scores()
+            b.record(stream)
+            torch.cuda.synchronize()
+            per = {"view": 0, "K": float(wp["K"]), "scores_ms": a.elapsed_time(b),
+                   "blend_evaluations": int(pd.stats[0].item()), "blends": int(pd.stats[1].item())}
+            per.update(dg.summary(scs))
+            per["skip_curve"] = dg.skip_curve(fractions=(0.2, 0.4, 0.6, 0.8))
+            per["max_T_by_depth"] = dg.max_T_by_depth(scs)
+            extras["peripheral"] = per
+            del pd, dg, scs
+        except ValueError as exc:
+            extras["peripheral"] = {"skipped": str(exc)}
 
         # end to end through host buffers: params H2D, render, images D2H, every step
         host = {k: v.cpu().pin_memory() for k, v in sc.items()}

@@ -25,6 +25,11 @@
  *                           the paper; the pair selection is held fixed)
  *   ags_calibrate_lut       T_up(depth) look-up table from per-Gaussian maximum
  *                           transmittance (Sec. 3.4)
+ *   ags_peripheral_scores   diagnostics: exact peripheral score (Eq. 4) at each
+ *   ags_contribution_hist   Gaussian's Th beside its estimates (Eq. 6, 7, 9);
+ *   ags_render_skip         the contribution distribution of a plain render and
+ *                           the image with low-contribution blends skipped
+ *                           (Sec. 2.2 Fig. 4a, Sec. 3.2 Fig. 5)
  *
  * Conventions (all entry points):
  *  - Every pointer is a DEVICE pointer owned by the caller unless it is marked
@@ -328,6 +333,52 @@ ags_status ags_rasterize(const ags_projected* proj, int64_t n, const uint32_t* s
 ags_status ags_calibrate_lut(const float* max_T, const float* depth, int64_t count,
                              int32_t lut_bins, float lut_depth_max, float* lut_out,
                              void* stream);
+
+/* Peripheral-score diagnostics (Sec. 3.1 Eq. 4, Sec. 3.2 Eq. 6-10).  Replays
+ * the blend of ags_rasterize over the given pair lists -- normally those of a
+ * PLAIN-mode preprocess, whose tiles cover the whole alpha >= tau region Eq. 4
+ * sums over -- with its exact per-pixel decisions, and writes for every
+ * Gaussian-view e (count = views*n), at its AdaGScale level Th_e from Eq. 10
+ * (params->K and the T_up table, det Sigma2D from the splat record):
+ *   scores[0][e]  Th_e (+inf where T_up = 0)
+ *   scores[1][e]  Eq. 4: sum of alpha T over the pixels where e blends with alpha < Th_e
+ *   scores[2][e]  Eq. 6: max T_e * sum of alpha over the same pixels
+ *   scores[3][e]  Eq. 7: T_up(depth_e) * that sum
+ *   scores[4][e]  Eq. 9: T_up(depth_e) 2 pi sqrt(det Sigma2D) (min(Th_e, opacity) - tau)
+ *                 (alpha never exceeds the opacity; equals K where Th_e <= opacity)
+ *   scores[5][e]  max T_e, the largest T before e over the pixels where it blends
+ *   scores[6][e]  the sum of alpha of row 1's pixels
+ * scores: fp32 [7][views*n], overwritten (culled Gaussian-views get zeros).
+ * The sums are fp32 atomics (order-dependent in the last bits). */
+ags_status ags_peripheral_scores(const ags_projected* proj, int64_t n, const uint32_t* sorted_vals,
+                                 const uint32_t* ranges, const ags_camera* cams, int32_t views,
+                                 const ags_params* params, float* scores, void* stream);
+
+/* Contribution histogram (Sec. 2.2 Fig. 4a, Sec. 3.2 Fig. 5).  For every blend
+ * of ags_rasterize over the given lists, its contribution under `rule`:
+ *   0: alpha T (Eq. 3);  1: max_T[e] alpha (Eq. 6; max_T e.g. row 5 of
+ *   ags_peripheral_scores);  2: T_up(depth_e) alpha (Eq. 7)
+ * is counted in hist[bits(c) >> 16] (uint32 [32768], overwritten; positive
+ * floats order as their bit patterns, so the bins are in contribution order;
+ * a negative contribution counts in the last bin).  max_T is read only for
+ * rule 1. */
+#define AGS_CONTRIB_HIST_BINS 32768
+ags_status ags_contribution_hist(const ags_projected* proj, int64_t n, const uint32_t* sorted_vals,
+                                 const uint32_t* ranges, const ags_camera* cams, int32_t views,
+                                 const ags_params* params, int32_t rule, const float* max_T,
+                                 uint32_t* hist, void* stream);
+
+/* Contribution-skip render (Sec. 2.2 Fig. 4a, Sec. 3.2 Fig. 5): the blends of
+ * ags_rasterize, each skipped when its contribution under `rule` (as for
+ * ags_contribution_hist) is below thr.  A skipped blend adds no colour and
+ * does not occlude; the unskipped T still ranks (rule 0) and decides the stop,
+ * so every rule and threshold acts on the same set of blends.  image
+ * [views][3][H][W] = kept colour + (image transmittance) bg; counts (uint64[2],
+ * accumulated: zero them first) += {blends, skipped}. */
+ags_status ags_render_skip(const ags_projected* proj, int64_t n, const uint32_t* sorted_vals,
+                           const uint32_t* ranges, const ags_camera* cams, int32_t views,
+                           const ags_params* params, int32_t rule, const float* max_T, float thr,
+                           float* image, uint64_t* counts, void* stream);
 
 /* Scratch bytes needed by ags_rasterize_backward. */
 size_t ags_backward_workspace_bytes(int64_t n, int32_t views);

@@ -83,6 +83,9 @@ EXPORTS = {
                    _I32),
     "ags_rasterize": ([_P, _I64, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "ags_calibrate_lut": ([_P, _P, _I64, _I32, _F, _P, _P], _I32),
+    "ags_peripheral_scores": ([_P, _I64, _P, _P, _P, _I32, _P, _P, _P], _I32),
+    "ags_contribution_hist": ([_P, _I64, _P, _P, _P, _I32, _P, _I32, _P, _P, _P], _I32),
+    "ags_render_skip": ([_P, _I64, _P, _P, _P, _I32, _P, _I32, _P, _F, _P, _P, _P], _I32),
     "ags_backward_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
     "ags_rasterize_backward": ([_P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                 ctypes.c_size_t, _P], _I32),
@@ -319,6 +322,34 @@ def ags_rasterize(proj, n, sorted_vals, ranges, cams, params_, image, final_T, n
 def ags_calibrate_lut(max_T, depth, count, lut_bins, lut_depth_max, lut_out, stream=None):
     _ok(lib().ags_calibrate_lut(ptr(max_T), ptr(depth), int(count), int(lut_bins), float(lut_depth_max),
                                 ptr(lut_out), stream_handle(stream)), "ags_calibrate_lut")
+
+
+AGS_CONTRIB_HIST_BINS = 32768
+SCORE_ROWS = ("th", "eq4", "eq6", "eq7", "eq9", "max_T", "sum_alpha")
+
+
+def ags_peripheral_scores(proj, n, sorted_vals, ranges, cams, params_, scores, stream=None):
+    pr = projected(proj)
+    cs = cameras(cams)
+    _ok(lib().ags_peripheral_scores(ctypes.byref(pr), int(n), ptr(sorted_vals), ptr(ranges), cs, len(cams),
+                                    ctypes.byref(params_), ptr(scores), stream_handle(stream)),
+        "ags_peripheral_scores")
+
+
+def ags_contribution_hist(proj, n, sorted_vals, ranges, cams, params_, rule, max_T, hist, stream=None):
+    pr = projected(proj)
+    cs = cameras(cams)
+    _ok(lib().ags_contribution_hist(ctypes.byref(pr), int(n), ptr(sorted_vals), ptr(ranges), cs, len(cams),
+                                    ctypes.byref(params_), int(rule), ptr(max_T), ptr(hist), stream_handle(stream)),
+        "ags_contribution_hist")
+
+
+def ags_render_skip(proj, n, sorted_vals, ranges, cams, params_, rule, max_T, thr, image, counts, stream=None):
+    pr = projected(proj)
+    cs = cameras(cams)
+    _ok(lib().ags_render_skip(ctypes.byref(pr), int(n), ptr(sorted_vals), ptr(ranges), cs, len(cams),
+                              ctypes.byref(params_), int(rule), ptr(max_T), float(thr), ptr(image), ptr(counts),
+                              stream_handle(stream)), "ags_render_skip")
 
 
 def ags_backward_workspace_bytes(n: int, views: int) -> int:

@@ -29,7 +29,8 @@ def declared_functions():
 def test_header_declares_the_pipeline():
     names = declared_functions()
     for n in ("ags_preprocess", "ags_emit_pairs", "ags_emit_tile_pairs", "ags_sort", "ags_sort32",
-              "ags_rasterize", "ags_rasterize_backward", "ags_calibrate_lut", "ags_check", "ags_status_reset"):
+              "ags_rasterize", "ags_rasterize_backward", "ags_calibrate_lut", "ags_check", "ags_status_reset",
+              "ags_peripheral_scores", "ags_contribution_hist", "ags_render_skip"):
         assert n in names
 
 
@@ -141,3 +142,20 @@ def test_invalid_arguments_rejected_on_host(lib):
                            ctypes.c_void_p(16), None, None, None, None, st, None) == 1
     # LUT: too many bins
     assert L.ags_calibrate_lut(None, None, 0, 33, 100.0, ctypes.c_void_p(16), None) == 1
+    # diagnostics: missing outputs or inputs, unknown ranking, rule 1 without weights, negative threshold
+    cam1 = B.cameras([dict(width=64, height=48, fx=50.0, fy=50.0, cx=31.5, cy=23.5,
+                           viewmat=[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], campos=[0, 0, 0])])
+    full = B.AgsProjected()
+    full.splat, full.depth, full.flags = ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.c_void_p(768)
+    rg, sv = ctypes.c_void_p(1024), ctypes.c_void_p(2048)
+    assert L.ags_peripheral_scores(ctypes.byref(full), 10, sv, rg, cam1, 1, ctypes.byref(par), None, None) == 1
+    assert L.ags_peripheral_scores(ctypes.byref(pr), 10, sv, rg, cam1, 1, ctypes.byref(par),
+                                   ctypes.c_void_p(4096), None) == 1
+    assert L.ags_contribution_hist(ctypes.byref(full), 10, sv, rg, cam1, 1, ctypes.byref(par), 3, None,
+                                   ctypes.c_void_p(4096), None) == 1
+    assert L.ags_contribution_hist(ctypes.byref(full), 10, sv, rg, cam1, 1, ctypes.byref(par), 1, None,
+                                   ctypes.c_void_p(4096), None) == 1
+    assert L.ags_render_skip(ctypes.byref(full), 10, sv, rg, cam1, 1, ctypes.byref(par), 0, None, -1.0,
+                             ctypes.c_void_p(4096), ctypes.c_void_p(8192), None) == 1
+    assert L.ags_render_skip(ctypes.byref(full), 10, sv, rg, cam1, 1, ctypes.byref(par), 0, None, 0.5,
+                             None, ctypes.c_void_p(8192), None) == 1
