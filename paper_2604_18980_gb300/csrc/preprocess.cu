@@ -8,7 +8,8 @@
 // One thread per Gaussian, looping over all views of the batch: the
 // structure-of-arrays geometry is read once (coalesced) whatever the number of
 // views; the 48 SH floats are read only for views in which the Gaussian
-// survives and touches a tile (from DRAM the first time, then from cache).  Outputs per view and
+// survives and touches a tile (from DRAM the first time, then from cache), by
+// a block-wide colour pass over the queued survivors.  Outputs per view and
 // survivor: a 48-byte splat record (three 16-byte stores), depth, the tile
 // rectangle (one 8-byte store), the tile count, a flag byte and the depth key.
 #include "ellipse.cuh"
@@ -49,119 +50,171 @@ __device__ __forceinline__ void tile_span(float lo, float hi, int len, int& t0, 
   t1 = ((int)phi >> 4) + 1;
 }
 
-// kCacheSH: keep the 48 SH coefficients in registers after the first view that
-// needs them (multi-view batches); otherwise re-read them through the caches.
-template <bool kCacheSH>
-__global__ void __launch_bounds__(256, kCacheSH ? 2 : 3) preprocess_kernel(PreIn in, int64_t n, int views,
-                                                         const __grid_constant__ CamBatch cams,
-                                                         const __grid_constant__ DevParams P, PreOut out,
-                                                         int64_t* status) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+constexpr int kPreThreads = 256;
+constexpr int kPreWarps = kPreThreads / 32;
+
+// Colour of one queued survivor (SH at the world-space direction from the
+// camera centre, + 0.5, clamped at 0) and the rest of its splat record.  The
+// Gaussian's mean and opacity arrive from its lane by shuffles (all lanes call
+// this; only `go` lanes write).
+__device__ __forceinline__ void colour_job(bool go, float4 jb, uint32_t tg, int64_t iw, int64_t n, const float m[3],
+                                           float opac, const CamBatch& cams, const DevParams& P, const PreIn& in,
+                                           const PreOut& out, int64_t* status) {
+  const int gl = (int)(tg & 31u), gv = (int)((tg >> 8) & 0xffu);
+  const float mx = __shfl_sync(0xffffffffu, m[0], gl), my = __shfl_sync(0xffffffffu, m[1], gl),
+              mz = __shfl_sync(0xffffffffu, m[2], gl), op = __shfl_sync(0xffffffffu, opac, gl);
+  if (!go) return;
+  const int64_t gi = iw + gl, ge = (int64_t)gv * n + gi;
+  const DevCam& C = cams.c[gv];
+  const float dx = mx - C.campos[0], dy = my - C.campos[1], dz = mz - C.campos[2];
+  const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+  float Y[16];
+  sh_basis(P.sh_degree, dx * il, dy * il, dz * il, Y);
+  const int nc = (P.sh_degree + 1) * (P.sh_degree + 1);
+  float rgb[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int c = 0; c < 16; c++) {
+    if (c < nc) {
+#pragma unroll
+      for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(__ldg(in.sh + (int64_t)(c * 3 + ch) * n + gi), Y[c], rgb[ch]);
+    }
+  }
+  uint8_t flags = (uint8_t)(tg >> 16);
+  bool bad = false;
+#pragma unroll
+  for (int ch = 0; ch < 3; ch++) {
+    if (!isfinite(rgb[ch])) bad = true;
+    if (rgb[ch] < 0.f) { rgb[ch] = 0.f; flags |= (uint8_t)(1 << ch); }
+  }
+  if (bad) {
+    if (gv == 0) atomicAdd(reinterpret_cast<unsigned long long*>(status + 2), 1ull);
+    write_culled(out, ge);
+    return;
+  }
+  float4* sp = reinterpret_cast<float4*>(out.splat + ge * kSplatFloats);
+  sp[1] = make_float4(jb.x, op, rgb[0], rgb[1]);
+  sp[2] = make_float4(rgb[2], jb.y, jb.z, jb.w);
+  out.flags[ge] = flags;
+}
+
+// One thread per Gaussian, looping over all views.  Per view each lane
+// projects its Gaussian, computes Th and the tile rectangle and writes either
+// the culled record or everything but the colour; the survivors queue up in
+// the warp's shared-memory queue, and whenever 32 are waiting (and after the
+// last view) the warp evaluates 32 SH colours at once, one per lane.  Culling
+// leaves few survivors scattered over the lanes (a few percent of the
+// Gaussian-views on city scenes, a fifth after the AdaGScale cull on object
+// scenes), so evaluating the colour in the lanes that found them would run the
+// SH stage, with most lanes idle, in almost every warp and view.
+__global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(PreIn in, int64_t n, int views,
+                                                                     const __grid_constant__ CamBatch cams,
+                                                                     const __grid_constant__ DevParams P,
+                                                                     PreOut out, int64_t* status) {
+  __shared__ float4 s_job[kPreWarps][64];     // conic C, Th, Sigma_xx, Sigma_yy
+  __shared__ uint32_t s_tag[kPreWarps][64];   // lane | view << 8 | frustum-clamp bits << 16
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kPreThreads + tid;
+  const int64_t iw = i - lane;                // the warp's first Gaussian
+  if (iw >= n) return;                        // whole warps only
+  const bool active = i < n;
 
   // geometry: read once for all views
-  float m[3], ls[3], q[4];
+  float m[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f}, logit = 0.f;
+  if (active) {
 #pragma unroll
-  for (int k = 0; k < 3; k++) m[k] = __ldg(in.mean + k * n + i);
+    for (int k = 0; k < 3; k++) m[k] = __ldg(in.mean + k * n + i);
 #pragma unroll
-  for (int k = 0; k < 3; k++) ls[k] = __ldg(in.ls + k * n + i);
+    for (int k = 0; k < 3; k++) ls[k] = __ldg(in.ls + k * n + i);
 #pragma unroll
-  for (int k = 0; k < 4; k++) q[k] = __ldg(in.quat + k * n + i);
-  const float logit = __ldg(in.logit + i);
+    for (int k = 0; k < 4; k++) q[k] = __ldg(in.quat + k * n + i);
+    logit = __ldg(in.logit + i);
+  }
   const bool finite = isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && isfinite(ls[0]) && isfinite(ls[1]) &&
                       isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]) &&
                       isfinite(logit);
-  if (!finite) {
+  if (active && !finite) {
     atomicAdd(reinterpret_cast<unsigned long long*>(status + 2), 1ull);
     for (int view = 0; view < views; view++) write_culled(out, (int64_t)view * n + i);
-    return;
   }
-  const int nc = (P.sh_degree + 1) * (P.sh_degree + 1);
+  const bool ok = active && finite;
   Frame F;                    // scales, rotation, R S and opacity: once for all views
   make_frame(ls, q, logit, F);
-  float shc[kCacheSH ? 16 : 1][3];
-  bool sh_loaded = false;
+  float4* qj = s_job[warp];
+  uint32_t* qt = s_tag[warp];
+  int qn = 0;                 // queued survivors (warp-uniform)
 
   for (int view = 0; view < views; view++) {
     const DevCam& C = cams.c[view];
     const int64_t e = (int64_t)view * n + i;
-    Proj pj;
-    if (!project_view(C, m, F, pj)) {
-      write_culled(out, e);
-      continue;
-    }
-    // footprint radius: plain 3-sigma, or AdaGScale (Eq. 10, Sec. 3.3)
-    float th = P.tau;
-    float rf;
-    if (P.scale_mode == AGS_SCALE_ADAGSCALE) {
-      const int bin = (int)fminf(pj.t[2] * P.lut_scale, (float)(P.lut_bins - 1));   // depth > 0: trunc = floor
-      const float tup = P.lut[bin];
-      if (!(tup > 0.f)) { write_culled(out, e); continue; }
-      th = P.K / (tup * 6.2831853f * sqrtf(pj.det)) + P.tau;
-      if (th > F.opac) { write_culled(out, e); continue; }
-      rf = ceilf(sqrtf(pj.lam1) * fminf(3.f, sqrtf(2.f * logf(F.opac / th))));
-    } else {
-      rf = ceilf(3.f * sqrtf(pj.lam1));
-    }
-    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-    if (rf > 0.f) {
-      tile_span(pj.u - rf, pj.u + rf, C.W, x0, x1);
-      tile_span(pj.v - rf, pj.v + rf, C.H, y0, y1);
-    }
-    const uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
-    if (touched == 0u) { write_culled(out, e); continue; }
-
-    // colour: SH at the world-space direction from the camera centre (the
-    // coefficients come from DRAM for the first view that needs them and from
-    // the caches for the others)
-    const float dx = m[0] - C.campos[0], dy = m[1] - C.campos[1], dz = m[2] - C.campos[2];
-    const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float Y[16];
-    sh_basis(P.sh_degree, dx * il, dy * il, dz * il, Y);
-    float rgb[3] = {0.5f, 0.5f, 0.5f};
-    if (kCacheSH) {
-      if (!sh_loaded) {
-#pragma unroll
-        for (int k = 0; k < (kCacheSH ? 16 : 1); k++)
-#pragma unroll
-          for (int ch = 0; ch < 3; ch++) shc[k][ch] = k < nc ? __ldg(in.sh + (int64_t)(k * 3 + ch) * n + i) : 0.f;
-        sh_loaded = true;
-      }
-#pragma unroll
-      for (int k = 0; k < (kCacheSH ? 16 : 1); k++)
-#pragma unroll
-        for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(shc[k][ch], Y[k], rgb[ch]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        if (k < nc) {
-#pragma unroll
-          for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(__ldg(in.sh + (int64_t)(k * 3 + ch) * n + i), Y[k], rgb[ch]);
+    bool surv = false;
+    float4 job = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t tag = 0u;
+    if (ok) {
+      Proj pj;
+      bool live = project_view(C, m, F, pj);
+      // footprint radius: plain 3-sigma, or AdaGScale (Eq. 10, Sec. 3.3)
+      float th = P.tau, rf = 0.f;
+      if (live) {
+        if (P.scale_mode == AGS_SCALE_ADAGSCALE) {
+          const int bin = (int)fminf(pj.t[2] * P.lut_scale, (float)(P.lut_bins - 1));   // depth > 0: trunc = floor
+          const float tup = P.lut[bin];
+          if (!(tup > 0.f)) {
+            live = false;
+          } else {
+            th = P.K / (tup * 6.2831853f * sqrtf(pj.det)) + P.tau;
+            if (th > F.opac) live = false;
+            else rf = ceilf(sqrtf(pj.lam1) * fminf(3.f, sqrtf(2.f * logf(F.opac / th))));
+          }
+        } else {
+          rf = ceilf(3.f * sqrtf(pj.lam1));
         }
       }
+      int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+      if (live && rf > 0.f) {
+        tile_span(pj.u - rf, pj.u + rf, C.W, x0, x1);
+        tile_span(pj.v - rf, pj.v + rf, C.H, y0, y1);
+      }
+      const uint32_t touched = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+      if (!live || touched == 0u) {
+        write_culled(out, e);
+      } else {
+        // everything but the colour now; the colour pass writes the rest
+        reinterpret_cast<float4*>(out.splat + e * kSplatFloats)[0] = make_float4(pj.u, pj.v, pj.A, pj.B);
+        out.depth[e] = pj.t[2];
+        reinterpret_cast<uint2*>(out.rect)[e] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16),
+                                                           (uint32_t)x1 | ((uint32_t)y1 << 16));
+        if (out.touched) out.touched[e] = touched;
+        if (out.dkey) out.dkey[e] = __float_as_uint(pj.t[2]);
+        surv = true;
+        job = make_float4(pj.C, th, pj.a + 0.3f, pj.c + 0.3f);
+        tag = (uint32_t)lane | ((uint32_t)view << 8) | ((uint32_t)pj.fclamp << 16);
+      }
     }
-    uint8_t flags = (uint8_t)pj.fclamp;
-    bool bad = false;
-#pragma unroll
-    for (int ch = 0; ch < 3; ch++) {
-      if (!isfinite(rgb[ch])) bad = true;
-      if (rgb[ch] < 0.f) { rgb[ch] = 0.f; flags |= (uint8_t)(1 << ch); }
+    // enqueue this view's survivors behind the waiting ones
+    const unsigned bal = __ballot_sync(0xffffffffu, surv);
+    if (surv) {
+      const int slot = qn + __popc(bal & lanemask_lt());
+      qj[slot] = job;
+      qt[slot] = tag;
     }
-    if (bad) {
-      if (view == 0) atomicAdd(reinterpret_cast<unsigned long long*>(status + 2), 1ull);
-      write_culled(out, e);
-      continue;
+    qn += __popc(bal);
+    __syncwarp();
+    if (qn >= 32) {           // a full batch: one colour per lane
+      colour_job(true, qj[lane], qt[lane], iw, n, m, F.opac, cams, P, in, out, status);
+      __syncwarp();
+      if (lane < qn - 32) {
+        qj[lane] = qj[lane + 32];
+        qt[lane] = qt[lane + 32];
+      }
+      qn -= 32;
+      __syncwarp();
     }
-    float4* sp = reinterpret_cast<float4*>(out.splat + e * kSplatFloats);
-    sp[0] = make_float4(pj.u, pj.v, pj.A, pj.B);
-    sp[1] = make_float4(pj.C, F.opac, rgb[0], rgb[1]);
-    sp[2] = make_float4(rgb[2], th, pj.a + 0.3f, pj.c + 0.3f);
-    out.depth[e] = pj.t[2];
-    reinterpret_cast<uint2*>(out.rect)[e] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16),
-                                                       (uint32_t)x1 | ((uint32_t)y1 << 16));
-    if (out.touched) out.touched[e] = touched;
-    out.flags[e] = flags;
-    if (out.dkey) out.dkey[e] = __float_as_uint(pj.t[2]);
+  }
+  if (qn > 0) {
+    const bool go = lane < qn;
+    colour_job(go, go ? qj[lane] : make_float4(0.f, 0.f, 0.f, 0.f), go ? qt[lane] : 0u, iw, n, m, F.opac, cams, P,
+               in, out, status);
   }
 }
 
@@ -219,8 +272,8 @@ extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* c
   if (((uintptr_t)out->splat & 15u) || ((uintptr_t)out->rect & 7u)) return AGS_ERR_INVALID_ARG;
   PreIn in{g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
   PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags, out->depth_key};
-  auto kern = views > 1 ? preprocess_kernel<true> : preprocess_kernel<false>;
-  kern<<<(unsigned)((g->n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, g->n, views, cb, dp, po, d_status);
+  preprocess_kernel<<<(unsigned)((g->n + kPreThreads - 1) / kPreThreads), kPreThreads, 0, (cudaStream_t)stream>>>(
+      in, g->n, views, cb, dp, po, d_status);
   if (dp.tile_test == AGS_TILE_ELLIPSE) {
     if (!out->tiles_touched) return AGS_ERR_INVALID_ARG;
     cudaError_t e = cudaGetLastError();
