@@ -449,13 +449,20 @@ static int preprocess_one(const double* mean, const double* log_scale, const dou
     double Q = 2.0 * log(opac.v / th);
     dbl[F_QELL] = Q;
     int64_t kept = 0;
-    for (int ty = y0; ty < y1; ty++)
+    for (int ty = y0; ty < y1; ty++) {
+      /* the GPU's keep margin grows with S, the size of q's terms over the
+       * row's part of the square before they cancel (thin, tilted ellipses):
+       * decisions within 2e-6 S of Q are edge cases too */
+      double X = fmax(fabs(OC_TILE * x0 - u.v), fabs(fmin(OC_TILE * x1 - 1, cam->width - 1) - u.v));
+      double Y = fmax(fabs(OC_TILE * ty - v.v), fabs(fmin(OC_TILE * ty + OC_TILE - 1, cam->height - 1) - v.v));
+      double S = A.v * X * X + 2.0 * fabs(B.v) * X * Y + C.v * Y * Y;
       for (int tx = x0; tx < x1; tx++) {
         double m = tile_min_form(dbl, tx, ty, cam->width, cam->height);
         if (m <= Q) kept++;
-        double tol = eps * fmax(Q, 1.0) + 2.0 * par->pos_err * sqrt((A.v + C.v) * fmax(fmax(Q, m), 0.0));
+        double tol = eps * fmax(Q, 1.0) + 2.0 * par->pos_err * sqrt((A.v + C.v) * fmax(fmax(Q, m), 0.0)) + 2e-6 * S;
         if (fabs(m - Q) <= tol) edge |= EDGE_ELLIPSE;
       }
+    }
     irec[I_EDGE] = edge;
     area = kept;
   }

@@ -47,11 +47,19 @@ __device__ __forceinline__ float rect_min_quad_r(float A, float B, float C, floa
 // Q from the stored opacity and threshold (the same expression everywhere).
 __device__ __forceinline__ float ellipse_level(float opacity, float th) { return 2.f * logf(opacity / th); }
 
-// A tile is kept when the minimum of q over its pixel-centre rectangle is at
-// most Q plus a relative 1e-5: a margin far above the fp32 rounding of the
-// blend's own alpha >= tau test, so that in plain mode no tile holding an
-// accepted pixel is ever dropped.
-__device__ __forceinline__ float ellipse_keep_level(float Q) { return Q + 1e-5f * fmaxf(Q, 1.f); }
+// A tile of row ty is kept when the minimum of q over its pixel-centre
+// rectangle is at most Q plus a margin far above the fp32 rounding of both
+// that minimum and the blend's own alpha >= tau test: 1e-5 of Q, plus 1e-6 of
+// S = A X^2 + 2|B| X Y + C Y^2, X and Y the largest |dx| and |dy| of the row's
+// part of the square, which bounds the terms of q before they cancel (thin,
+// tilted ellipses far across a large image).  So in plain mode no tile holding
+// an accepted pixel is ever dropped.
+__device__ __forceinline__ float ellipse_row_keep_level(const EllipseTiles& E, int ty) {
+  const float X = fmaxf(fabsf((float)(kTile * E.x0) - E.u), fabsf((float)min(kTile * E.x1 - 1, E.W - 1) - E.u));
+  const float Y = fmaxf(fabsf((float)(kTile * ty) - E.v), fabsf((float)min(kTile * ty + kTile - 1, E.H - 1) - E.v));
+  const float S = E.A * X * X + 2.f * fabsf(E.B) * X * Y + E.C * Y * Y;
+  return E.Q + 1e-5f * fmaxf(E.Q, 1.f) + 1e-6f * S;
+}
 
 __device__ __forceinline__ float tile_min_q(const EllipseTiles& E, int tx, int ty) {
   const float xl = (float)(kTile * tx) - E.u, xh = (float)min(kTile * tx + kTile - 1, E.W - 1) - E.u;
@@ -139,7 +147,7 @@ __device__ __forceinline__ void ellipse_row_span(const EllipseTiles& E, int ty, 
   lo = 1;
   hi = 0;
   if (!(E.Q >= 0.f) || E.x0 >= E.x1) return;
-  const float Qk = ellipse_keep_level(E.Q);
+  const float Qk = ellipse_row_keep_level(E, ty);
   const float yl = (float)(kTile * ty) - E.v, yh = (float)min(kTile * ty + kTile - 1, E.H - 1) - E.v;
   // det = AC - B^2 to about an ulp however thin the ellipse (Kahan's fma
   // form: the rounding error of B^2 is recovered exactly and subtracted)
