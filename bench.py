@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/backward legs")
     ap.add_argument("--views", type=int, default=None, help="views per step (default: all of the workload's poses)")
+    ap.add_argument("--given-order", action="store_true",
+                    help="keep the Gaussians in the generator's order instead of the Morton storage order")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default: the benchmark configuration); the other configurations "
                          "give lines for the results table")
@@ -237,6 +239,11 @@ def run_ours(args, world, rank, local):
     scene_np, cams, calib = synth.workload(workload)
     cams = cams[:args.views] if args.views else cams
     sc = R.scene_to_device(scene_np)
+    storage = "given order"
+    if not args.given_order:
+        # the renderer's storage order: along a Morton curve of the means (untimed set-up; same images)
+        sc, _ = R.spatial_order(sc)
+        storage = "Morton order of the means (untimed set-up)"
     wp = workload_params(sc, calib, workload)
     V = len(cams)
     # launch parameters from the autotuner (untimed set-up; identical results for every candidate)
@@ -507,7 +514,7 @@ def run_ours(args, world, rank, local):
                    "pairs_per_frame": ada_pairs / V, "sort_passes": passes,
                    "l2": "inputs larger than L2 (params 236 MB, pair keys and values %.2f GB per sort pass)" % (
                        ada_pairs * 16 / 1e9),
-                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU", "storage": storage},
         "timing": "CUDA-graph replay of the whole forward per step; stage_ms from the same steps launched "
                   "eagerly with events between stages (eager %.3f ms/step)" % eager_ms,
         "tuned": dict(knobs),

@@ -25,6 +25,8 @@
  *                           the paper; the pair selection is held fixed)
  *   ags_calibrate_lut       T_up(depth) look-up table from per-Gaussian maximum
  *                           transmittance (Sec. 3.4)
+ *   ags_morton_codes,       storage order of the Gaussians along a Morton curve
+ *   ags_gather_gaussians    (a setup step, not in the paper)
  *   ags_peripheral_scores   diagnostics: exact peripheral score (Eq. 4) at each
  *   ags_contribution_hist   Gaussian's Th beside its estimates (Eq. 6, 7, 9);
  *   ags_render_skip         the contribution distribution of a plain render and
@@ -379,6 +381,28 @@ ags_status ags_render_skip(const ags_projected* proj, int64_t n, const uint32_t*
                            const uint32_t* ranges, const ags_camera* cams, int32_t views,
                            const ags_params* params, int32_t rule, const float* max_T, float thr,
                            float* image, uint64_t* counts, void* stream);
+
+/* Storage order of the Gaussians (not in the paper).  The preprocess runs a
+ * warp's 32 Gaussians through every view together; stored along a Morton
+ * (Z-order) curve of their means, the Gaussians of a warp lie close together,
+ * so the views that cull them (behind the camera, off the image) cull them
+ * together and the projection work follows the visible Gaussians.  The order
+ * is a stable sort (ags_sort32, AGS_SORT_IDENTITY_VALUES, bits [0, 30)) of the
+ * codes below; rendering the permuted scene gives the same images (only
+ * Gaussians of exactly equal depth in one tile, ordered by index, can swap).
+ *
+ * ags_morton_codes: codes[n] (uint32) = the 30-bit Morton code of each mean,
+ * 10 bits per axis over the bounding box of the finite means (bit 3b+a holds
+ * bit b of axis a); a mean that is not finite gets 0xffffffff.  Workspace:
+ * ags_morton_workspace_bytes(), 4-byte aligned.
+ * ags_gather_gaussians: every attribute array of the n Gaussians of `src`
+ * (SH rows for sh_degree) permuted into the caller's arrays (same layouts):
+ * dst[.][k] = src[.][perm[k]]; perm is a permutation of 0..n-1 (an entry >= n
+ * leaves its destination column unwritten). */
+size_t ags_morton_workspace_bytes(void);
+ags_status ags_morton_codes(const ags_gaussians* g, uint32_t* codes, void* ws, size_t ws_bytes, void* stream);
+ags_status ags_gather_gaussians(const ags_gaussians* src, const uint32_t* perm, int32_t sh_degree, float* mean,
+                                float* log_scale, float* quat, float* opacity_logit, float* sh, void* stream);
 
 /* Scratch bytes needed by ags_rasterize_backward. */
 size_t ags_backward_workspace_bytes(int64_t n, int32_t views);

@@ -83,6 +83,9 @@ EXPORTS = {
                    _I32),
     "ags_rasterize": ([_P, _I64, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "ags_calibrate_lut": ([_P, _P, _I64, _I32, _F, _P, _P], _I32),
+    "ags_morton_workspace_bytes": ([], ctypes.c_size_t),
+    "ags_morton_codes": ([_P, _P, _P, ctypes.c_size_t, _P], _I32),
+    "ags_gather_gaussians": ([_P, _P, _I32, _P, _P, _P, _P, _P, _P], _I32),
     "ags_peripheral_scores": ([_P, _I64, _P, _P, _P, _I32, _P, _P, _P], _I32),
     "ags_contribution_hist": ([_P, _I64, _P, _P, _P, _I32, _P, _I32, _P, _P, _P], _I32),
     "ags_render_skip": ([_P, _I64, _P, _P, _P, _I32, _P, _I32, _P, _F, _P, _P, _P], _I32),
@@ -322,6 +325,23 @@ def ags_rasterize(proj, n, sorted_vals, ranges, cams, params_, image, final_T, n
 def ags_calibrate_lut(max_T, depth, count, lut_bins, lut_depth_max, lut_out, stream=None):
     _ok(lib().ags_calibrate_lut(ptr(max_T), ptr(depth), int(count), int(lut_bins), float(lut_depth_max),
                                 ptr(lut_out), stream_handle(stream)), "ags_calibrate_lut")
+
+
+def ags_morton_workspace_bytes() -> int:
+    return int(lib().ags_morton_workspace_bytes())
+
+
+def ags_morton_codes(scene, codes, ws, stream=None):
+    g = gaussians(scene)
+    _ok(lib().ags_morton_codes(ctypes.byref(g), ptr(codes), ptr(ws), ws.numel() * ws.element_size(),
+                               stream_handle(stream)), "ags_morton_codes")
+
+
+def ags_gather_gaussians(scene, perm, sh_degree, dst, stream=None):
+    g = gaussians(scene)
+    _ok(lib().ags_gather_gaussians(ctypes.byref(g), ptr(perm), int(sh_degree), ptr(dst["mean"]),
+                                   ptr(dst["log_scale"]), ptr(dst["quat"]), ptr(dst["opacity_logit"]), ptr(dst["sh"]),
+                                   stream_handle(stream)), "ags_gather_gaussians")
 
 
 AGS_CONTRIB_HIST_BINS = 32768

@@ -24,6 +24,32 @@ def scene_to_device(scene: dict, device="cuda") -> dict:
             for k in SCENE_KEYS}
 
 
+def spatial_order(scene: dict) -> tuple:
+    """The scene stored along a Morton curve of its means (a setup step, not in
+    the paper): returns (permuted scene, perm) with new[k] = old[perm[k]].  The
+    Gaussians of a warp then lie close together, so a view culls them together;
+    the images are those of the original order (only Gaussians of exactly equal
+    depth in one tile can swap places)."""
+    n = int(scene["opacity_logit"].shape[0])
+    dev = scene["mean"].device
+    sh_degree = int(round(math.sqrt(scene["sh"].shape[0]))) - 1
+    codes = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ws = torch.empty(B.ags_morton_workspace_bytes(), dtype=torch.uint8, device=dev)
+    B.ags_morton_codes(scene, codes, ws)
+    codes_alt = torch.empty_like(codes)
+    vals, vals_alt = torch.empty_like(codes), torch.empty_like(codes)
+    count = torch.full((1,), n, dtype=torch.int64, device=dev)
+    status = torch.zeros(4, dtype=torch.int64, device=dev)
+    ws_sort = torch.empty(B.ags_sort_workspace_bytes(max(n, 1)), dtype=torch.uint8, device=dev)
+    alt = B.ags_sort32(codes, vals, codes_alt, vals_alt, count, max(n, 1), 0, 30, 8, None, 0, status, ws_sort,
+                       flags=B.AGS_SORT_IDENTITY_VALUES)
+    perm = (vals_alt if alt else vals)[:n]
+    out = {k: torch.empty_like(v) for k, v in scene.items()}
+    B.ags_gather_gaussians(scene, perm, sh_degree, out)
+    B.ags_check(status)
+    return out, perm
+
+
 def tiles_per_view(cam: dict) -> int:
     return ((cam["width"] + B.AGS_TILE - 1) // B.AGS_TILE) * ((cam["height"] + B.AGS_TILE - 1) // B.AGS_TILE)
 
