@@ -493,8 +493,28 @@ def run_ours(args, world, rank, local):
         b.record(stream)
         barrier()
         fb.check()
+        eager_ms = max_over_ranks(a.elapsed_time(b)) / args.steps
+        # the same step captured in a CUDA graph, as the forward is timed
+        g_fb = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            fwd_bwd()
+        stream.wait_stream(side)
+        with torch.cuda.graph(g_fb):
+            fwd_bwd()
+        for _ in range(args.warmup):
+            g_fb.replay()
+        barrier()
+        a.record(stream)
+        for _ in range(args.steps):
+            g_fb.replay()
+        b.record(stream)
+        barrier()
+        fb.check()
         extras["fwd_bwd_ms"] = max_over_ranks(a.elapsed_time(b)) / args.steps
-        del fb, grads, target
+        extras["fwd_bwd_ms_eager"] = eager_ms
+        del fb, grads, target, g_fb
 
     if rank != 0:
         if world > 1:
