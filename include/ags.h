@@ -218,6 +218,11 @@ size_t ags_emit_tile_workspace_bytes(int64_t n, int32_t views);
 #define AGS_EMIT_SINGLE_PASS 1  /* ags_emit_tile_pairs flag: one fused scan-and-emit pass over
                                    partitions of Gaussian-views (faster when the tile counts
                                    are spread evenly along the order) */
+#define AGS_EMIT_VIEW_SHIFT 4   /* ags_emit_tile_pairs flag: key = (view << tile_bits) | tile,
+                                   tile_bits = the bits of tiles_per_view - 1 (at least 1), for
+                                   ags_sort_tiles; with an `order` that lists each view's
+                                   Gaussian-views together (views ascending, depth order within
+                                   each: a stable sort of ags_view_keys after the depth sort) */
 ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, int32_t views,
                                const ags_camera* cams, const uint32_t* order,
                                const int64_t* d_order_count, uint32_t* keys, uint32_t* vals,
@@ -238,6 +243,13 @@ size_t ags_compact_workspace_bytes(int64_t n, int32_t views);
 ags_status ags_compact_visible(const ags_projected* proj, int64_t n, int32_t views, uint32_t* keys,
                                uint32_t* ids, int64_t* d_count, int64_t* d_status, void* ws,
                                size_t ws_bytes, void* stream);
+
+/* View of each listed Gaussian-view: keys[k] = order[k] / n for k < *d_count
+ * (device int64, clamped to [0, capacity]).  A stable sort of these keys
+ * (ags_sort32, values `order`) after the depth sort lists the views one after
+ * the other, each in depth order -- the order AGS_EMIT_VIEW_SHIFT expects. */
+ags_status ags_view_keys(const uint32_t* order, const int64_t* d_count, int64_t capacity, int64_t n,
+                         uint32_t* keys, void* stream);
 
 /* Largest views*n that ags_emit_pairs_noalloc accepts (2^24). */
 int64_t ags_emit_pairs_noalloc_max_gaussians(void);
@@ -308,6 +320,20 @@ ags_status ags_sort32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
                       int32_t end_bit, int32_t digit_bits, int32_t flags, uint32_t* ranges,
                       int64_t num_ranges, int32_t* result_in_alt, int64_t* d_status, void* ws,
                       size_t ws_bytes, void* stream);
+
+/* Sort of view-shifted tile keys (AGS_EMIT_VIEW_SHIFT): ags_sort32 over bits
+ * [0, tile_bits) only, i.e. by tile, stable, so that the pairs of one tile keep
+ * the emission order -- view by view, each in depth order; fewer key bits than
+ * view * tiles_per_view + tile when the views outnumber the spare bits.  ranges
+ * (nullable, [views * tiles_per_view][2]) are indexed by view * tiles_per_view +
+ * tile, the view being the key's bits above tile_bits.  Same workspace, flags
+ * and results as ags_sort32; tiles_per_view <= 2^tile_bits, views << tile_bits
+ * <= 2^32. */
+ags_status ags_sort_tiles(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                          const int64_t* d_num_pairs, int64_t capacity, int32_t tile_bits,
+                          int32_t digit_bits, int32_t flags, uint32_t* ranges, int32_t views,
+                          int32_t tiles_per_view, int32_t* result_in_alt, int64_t* d_status, void* ws,
+                          size_t ws_bytes, void* stream);
 
 /* Blending (Eq. 1, Eq. 2; Sec. 3.3 dual size).  One CTA per 16x16 tile of
  * each view; per pixel, front to back over the tile's sorted pairs:

@@ -81,6 +81,9 @@ EXPORTS = {
                  _I32),
     "ags_sort32": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _I32, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P],
                    _I32),
+    "ags_sort_tiles": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P, ctypes.c_size_t,
+                        _P], _I32),
+    "ags_view_keys": ([_P, _P, _I64, _I64, _P, _P], _I32),
     "ags_rasterize": ([_P, _I64, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "ags_calibrate_lut": ([_P, _P, _I64, _I32, _F, _P, _P], _I32),
     "ags_morton_workspace_bytes": ([], ctypes.c_size_t),
@@ -242,6 +245,7 @@ def ags_emit_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, w
 
 
 AGS_EMIT_SINGLE_PASS = 1
+AGS_EMIT_VIEW_SHIFT = 4
 
 
 def ags_emit_tile_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, ws, order=None,
@@ -311,6 +315,22 @@ def ags_sort32(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit,
                          ctypes.byref(alt), ptr(d_status), ptr(ws), ws.numel() * ws.element_size(),
                          stream_handle(stream)), "ags_sort32")
     return bool(alt.value)
+
+
+def ags_sort_tiles(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, tile_bits, digit_bits, ranges, views,
+                   tiles_per_view, d_status, ws, flags=0, stream=None) -> bool:
+    """Sort of view-shifted tile keys by their tile bits; returns True when the result is in the alt buffers."""
+    alt = ctypes.c_int32(0)
+    _ok(lib().ags_sort_tiles(ptr(keys), ptr(vals), ptr(keys_alt), ptr(vals_alt), ptr(d_num_pairs), int(capacity),
+                             int(tile_bits), int(digit_bits), int(flags), ptr(ranges), int(views),
+                             int(tiles_per_view), ctypes.byref(alt), ptr(d_status), ptr(ws),
+                             ws.numel() * ws.element_size(), stream_handle(stream)), "ags_sort_tiles")
+    return bool(alt.value)
+
+
+def ags_view_keys(order, d_count, capacity, n, keys, stream=None):
+    _ok(lib().ags_view_keys(ptr(order), ptr(d_count), int(capacity), int(n), ptr(keys), stream_handle(stream)),
+        "ags_view_keys")
 
 
 def ags_rasterize(proj, n, sorted_vals, ranges, cams, params_, image, final_T, n_contrib, d_status, max_T=None,

@@ -555,14 +555,20 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
   cudaStream_t st = (cudaStream_t)stream;
   if (total == 0) return launch_status(cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st));
   if (!proj->rect || (capacity > 0 && (!keys || !vals))) return AGS_ERR_INVALID_ARG;
-  if (flags & ~(AGS_EMIT_SINGLE_PASS | AGS_EMIT_ELLIPSE)) return AGS_ERR_INVALID_ARG;
+  if (flags & ~(AGS_EMIT_SINGLE_PASS | AGS_EMIT_ELLIPSE | AGS_EMIT_VIEW_SHIFT)) return AGS_ERR_INVALID_ARG;
   EllipseSrc ell;
   s = ellipse_src(proj, cb, flags, &ell);
   if (s != AGS_OK) return s;
   if (!ws || ws_bytes < ags_emit_tile_workspace_bytes(n, views) || ((uintptr_t)ws & 15u)) return AGS_ERR_INVALID_ARG;
   const size_t parts = emit_parts(total);
+  // the view's part of a key: view * tiles_per_view, or view << tile_bits (AGS_EMIT_VIEW_SHIFT)
   uint32_t tiles_per_view = (uint32_t)cb.c[0].gx * (uint32_t)cb.c[0].gy;
-  if ((uint64_t)tiles_per_view * (uint64_t)views >= (1ull << 32)) return AGS_ERR_INVALID_ARG;
+  if (flags & AGS_EMIT_VIEW_SHIFT) {
+    uint32_t stride = 2u;
+    while (stride < tiles_per_view) stride <<= 1;
+    tiles_per_view = stride;
+  }
+  if ((uint64_t)tiles_per_view * (uint64_t)views > (1ull << 32)) return AGS_ERR_INVALID_ARG;
   cudaError_t e = cudaMemsetAsync(ws, 0, 256 + 8 * parts, st);
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws);

@@ -41,8 +41,17 @@ __device__ __forceinline__ uint32_t key_digit(uint64_t k, int shift, uint32_t ma
 }
 // Range (tile) index of a key: 32-bit keys are the index, 64-bit pair keys
 // carry it in the high word.
-__device__ __forceinline__ uint32_t key_range(uint32_t k) { return k; }
-__device__ __forceinline__ uint32_t key_range(uint64_t k) { return (uint32_t)(k >> 32); }
+// Range index of a key: the key itself (64-bit keys: their high word), or, for
+// tile keys that carry the view above `shift` bits (view << shift | tile),
+// view * per + tile.
+struct RangeMap {
+  uint32_t shift;   // 0: the key itself
+  uint32_t per;     // ranges per view
+};
+__device__ __forceinline__ uint32_t key_range(uint32_t k, RangeMap m) {
+  return m.shift ? (k >> m.shift) * m.per + (k & ((1u << m.shift) - 1u)) : k;
+}
+__device__ __forceinline__ uint32_t key_range(uint64_t k, RangeMap) { return (uint32_t)(k >> 32); }
 
 // Staging index with one padding word per 32: keys of consecutive digits are
 // staged about 4096 / RADIX words apart, which would otherwise put many lanes
@@ -179,7 +188,7 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 3 : 2)
 onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
                 uint32_t* __restrict__ vout, const int64_t* count_ptr, int64_t capacity, int identity, int shift,
                 uint32_t mask, int rank_or, const uint32_t* __restrict__ gprefix, uint32_t* lookback,
-                uint32_t* counter, int64_t* status, uint32_t* ranges, uint32_t num_ranges) {
+                uint32_t* counter, int64_t* status, uint32_t* ranges, uint32_t num_ranges, RangeMap rmap) {
   using Sm = SortSmem<RADIX, K>;
   constexpr int kWarps = Sm::kWarps;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -336,10 +345,10 @@ onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* 
       // last pass: the output is fully sorted, so a range index's keys are
       // consecutive here and in the output; its first and last key in this
       // block bound its range (other blocks holding it do the same)
-      const uint32_t r = key_range(k);
+      const uint32_t r = key_range(k, rmap);
       uint32_t rp = __shfl_up_sync(0xffffffffu, r, 1), rn = __shfl_down_sync(0xffffffffu, r, 1);
-      if (lane == 0) rp = (v && j > 0) ? key_range(S.u.stage.keys[stage_index(j - 1)]) : 0xffffffffu;
-      if (lane == 31) rn = (j + 1 < nvalid) ? key_range(S.u.stage.keys[stage_index(j + 1)]) : 0xffffffffu;
+      if (lane == 0) rp = (v && j > 0) ? key_range(S.u.stage.keys[stage_index(j - 1)], rmap) : 0xffffffffu;
+      if (lane == 31) rn = (j + 1 < nvalid) ? key_range(S.u.stage.keys[stage_index(j + 1)], rmap) : 0xffffffffu;
       if (j + 1 >= nvalid) rn = 0xffffffffu;
       if (j == 0) rp = 0xffffffffu;
       if (dst < count && r < num_ranges) {
@@ -361,13 +370,13 @@ __global__ void ranges_fixup_kernel(uint2* ranges, int64_t num_ranges) {
 // Ranges of keys that are already sorted (a sort with no digit pass).
 template <typename K>
 __global__ void ranges_kernel(const K* __restrict__ keys, const int64_t* count_ptr, int64_t capacity,
-                              uint32_t* ranges, int64_t num_ranges) {
+                              uint32_t* ranges, int64_t num_ranges, RangeMap rmap) {
   const int64_t count = clamped_count(count_ptr, capacity);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t r = key_range(keys[i]);
+    const uint32_t r = key_range(keys[i], rmap);
     if (r >= (uint64_t)num_ranges) continue;
-    if (i == 0 || key_range(keys[i - 1]) != r) ranges[2 * (size_t)r] = (uint32_t)i;
-    if (i == count - 1 || key_range(keys[i + 1]) != r) ranges[2 * (size_t)r + 1] = (uint32_t)(i + 1);
+    if (i == 0 || key_range(keys[i - 1], rmap) != r) ranges[2 * (size_t)r] = (uint32_t)i;
+    if (i == count - 1 || key_range(keys[i + 1], rmap) != r) ranges[2 * (size_t)r + 1] = (uint32_t)(i + 1);
   }
 }
 
@@ -377,7 +386,8 @@ template <int RADIX, typename K>
 static cudaError_t launch_passes(K*& kin, uint32_t*& vin, K* kout, uint32_t* vout, const int64_t* d_num_pairs,
                                  int64_t capacity, int begin_bit, int end_bit, int digit_bits, int passes,
                                  int flags, uint32_t* ghist, uint32_t* lookback, uint32_t* counters,
-                                 int64_t* d_status, uint32_t* ranges, int64_t num_ranges, cudaStream_t st) {
+                                 int64_t* d_status, uint32_t* ranges, int64_t num_ranges, RangeMap rmap,
+                                 cudaStream_t st) {
   hist_scan_kernel<RADIX><<<passes, RADIX, 0, st>>>(ghist);
   const int rank_or = (flags & AGS_SORT_RANK_OR) ? 1 : 0;
   const int smem = (int)sort_smem_bytes<RADIX, K>(rank_or != 0);
@@ -398,7 +408,7 @@ static cudaError_t launch_passes(K*& kin, uint32_t*& vin, K* kout, uint32_t* vou
     onesweep_kernel<RADIX, K><<<(unsigned)parts, kSortThreads, smem, st>>>(
         kin, vin, ko, vout, d_num_pairs, capacity, identity, sh, mask, rank_or, ghist + p * RADIX, lookback,
         counters + p,
-        d_status, last ? ranges : nullptr, (uint32_t)num_ranges);
+        d_status, last ? ranges : nullptr, (uint32_t)num_ranges, rmap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     std::swap(kin, kout);
@@ -411,7 +421,7 @@ template <typename K>
 static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, const int64_t* d_num_pairs,
                             int64_t capacity, int32_t begin_bit, int32_t end_bit, int32_t digit_bits, int32_t flags,
                             uint32_t* ranges, int64_t num_ranges, int32_t* result_in_alt, int64_t* d_status,
-                            void* ws, size_t ws_bytes, void* stream);
+                            void* ws, size_t ws_bytes, void* stream, RangeMap rmap = RangeMap{0u, 0u});
 
 }  // namespace ags
 
@@ -426,7 +436,7 @@ template <typename K>
 static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, const int64_t* d_num_pairs,
                             int64_t capacity, int32_t begin_bit, int32_t end_bit, int32_t digit_bits, int32_t flags,
                             uint32_t* ranges, int64_t num_ranges, int32_t* result_in_alt, int64_t* d_status,
-                            void* ws, size_t ws_bytes, void* stream) {
+                            void* ws, size_t ws_bytes, void* stream, RangeMap rmap) {
   constexpr int kKeyBits = 8 * (int)sizeof(K);
   if (!d_num_pairs || !d_status || capacity < 0 || capacity >= AGS_MAX_PAIRS) return AGS_ERR_INVALID_ARG;
   if (begin_bit < 0 || end_bit > kKeyBits || begin_bit > end_bit || digit_bits < 4 || digit_bits > 9)
@@ -464,10 +474,10 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
     }
     e = radix == 512 ? launch_passes<512, K>(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
                                              digit_bits, passes, flags, ghist, lookback, counters, d_status, ranges,
-                                             num_ranges, st)
+                                             num_ranges, rmap, st)
                      : launch_passes<256, K>(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
                                              digit_bits, passes, flags, ghist, lookback, counters, d_status, ranges,
-                                             num_ranges, st);
+                                             num_ranges, rmap, st);
     if (e != cudaSuccess) return AGS_ERR_CUDA;
   }
   if (ranges) {
@@ -479,7 +489,7 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
       if (e != cudaSuccess) return AGS_ERR_CUDA;
       if (capacity > 0) {
         const int blocks = (int)std::min<int64_t>((capacity + 255) / 256, 65535 * 4);
-        ranges_kernel<K><<<blocks, 256, 0, st>>>(kin, d_num_pairs, capacity, ranges, num_ranges);
+        ranges_kernel<K><<<blocks, 256, 0, st>>>(kin, d_num_pairs, capacity, ranges, num_ranges, rmap);
       }
     }
   }
@@ -506,4 +516,17 @@ extern "C" ags_status ags_sort32(uint32_t* keys, uint32_t* vals, uint32_t* keys_
   return ags::sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
                                   digit_bits, flags, ranges, num_ranges, result_in_alt, d_status, ws, ws_bytes,
                                   stream);
+}
+
+extern "C" ags_status ags_sort_tiles(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                                     const int64_t* d_num_pairs, int64_t capacity, int32_t tile_bits,
+                                     int32_t digit_bits, int32_t flags, uint32_t* ranges, int32_t views,
+                                     int32_t tiles_per_view, int32_t* result_in_alt, int64_t* d_status, void* ws,
+                                     size_t ws_bytes, void* stream) {
+  if (tile_bits < 1 || tile_bits > 31 || views < 1 || tiles_per_view < 1 ||
+      (int64_t)tiles_per_view > ((int64_t)1 << tile_bits) || (int64_t)views << tile_bits > ((int64_t)1 << 32))
+    return AGS_ERR_INVALID_ARG;
+  return ags::sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, 0, tile_bits, digit_bits,
+                                  flags, ranges, (int64_t)views * tiles_per_view, result_in_alt, d_status, ws,
+                                  ws_bytes, stream, ags::RangeMap{(uint32_t)tile_bits, (uint32_t)tiles_per_view});
 }

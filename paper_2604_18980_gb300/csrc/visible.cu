@@ -9,6 +9,8 @@
 // look-back over the preceding blocks (bounded spin), and writes
 // (float_bits(depth[e]), e) for its visible entries in increasing e -- so each
 // view's entries keep increasing Gaussian index, the tie order of the sort.
+#include <algorithm>
+
 #include "ags_internal.cuh"
 
 namespace ags {
@@ -159,5 +161,31 @@ extern "C" ags_status ags_compact_visible(const ags_projected* proj, int64_t n, 
   visible_kernel<<<(unsigned)parts, kVisThreads, 0, st>>>(proj->flags, proj->depth, (uint32_t)total, keys, ids,
                                                           d_count, d_status, part_status, counter,
                                                           (uint32_t)parts);
+  return launch_status(cudaGetLastError());
+}
+
+namespace ags {
+
+__global__ void __launch_bounds__(256) view_keys_kernel(const uint32_t* __restrict__ order, const int64_t* d_count,
+                                                        int64_t capacity, uint32_t n, uint32_t* __restrict__ keys) {
+  int64_t count = *d_count;
+  count = count < 0 ? 0 : (count > capacity ? capacity : count);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+    keys[k] = __ldg(order + k) / n;
+}
+
+}  // namespace ags
+
+extern "C" ags_status ags_view_keys(const uint32_t* order, const int64_t* d_count, int64_t capacity, int64_t n,
+                                    uint32_t* keys, void* stream) {
+  using namespace ags;
+  if (!d_count || capacity < 0 || n < 1 || n > ((int64_t)1 << 32) - 1) return AGS_ERR_INVALID_ARG;
+  if (capacity == 0) return AGS_OK;
+  if (!order || !keys) return AGS_ERR_INVALID_ARG;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<int64_t>((capacity + 255) / 256, (int64_t)sms * 8);
+  view_keys_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(order, d_count, capacity, (uint32_t)n, keys);
   return launch_status(cudaGetLastError());
 }

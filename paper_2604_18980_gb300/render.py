@@ -77,7 +77,7 @@ class Renderer:
                  sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 9,
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
                  presort: bool = True, pair_rank_or: bool = True, emit_two_pass: bool = True,
-                 keep_state: bool = True, tile_test: int = B.AGS_TILE_SQUARE):
+                 keep_state: bool = True, tile_test: int = B.AGS_TILE_SQUARE, view_major: bool | None = None):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -91,6 +91,13 @@ class Renderer:
         self.emit_two_pass = emit_two_pass
         self.tile_test = tile_test
         self.emit_flags = B.AGS_EMIT_ELLIPSE if tile_test == B.AGS_TILE_ELLIPSE else 0
+        # view-major tile keys (view << tile_bits | tile, sorted by the tile bits
+        # alone): by default wherever they save a pair-sort pass
+        self.tile_bits = max(1, (self.T - 1).bit_length())
+        if view_major is None:
+            view_major = (self.V > 1 and digit_plan(self.tile_bits, digit_bits)[0]
+                          < digit_plan(tile_key_bits(self.V, self.T), digit_bits)[0])
+        self.view_major = bool(view_major) and presort and (self.V << self.tile_bits) <= (1 << 32)
         self.keep_state = keep_state or want_backward   # final_T / n_contrib for the backward
         self.set_params(scale_mode, K, lut, sh_degree, bg)
         dev, V, n = self.device, self.V, self.n
@@ -161,8 +168,11 @@ class Renderer:
 
     @property
     def end_bit(self) -> int:
-        """Highest sorted key bit + 1: the tile key (32-bit keys) or tile | depth (64-bit keys)."""
-        return tile_key_bits(self.V, self.T) if self.presort else key_end_bit(self.V, self.T)
+        """Highest sorted key bit + 1: the tile key (32-bit keys; the tile alone with
+        view-major keys) or tile | depth (64-bit keys)."""
+        if self.presort:
+            return self.tile_bits if self.view_major else tile_key_bits(self.V, self.T)
+        return key_end_bit(self.V, self.T)
 
     def sort_plan(self) -> tuple:
         """(passes, digit_bits) of the pair sort."""
@@ -175,6 +185,8 @@ class Renderer:
         n = 1 + 1 + (2 + self.sort_plan()[0] + 1) + 1
         if self.presort:       # compaction, then (histogram, digit scan, passes)
             n += 1 + 2 + digit_plan(self.dsort_end, self.digit_bits)[0]
+            if self.view_major:   # view keys, then (histogram, digit scan, one pass)
+                n += 1 + 3
         return n
 
     # -- stages ---------------------------------------------------------------
@@ -192,13 +204,24 @@ class Renderer:
                                self.V * self.n, 0, self.dsort_end, db, None, 0, self.status, self.ws_dsort,
                                flags=B.AGS_SORT_DISCARD_KEYS)
             self.emit_order = self.order_alt if alt else self.order
+            if self.view_major:
+                # then stably by view: the views one after the other, each in
+                # depth order (the depth keys are spent; their buffers hold the views)
+                other = self.order if alt else self.order_alt
+                vb = max(1, (self.V - 1).bit_length())
+                B.ags_view_keys(self.emit_order, self.n_visible, self.V * self.n, self.n, self.dkey)
+                alt2 = B.ags_sort32(self.dkey, self.emit_order, self.dkey_alt, other, self.n_visible, self.V * self.n,
+                                    0, vb, min(9, max(4, vb)), None, 0, self.status, self.ws_dsort,
+                                    flags=B.AGS_SORT_DISCARD_KEYS)
+                self.emit_order = other if alt2 else self.emit_order
 
     def emit(self):
         if self.presort:
             B.ags_emit_tile_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity,
                                   self.num_pairs, self.status, self.ws_emit, order=self.emit_order,
                                   order_count=self.n_visible,
-                                  flags=self.emit_flags | (0 if self.emit_two_pass else B.AGS_EMIT_SINGLE_PASS))
+                                  flags=self.emit_flags | (0 if self.emit_two_pass else B.AGS_EMIT_SINGLE_PASS)
+                                  | (B.AGS_EMIT_VIEW_SHIFT if self.view_major else 0))
         else:
             B.ags_emit_pairs(self.proj, self.n, self.cams, self.keys, self.vals, self.capacity, self.num_pairs,
                              self.status, self.ws_emit, flags=self.emit_flags)
@@ -207,10 +230,15 @@ class Renderer:
         """Stable sort of the pairs by tile (and depth); only the values and the
         per-tile ranges are kept."""
         _, db = self.sort_plan()
-        fn = B.ags_sort32 if self.presort else B.ags_sort
         flags = B.AGS_SORT_DISCARD_KEYS | (B.AGS_SORT_RANK_OR if self.pair_rank_or else 0)
-        alt = fn(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity, 0, self.end_bit,
-                 db, self.ranges, self.V * self.T, self.status, self.ws_sort, flags=flags)
+        if self.view_major:
+            alt = B.ags_sort_tiles(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity,
+                                   self.tile_bits, db, self.ranges, self.V, self.T, self.status, self.ws_sort,
+                                   flags=flags)
+        else:
+            fn = B.ags_sort32 if self.presort else B.ags_sort
+            alt = fn(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity, 0,
+                     self.end_bit, db, self.ranges, self.V * self.T, self.status, self.ws_sort, flags=flags)
         self.sorted_vals = self.vals_alt if alt else self.vals
 
     def rasterize(self, max_T=None):

@@ -77,18 +77,24 @@ def compare_features(r, orc_out, view=0):
 def gpu_pairs(r):
     """Sorted pairs as 64-bit (tile | depth) keys and values, rebuilt from the
     sorted values, the tile ranges and the per-splat depths (the renderer keeps
-    no sorted keys).  Checks on the way that the non-empty ranges tile
-    [0, pairs) in tile order."""
+    no sorted keys), in the order of the range index view * T + tile (view-major
+    keys group the array by tile, then view).  Checks on the way that the
+    non-empty ranges partition [0, pairs)."""
     npairs = r.pairs()
     vals = r.sorted_vals[:npairs].cpu().numpy().view(np.uint32).astype(np.int64)
     rg = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
     length = rg[:, 1] - rg[:, 0]
     assert np.all(length >= 0)
     full = np.nonzero(length > 0)[0]
-    ends = np.cumsum(length[full])
-    assert ends.size == 0 or ends[-1] == npairs, "ranges do not cover the pairs"
-    np.testing.assert_array_equal(rg[full, 0], ends - length[full])
-    tile = np.repeat(full, length[full]).astype(np.uint64)
+    starts, lens = rg[full, 0], length[full]
+    by_start = np.argsort(starts, kind="stable")
+    s_sorted, e_sorted = starts[by_start], starts[by_start] + lens[by_start]
+    assert npairs == 0 or (s_sorted[0] == 0 and e_sorted[-1] == npairs), "ranges do not cover the pairs"
+    assert np.array_equal(s_sorted[1:], e_sorted[:-1]), "ranges overlap or leave gaps"
+    excl = np.cumsum(lens) - lens
+    idx = np.arange(int(lens.sum()), dtype=np.int64) + np.repeat(starts - excl, lens)
+    vals = vals[idx]
+    tile = np.repeat(full, lens).astype(np.uint64)
     dbits = r.proj["depth"].cpu().numpy().view(np.uint32)[vals].astype(np.uint64)
     return (tile << np.uint64(32)) | dbits, vals
 

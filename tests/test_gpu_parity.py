@@ -231,13 +231,18 @@ def test_backward_c1_scale_and_views():
         assert rel <= 1e-3, (k, rel)
 
 
-def test_depth_presort_equals_full_key_sort():
+@pytest.mark.parametrize("knobs", [dict(view_major=False), dict(view_major=True),
+                                   dict(view_major=True, emit_two_pass=False, digit_bits=5)])
+def test_depth_presort_equals_full_key_sort(knobs):
     """Sorting the Gaussians by depth first and then only the tile digits of the
-    pairs gives exactly the stable sort of the full (tile | depth) keys."""
+    pairs gives exactly the stable sort of the full (tile | depth) keys; so do
+    view-major keys (the views one after the other in the emission order,
+    sorted by the tile bits alone, the ranges indexed through the view bits)."""
     scene, cams = _c1(n=12000, W=200, H=150, views=3)
     sc = R.scene_to_device(scene)
     for mode, K in ((0, 0.0), (1, 0.5)):
-        a = R.Renderer(sc, cams, mode, K, presort=True)
+        a = R.Renderer(sc, cams, mode, K, presort=True, **knobs)
+        assert a.view_major == knobs["view_major"]
         b = R.Renderer(sc, cams, mode, K, presort=False)
         ia, ib = a.forward().clone(), b.forward().clone()
         a.check()
@@ -247,9 +252,13 @@ def test_depth_presort_equals_full_key_sort():
         ka, va = gpu_pairs(a)
         kb, vb = gpu_pairs(b)
         np.testing.assert_array_equal(ka, kb)
-        assert torch.equal(a.sorted_vals[:np_], b.sorted_vals[:np_])
+        np.testing.assert_array_equal(va, vb)
         assert torch.equal(ia, ib)
-        assert torch.equal(a.ranges, b.ranges)
+        ra, rb = a.ranges.view(-1, 2), b.ranges.view(-1, 2)
+        assert torch.equal(ra[:, 1] - ra[:, 0], rb[:, 1] - rb[:, 0])
+        if not a.view_major:
+            assert torch.equal(a.sorted_vals[:np_], b.sorted_vals[:np_])
+            assert torch.equal(a.ranges, b.ranges)
 
 
 def test_sort_identity_values_flag():
@@ -454,9 +463,10 @@ def test_autotuner_candidates_render_identically():
         r = R.Renderer(sc, cams, 1, 0.3, **cand)
         imgs.append(r.forward().clone())
         r.check()
-        lists.append((r.sorted_vals[:r.pairs()].clone(), r.ranges.clone()))
-    for im, (v, rg) in zip(imgs[1:], lists[1:]):
+        lists.append(gpu_pairs(r))                       # per-tile lists in range order
+    for im, (k, v) in zip(imgs[1:], lists[1:]):
         assert torch.equal(im, imgs[0])
-        assert torch.equal(v, lists[0][0]) and torch.equal(rg, lists[0][1])
+        np.testing.assert_array_equal(k, lists[0][0])
+        np.testing.assert_array_equal(v, lists[0][1])
     best = autotune.tune(sc, cams, 1, 0.3, use_cache=False, warmup=1, reps=2)
     assert best["digit_bits"] in (7, 8, 9) and len(best["table"]) == len(autotune.CANDIDATES)

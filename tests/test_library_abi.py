@@ -142,6 +142,14 @@ def test_invalid_arguments_rejected_on_host(lib):
                            ctypes.c_void_p(16), None, None, None, None, st, None) == 1
     # LUT: too many bins
     assert L.ags_calibrate_lut(None, None, 0, 33, 100.0, ctypes.c_void_p(16), None) == 1
+    # view-major tile sort: no tile bits, more tiles than the bits hold, key overflow; view keys without n
+    assert L.ags_sort_tiles(None, None, None, None, npairs, 0, 0, 8, 0, None, 2, 1, ctypes.byref(alt), st, None, 0,
+                            None) == 1
+    assert L.ags_sort_tiles(None, None, None, None, npairs, 0, 4, 8, 0, None, 2, 17, ctypes.byref(alt), st, None, 0,
+                            None) == 1
+    assert L.ags_sort_tiles(None, None, None, None, npairs, 0, 30, 8, 0, None, 5, 17, ctypes.byref(alt), st, None,
+                            0, None) == 1
+    assert L.ags_view_keys(ctypes.c_void_p(16), npairs, 10, 0, ctypes.c_void_p(16), None) == 1
     # diagnostics: missing outputs or inputs, unknown ranking, rule 1 without weights, negative threshold
     cam1 = B.cameras([dict(width=64, height=48, fx=50.0, fy=50.0, cx=31.5, cy=23.5,
                            viewmat=[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], campos=[0, 0, 0])])
