@@ -92,11 +92,13 @@ class Renderer:
         self.tile_test = tile_test
         self.emit_flags = B.AGS_EMIT_ELLIPSE if tile_test == B.AGS_TILE_ELLIPSE else 0
         # view-major tile keys (view << tile_bits | tile, sorted by the tile bits
-        # alone): by default wherever they save a pair-sort pass
+        # alone): by default for batches of views wherever they add no pair-sort
+        # pass (narrower digits even at the same pass count: C2 sort 0.68 ->
+        # 0.61 ms for 0.05 ms more depth pre-sort)
         self.tile_bits = max(1, (self.T - 1).bit_length())
         if view_major is None:
             view_major = (self.V > 1 and digit_plan(self.tile_bits, digit_bits)[0]
-                          < digit_plan(tile_key_bits(self.V, self.T), digit_bits)[0])
+                          <= digit_plan(tile_key_bits(self.V, self.T), digit_bits)[0])
         self.view_major = bool(view_major) and presort and (self.V << self.tile_bits) <= (1 << 32)
         self.keep_state = keep_state or want_backward   # final_T / n_contrib for the backward
         self.set_params(scale_mode, K, lut, sh_degree, bg)
