@@ -297,6 +297,69 @@ class Renderer:
         return int(self.num_pairs.item())
 
 
+class HostPipeline:
+    """Frames from parameters in (pinned) host memory to images in host memory,
+    double-buffered.  A frame uploads its parameters on an upload stream,
+    renders them (a CUDA graph of the whole forward) on the caller's stream and
+    downloads its images on a download stream.  With two sets of device
+    buffers, the upload of the next frame and the download of the previous one
+    run while a frame renders.  Every frame still copies all of its inputs and
+    its whole result; nothing is kept from one frame to the next.  Takes the
+    Renderer's arguments and twice its device memory."""
+
+    def __init__(self, scene: dict, cams: list, *args, **kwargs):
+        self.renderers = [Renderer({k: v.clone() for k, v in scene.items()}, cams, *args, **kwargs)
+                          for _ in range(2)]
+        self.graphs = [r.capture() for r in self.renderers]
+        self.up, self.down = torch.cuda.Stream(), torch.cuda.Stream()
+        cur = torch.cuda.current_stream()
+        self.uploaded = [torch.cuda.Event() for _ in range(2)]
+        self.rendered = [torch.cuda.Event() for _ in range(2)]
+        self.downloaded = [torch.cuda.Event() for _ in range(2)]
+        for e in self.rendered + self.downloaded:     # both slots free
+            e.record(cur)
+        self.frames = 0
+
+    def submit(self, host_params: dict, host_image: torch.Tensor):
+        """Enqueue one frame: upload `host_params` (pinned, the scene's keys and
+        shapes), render, download into `host_image` (pinned, [views][3][H][W]).
+        Returns at once; the host buffers must stay untouched until wait()."""
+        slot = self.frames % 2
+        self.frames += 1
+        r = self.renderers[slot]
+        cur = torch.cuda.current_stream()
+        self.up.wait_event(self.rendered[slot])       # the slot's parameters are no longer read
+        with torch.cuda.stream(self.up):
+            for k, v in host_params.items():
+                r.scene[k].copy_(v, non_blocking=True)
+            self.uploaded[slot].record(self.up)
+        cur.wait_event(self.uploaded[slot])
+        cur.wait_event(self.downloaded[slot])         # the slot's previous images have left
+        self.graphs[slot].replay()
+        self.rendered[slot].record(cur)
+        self.down.wait_event(self.rendered[slot])
+        with torch.cuda.stream(self.down):
+            host_image.copy_(r.image, non_blocking=True)
+            self.downloaded[slot].record(self.down)
+
+    def begin(self):
+        """Order the frames submitted from now on after the work already queued
+        on the caller's stream (e.g. an event that starts a timed region)."""
+        cur = torch.cuda.current_stream()
+        self.up.wait_stream(cur)
+        self.down.wait_stream(cur)
+
+    def wait(self):
+        """Make the caller's stream wait for every submitted frame's download."""
+        cur = torch.cuda.current_stream()
+        for e in self.downloaded:
+            cur.wait_event(e)
+
+    def check(self):
+        for r in self.renderers:
+            r.check()
+
+
 class AgsRender(torch.autograd.Function):
     """image = render(params); backward through libags with the pair lists of the forward held fixed."""
 
