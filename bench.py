@@ -53,10 +53,10 @@ FALLBACK_HBM_GBS = 6800.0
 RASTER_OPS_PER_EVAL = 18
 # DRAM bytes (read + write) of one raster_kernel<false,false,false> launch per
 # view of this workload, from the ncu capture summarised in
-# profiles/raster_kernel_c2_clusters1m_1080p_6views.md ((108.18 + 108.41) MB over
+# profiles/raster_kernel_c2_clusters1m_1080p_6views.md ((104.19 + 107.42) MB over
 # 6 views; the kernel's traffic grows with the number of views it renders).  Set
 # to None whenever the kernel changes until it is captured again.
-RASTER_TRAFFIC_PER_VIEW = (108.179456e6 + 108.414976e6) / 6
+RASTER_TRAFFIC_PER_VIEW = (104.194048e6 + 107.41504e6) / 6
 
 
 def parse():
