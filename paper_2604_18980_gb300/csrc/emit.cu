@@ -10,7 +10,9 @@
 // are coalesced whatever the per-Gaussian tile counts are.
 //
 //   64-bit keys: key = ((view * tiles_per_view + tile) << 32) | float_bits(depth)
-//   32-bit keys: key = view * tiles_per_view + tile (pairs emitted in depth order)
+//   32-bit keys: key = view * tiles_per_view + tile (pairs emitted in depth order),
+//                or view << tile_bits | tile (AGS_EMIT_VIEW_SHIFT: the kernels
+//                take the power of two 2^tile_bits as their view stride)
 //   val = view * n + i
 //
 // The look-back spins are bounded (globaltimer); on expiry the status block

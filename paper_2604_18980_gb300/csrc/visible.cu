@@ -1,5 +1,7 @@
 // visible.cu -- stable compaction of the Gaussian-views that have pairs,
-// with their depth keys: the input of the depth pre-sort.
+// with their depth keys: the input of the depth pre-sort; and the view of each
+// entry of the sorted order (ags_view_keys), the key of the one stable pass
+// that groups the depth order view by view for view-major tile keys.
 //
 // A culled Gaussian-view (no pairs in its view, Sec. 2.1 frustum cull and
 // Sec. 3.3 Th > opacity cull) never reaches a tile list, so the depth
