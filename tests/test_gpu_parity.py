@@ -278,6 +278,57 @@ def test_sort_identity_values_flag():
     np.testing.assert_array_equal(vs, np.argsort(keys, kind="stable"))
 
 
+@pytest.mark.parametrize("count,views,tiles,digit,flags", [(1, 2, 5, 4, 0), (50000, 3, 130, 8, 2),
+                                                          (123457, 16, 45800, 8, 6), (70001, 10, 8160, 7, 6)])
+def test_sort_tiles_view_shifted_keys(count, views, tiles, digit, flags):
+    """ags_sort_tiles: stable by the tile bits alone, the view bits above them
+    untouched; ranges indexed by view * tiles + tile.  ags_view_keys: order // n."""
+    rng = np.random.default_rng(count + views)
+    tb = max(1, (tiles - 1).bit_length())
+    view = np.sort(rng.integers(0, views, count)).astype(np.uint64)   # emitted view by view
+    tile = rng.integers(0, tiles, count).astype(np.uint64)
+    tile[rng.random(count) < 0.3] = tile[0]
+    keys = ((view << np.uint64(tb)) | tile).astype(np.uint32)
+    vals = rng.permutation(count).astype(np.uint32)
+    cap = count + 5
+    k = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    k[:count] = torch.from_numpy(keys.view(np.int32))
+    v = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    v[:count] = torch.from_numpy(vals.view(np.int32))
+    ka, va = torch.zeros_like(k), torch.zeros_like(v)
+    n = torch.tensor([count], dtype=torch.int64, device="cuda")
+    st = torch.zeros(4, dtype=torch.int64, device="cuda")
+    ws = torch.empty(B.ags_sort_workspace_bytes(cap), dtype=torch.uint8, device="cuda")
+    rg = torch.full((views * tiles * 2,), -1, dtype=torch.int32, device="cuda")
+    alt = B.ags_sort_tiles(k, v, ka, va, n, cap, tb, digit, rg, views, tiles, st, ws, flags=flags)
+    B.ags_check(st)
+    order = np.argsort(tile, kind="stable")
+    got_v = (va if alt else v)[:count].cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(got_v, vals[order])
+    if not (flags & B.AGS_SORT_DISCARD_KEYS):
+        np.testing.assert_array_equal((ka if alt else k)[:count].cpu().numpy().view(np.uint32), keys[order])
+    ranges = rg.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    r_idx = (view * np.uint64(tiles) + tile)[order].astype(np.int64)
+    exp = np.zeros((views * tiles, 2), dtype=np.int64)
+    first = np.ones(count, dtype=bool)
+    first[1:] = r_idx[1:] != r_idx[:-1]
+    last = np.ones(count, dtype=bool)
+    last[:-1] = r_idx[1:] != r_idx[:-1]
+    pos = np.arange(count)
+    exp[r_idx[first], 0] = pos[first]
+    exp[r_idx[last], 1] = pos[last] + 1
+    np.testing.assert_array_equal(ranges, exp)
+    # the view of each entry of an order over views * n entries
+    nn = 1000
+    order_e = torch.from_numpy(rng.permutation(views * nn).astype(np.int32)).cuda()
+    vk = torch.full((views * nn,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([views * nn - 3], dtype=torch.int64, device="cuda")
+    B.ags_view_keys(order_e, cnt, views * nn, nn, vk)
+    got = vk.cpu().numpy()
+    np.testing.assert_array_equal(got[:views * nn - 3], order_e.cpu().numpy()[:views * nn - 3] // nn)
+    assert np.all(got[views * nn - 3:] == -1)
+
+
 @pytest.mark.parametrize("rank_or", [False, True])
 @pytest.mark.parametrize("count,bits,digit,flags", [(1, 12, 8, 0), (4095, 13, 8, 2), (4097, 17, 9, 0),
                                                     (100003, 17, 9, 2), (250000, 20, 7, 1), (77777, 16, 5, 3),
