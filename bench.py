@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="no timing: run one forward (with one view, also one forward + backward) inside a "
                          "profiler range for `ncu --profile-from-start off`, then exit")
+    ap.add_argument("--profile-leg", default="forward", choices=["forward", "ellipse", "peripheral"],
+                    help="with --profile: the benchmark forward, one forward with the ellipse tile test at its "
+                         "own K, or the peripheral scores of the plain render of the first view")
     return ap.parse_args()
 
 
@@ -284,7 +287,7 @@ def run_ours(args, world, rank, local):
     ada.stats = None      # the timed region runs without the counters
     barrier()
     if args.profile:
-        return profile_once(ada, sc, cams, wp, rank)
+        return profile_once(ada, sc, cams, wp, rank, args.profile_leg, knobs)
 
     # timed region: one CUDA-graph replay of the whole forward per step
     graph = ada.capture()
@@ -577,14 +580,38 @@ def run_ours(args, world, rank, local):
     return 0
 
 
-def profile_once(ada, sc, cams, wp, rank):
+def profile_once(ada, sc, cams, wp, rank, leg="forward", knobs=None):
     """One eager forward of the benchmark renderer -- and with one view one
     forward + backward of a gradient-enabled renderer -- between
     cudaProfilerStart and cudaProfilerStop (`ncu --profile-from-start off`
-    captures exactly these launches)."""
+    captures exactly these launches).  leg "ellipse": one forward with the
+    ellipse tile test instead; "peripheral": the peripheral scores of the
+    plain render of the first view."""
     import torch
     from paper_2604_18980_gb300 import binding as B
     from paper_2604_18980_gb300 import render as R
+    if leg != "forward":
+        from paper_2604_18980_gb300 import diagnostics as D
+        if leg == "ellipse":
+            run = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp.get("K_ellipse", wp["K"]), wp["lut"], keep_state=False,
+                             tile_test=B.AGS_TILE_ELLIPSE, **dict(knobs or {}, emit_two_pass=True))
+            run.forward()
+            step = run.forward
+        else:
+            run = R.Renderer(sc, cams[:1], B.AGS_SCALE_PLAIN, keep_state=False, **(knobs or {}))
+            run.forward()
+            dg = D.Diagnostics(run, wp["K"], wp["lut"])
+            dg.scores()
+            step = dg.scores
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        run.check()
+        if rank == 0:
+            print(json.dumps({"profile": leg}))
+        return 0
     fb = grads = None
     if len(cams) == 1:
         fb = R.Renderer(sc, cams[:1], B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_backward=True)
