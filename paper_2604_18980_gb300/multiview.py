@@ -20,10 +20,24 @@ def shard_views(cams: list, rank: int, world: int) -> list:
 
 
 def sum_gradients(grads: dict, group=None) -> dict:
-    """All-reduce (sum) every gradient tensor across the process group, in place."""
+    """All-reduce (sum) every gradient tensor across the process group, in place.
+
+    The tensors of one dtype and device travel in a single flat buffer (one
+    collective of 236 B per Gaussian rather than one per attribute)."""
+    import torch
     import torch.distributed as dist
     if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
         return grads
-    for k in sorted(grads):
-        dist.all_reduce(grads[k], op=dist.ReduceOp.SUM, group=group)
+    keys = sorted(grads)
+    groups = {}
+    for k in keys:
+        groups.setdefault((grads[k].dtype, grads[k].device), []).append(k)
+    for ks in groups.values():
+        flat = torch.cat([grads[k].reshape(-1) for k in ks])
+        dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+        off = 0
+        for k in ks:
+            n = grads[k].numel()
+            grads[k].copy_(flat[off:off + n].view_as(grads[k]))
+            off += n
     return grads
