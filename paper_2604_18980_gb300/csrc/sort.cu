@@ -454,7 +454,8 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
   uint32_t* counters = reinterpret_cast<uint32_t*>(w);
   uint32_t* ghist = reinterpret_cast<uint32_t*>(w + kSortHdr);
   uint32_t* lookback = reinterpret_cast<uint32_t*>(w + kSortHdr + kSortHistBytes);
-  const int radix = digit_bits > 8 ? 512 : 256;
+  // the smallest digit table that holds the digit (at least 64 entries)
+  const int radix = digit_bits > 8 ? 512 : digit_bits > 7 ? 256 : digit_bits > 6 ? 128 : 64;
   cudaError_t e = cudaSuccess;
   K* kin = keys;
   uint32_t* vin = vals;
@@ -472,12 +473,12 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
       if (e == cudaSuccess) e = cudaMemset2DAsync(ranges + 1, 8, 0, 4, (size_t)num_ranges, st);
       if (e != cudaSuccess) return AGS_ERR_CUDA;
     }
-    e = radix == 512 ? launch_passes<512, K>(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
-                                             digit_bits, passes, flags, ghist, lookback, counters, d_status, ranges,
-                                             num_ranges, rmap, st)
-                     : launch_passes<256, K>(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit,
-                                             digit_bits, passes, flags, ghist, lookback, counters, d_status, ranges,
-                                             num_ranges, rmap, st);
+    auto launch = radix == 512   ? launch_passes<512, K>
+                  : radix == 256 ? launch_passes<256, K>
+                  : radix == 128 ? launch_passes<128, K>
+                                 : launch_passes<64, K>;
+    e = launch(kin, vin, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit, digit_bits, passes, flags,
+               ghist, lookback, counters, d_status, ranges, num_ranges, rmap, st);
     if (e != cudaSuccess) return AGS_ERR_CUDA;
   }
   if (ranges) {
