@@ -537,7 +537,7 @@ def run_ours(args, world, rank, local):
         b.record(stream)
         barrier()
         fb.check()
-        eager_ms = max_over_ranks(a.elapsed_time(b)) / args.steps
+        fb_eager_ms = max_over_ranks(a.elapsed_time(b)) / args.steps
         # the same step captured in a CUDA graph, as the forward is timed
         g_fb = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
@@ -557,7 +557,7 @@ def run_ours(args, world, rank, local):
         barrier()
         fb.check()
         extras["fwd_bwd_ms"] = max_over_ranks(a.elapsed_time(b)) / args.steps
-        extras["fwd_bwd_ms_eager"] = eager_ms
+        extras["fwd_bwd_ms_eager"] = fb_eager_ms
         del fb, grads, target, g_fb
 
     if rank != 0:
