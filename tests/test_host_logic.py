@@ -29,18 +29,11 @@ def test_digit_plan_covers_the_bits(bits, max_digit):
     assert passes == max(1, -(-bits // max_digit))    # the fewest passes
 
 
-def _view_major_rule(V, T, digit_bits):
-    """The default of Renderer: view-major keys for batches of views wherever
-    they add no pair-sort pass."""
-    tb = max(1, (T - 1).bit_length())
-    return V > 1 and R.digit_plan(tb, digit_bits)[0] <= R.digit_plan(R.tile_key_bits(V, T), digit_bits)[0]
-
-
 def test_view_major_rule_on_the_workloads():
-    assert _view_major_rule(10, 8160, 9)              # C2: two 7/6-bit passes instead of 9/8
-    assert _view_major_rule(8, 62208, 8)              # C3: two passes instead of three
-    assert _view_major_rule(16, 45800, 9)             # C4: two passes instead of three
-    assert not _view_major_rule(1, 256, 8)            # a single view has nothing to regroup
+    assert R.view_major_default(10, 8160, 9)              # C2: two 7/6-bit passes instead of 9/8
+    assert R.view_major_default(8, 62208, 8)              # C3: two passes instead of three
+    assert R.view_major_default(16, 45800, 9)             # C4: two passes instead of three
+    assert not R.view_major_default(1, 256, 8)            # a single view has nothing to regroup
     for V in range(2, 33):
         for T in (1, 2, 17, 256, 8160, 45800, 62208):
             tb = max(1, (T - 1).bit_length())
