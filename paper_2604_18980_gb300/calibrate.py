@@ -102,15 +102,27 @@ def search_K(scene: dict, calib_cams: list, lut, target_psnr: float, sh_degree: 
 
 
 def calibrate_workload(name: str, device="cuda") -> dict:
+    """LUT, K and the ellipse test's K of a named workload, with the wall-clock
+    seconds each took on this GPU (the scene already on the device)."""
+    import time
     scene, cams, calib = synth.workload(name)
     sc = R.scene_to_device(scene, device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     lut = calibrate_lut(sc, calib)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     target = TARGET_PSNR[name[:2]]
     K, p = search_K(sc, calib, lut, target)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     # the ellipse tile test drops more of each footprint: its own K for the same target
     Ke, pe = search_K(sc, calib, lut, target, tile_test=B.AGS_TILE_ELLIPSE)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
     return dict(K=float(np.float32(K)), lut=[float(x) for x in lut], target_psnr=target, calib_psnr=p,
-                calibration_views=len(calib), K_ellipse=float(np.float32(Ke)), calib_psnr_ellipse=pe)
+                calibration_views=len(calib), K_ellipse=float(np.float32(Ke)), calib_psnr_ellipse=pe,
+                seconds=dict(lut=round(t1 - t0, 3), K_search=round(t2 - t1, 3), K_search_ellipse=round(t3 - t2, 3)))
 
 
 def load_params(name: str) -> dict | None:
