@@ -1,21 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the AdaGScale 3D-GS rendering hot path on GB300.
 
-Workload (seeded, synthetic, resident in HBM): 1,048,576 Gaussians drawn from
-64 surface-like clusters, rendered at 1920x1080 from 10 fixed orbit poses, all
-10 views in one launch per stage.  A step is one pass of the whole forward
+Default workload (seeded, synthetic, resident in HBM): the batched stereo VR
+configuration -- 4,194,304 Gaussians of the city-scale distribution rendered
+into 8 eye pairs (16 views of 3660x3200, the VR display of Sec. 1) along a
+street-level camera path, all 16 views in one launch per stage, the whole
+forward replayed as one CUDA graph.  A step is one pass of the whole forward
 path (preprocess with the AdaGScale threshold, pair emission, key sort, tile
-ranges, blending) over the 10-view batch; `value` is frames per second in
-AdaGScale mode at the calibrated K (Sec. 3.4).  Reported beside it: plain
+ranges, blending) over the 16-view batch; `value` is frames (views) per second
+in AdaGScale mode at the calibrated K (Sec. 3.4).  Reported beside it: plain
 3-sigma FPS on the same GPU, pairs per frame in both modes, PSNR of AdaGScale
-against plain, forward+backward ms (pose 0, L2 loss, pair selection fixed),
+against plain, forward+backward ms (view 0, L2 loss, pair selection fixed),
 per-stage times, the roofline of the dominant kernel, an end-to-end number
-through host buffers, and the CPU oracle as a baseline.
+through host buffers, and the CPU oracle as a baseline.  `--workload` selects
+another configuration (c1 .. c3: the single-frame and 10-/8-pose batches).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 With N > 1 it runs under torchrun, one rank per GPU, each rank rendering its
-own copy of the 10-view batch (weak scaling; no collective on the data path).
+own copy of the batch (weak scaling; no collective on the data path).
 """
 from __future__ import annotations
 
@@ -32,15 +35,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "c2_clusters1m_1080p"
-METRIC = "FPS (AdaGScale, 1M Gaussians, 1920x1080, 10 poses)"
+WORKLOAD = "c4_city4m_vr16x3660x3200"
 # K values of the sweep reported beside the calibrated K (plus K itself)
 K_SWEEP = (0.0, 0.1, 0.3, 1.0, 3.0, 10.0)
 
 
 def metric_for(workload: str, n: int, W: int, H: int, V: int) -> str:
-    if workload == WORKLOAD:
-        return METRIC
     return "FPS (AdaGScale, %s Gaussians, %dx%d, %d views)" % (
         ("%dM" % (n >> 20)) if n >= 1 << 20 else ("%dK" % (n >> 10)), W, H, V)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -51,12 +51,13 @@ FALLBACK_HBM_GBS = 6800.0
 # 1 - alpha and the transmittance product (2); the three colour FMAs and
 # alpha*T (4) = 18.  The exponential itself runs on the SFU.
 RASTER_OPS_PER_EVAL = 18
-# DRAM bytes (read + write) of one raster_kernel<false,false,false> launch per
-# view of this workload, from the ncu capture summarised in
-# profiles/raster_kernel_c2_clusters1m_1080p_6views.md ((104.19 + 107.42) MB over
-# 6 views; the kernel's traffic grows with the number of views it renders).  Set
-# to None whenever the kernel changes until it is captured again.
-RASTER_TRAFFIC_PER_VIEW = (104.194048e6 + 107.41504e6) / 6
+# DRAM bytes (read + write) per view of one raster_kernel<false,false,false>
+# launch, by workload, from ncu captures of that kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of a multi-view launch divided by its views; the
+# kernel's traffic grows with the number of views it renders).  A workload
+# missing here, or any entry after the kernel changed and before it was
+# captured again, reports traffic null.
+RASTER_TRAFFIC_PER_VIEW = {}
 
 
 def parse():
@@ -568,7 +569,7 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant stage
     pk, pk_src = peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    roof = roofline(dom, stage_ms[dom], ada, evals_per_step, pk, pk_src, passes, clk)
+    roof = roofline(dom, stage_ms[dom], ada, evals_per_step, pk, pk_src, passes, clk, workload)
     line = {
         "metric": metric_for(workload, ada.n, ada.W, ada.H, V), "value": fps, "unit": "FPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -690,7 +691,7 @@ def stage_bytes(stage, r, passes):
     return n * 44 + any_live * 192 + live * 69 + (G - live) * 17, "preprocess_kernel"
 
 
-def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):
+def roofline(stage, ms, r, evals, pk, pk_src, passes, clk, workload=WORKLOAD):
     V, n = r.V, r.n
     P = r.pairs()
     if stage == "raster":
@@ -699,10 +700,12 @@ def roofline(stage, ms, r, evals, pk, pk_src, passes, clk):
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12           # FP32 lanes x clock, Tops/s
         achieved = evals * RASTER_OPS_PER_EVAL / (ms / 1e3) / 1e12
-        traffic = None if RASTER_TRAFFIC_PER_VIEW is None else RASTER_TRAFFIC_PER_VIEW * V
+        tpv = RASTER_TRAFFIC_PER_VIEW.get(workload)
+        traffic = None if tpv is None else tpv * V
         return {"kernel": "raster_kernel", "bound": "alu", "achieved": achieved, "peak": peak_ops,
                 "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read+write of a 6-view capture / 6 x views",
+                "traffic_source": "ncu dram__bytes_read+write per view x views" if traffic else
+                                  "not captured for this kernel build and workload",
                 "work": "%d pixel-pair evaluations x %d FP32 ops" % (evals, RASTER_OPS_PER_EVAL),
                 "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (%s)" % (sms, sm_mhz, pk_src)}
     hbm = pk.get("hbm_gbs", FALLBACK_HBM_GBS)

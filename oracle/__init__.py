@@ -38,10 +38,11 @@ _LIB = os.path.join(_HERE, "_build", "libags_oracle.so")
  F_COVA, F_COVB, F_COVC, F_DEPTH32, F_RARG, F_QELL) = range(19)
 NF = 19
 # per-Gaussian integer fields
-I_RADIUS, I_X0, I_Y0, I_X1, I_Y1, I_TOUCHED, I_CULL, I_EDGE, I_CLAMP = range(9)
-NI = 9
+I_RADIUS, I_X0, I_Y0, I_X1, I_Y1, I_TOUCHED, I_CULL, I_EDGE, I_CLAMP, I_GEDGE = range(10)
+NI = 10
 CULL_NONE, CULL_NEAR, CULL_DET, CULL_TH, CULL_TUP, CULL_NONFINITE, CULL_EMPTY = range(7)
 EDGE_NEAR, EDGE_DET, EDGE_TH, EDGE_CEIL, EDGE_RECT, EDGE_LUT, EDGE_ELLIPSE = 1, 2, 4, 8, 16, 32, 64
+GEDGE_FRUSTUM, GEDGE_COLOUR = 1, 2   # decisions that change only the derivatives
 TILE_SQUARE, TILE_ELLIPSE = 0, 1     # tile test: square footprint, or square and ellipse
 TILE = 16
 
@@ -158,7 +159,7 @@ class Oracle:
                                          ctypes.c_int, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]
         L.oracle_render_skip.restype = None
         L.oracle_backward.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P,
-                                      _P, _P, _P, _P, _P, _P]
+                                      _P, _P, _P, _P, _P, _P, _P, _P]
         L.oracle_backward.restype = None
         L.oracle_sh_basis.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]
         L.oracle_sh_basis.restype = None
@@ -224,19 +225,36 @@ class Oracle:
         return img
 
     def backward(self, scene: dict, cam: dict, par: OcParams, tile_start, ids, dL_dimage) -> dict:
-        """Gradients of sum(dL_dimage * image) w.r.t. the raw parameters, lists frozen."""
+        """Gradients of sum(dL_dimage * image) w.r.t. the raw parameters, lists frozen.
+
+        Also `edge` [n]: per Gaussian, the number of pixel decisions (alpha vs
+        tau, alpha vs its clamp, p vs 0, the transmittance stop) within their
+        edge band; with the gradient-only bits of the preprocess record
+        (frustum and colour clamps, I_GEDGE) these mark the Gaussians whose
+        derivative can jump under a one-rounding change of the inputs.
+        And `budget`: per raw gradient entry (the gradients' shapes), a bound
+        on what a near-threshold decision of another Gaussian at a shared
+        pixel can change in it (that decision's T and colour-behind
+        perturbation, chained through the absolute derivatives)."""
         mean, ls, q = _d(scene["mean"]), _d(scene["log_scale"]), _d(scene["quat"])
         lg, sh = _d(scene["opacity_logit"]), _d(scene["sh"])
         n = lg.shape[0]
         nc = (par.sh_degree + 1) ** 2
         g = dict(mean=np.zeros((3, n)), log_scale=np.zeros((3, n)), quat=np.zeros((4, n)),
-                 opacity_logit=np.zeros(n), sh=np.zeros((nc, 3, n)), feat=np.zeros((n, 9)))
+                 opacity_logit=np.zeros(n), sh=np.zeros((nc, 3, n)), feat=np.zeros((n, 9)), edge=np.zeros(max(n, 1)))
         c = camera(cam)
+        bud = np.zeros((max(n, 1), 11 + 48))
         ids = np.ascontiguousarray(ids, dtype=np.int32) if len(ids) else np.zeros(1, dtype=np.int32)
         self.L.oracle_backward(_ptr(mean), _ptr(ls), _ptr(q), _ptr(lg), _ptr(sh), n, ctypes.byref(c),
                                ctypes.byref(par), _ptr(np.ascontiguousarray(tile_start, dtype=np.int64)),
                                _ptr(ids), _ptr(_d(dL_dimage)), _ptr(g["mean"]), _ptr(g["log_scale"]),
-                               _ptr(g["quat"]), _ptr(g["opacity_logit"]), _ptr(g["sh"]), _ptr(g["feat"]))
+                               _ptr(g["quat"]), _ptr(g["opacity_logit"]), _ptr(g["sh"]), _ptr(g["feat"]),
+                               _ptr(g["edge"]), _ptr(bud))
+        g["edge"] = g["edge"][:n]
+        nj = 11
+        g["budget"] = dict(mean=np.ascontiguousarray(bud[:n, 0:3].T), log_scale=np.ascontiguousarray(bud[:n, 3:6].T),
+                           quat=np.ascontiguousarray(bud[:n, 6:10].T), opacity_logit=bud[:n, 10].copy(),
+                           sh=np.ascontiguousarray(bud[:n, nj:nj + 3 * nc].reshape(n, nc, 3).transpose(1, 2, 0)))
         return g
 
     def sh_basis(self, degree: int, dirs: np.ndarray) -> np.ndarray:

@@ -76,7 +76,9 @@ enum {
   OC_NF
 };
 /* Per-Gaussian integer outputs. */
-enum { I_RADIUS = 0, I_X0, I_Y0, I_X1, I_Y1, I_TOUCHED, I_CULL, I_EDGE, I_CLAMP, OC_NI };
+enum { I_RADIUS = 0, I_X0, I_Y0, I_X1, I_Y1, I_TOUCHED, I_CULL, I_EDGE, I_CLAMP,
+       I_GEDGE,   /* decisions that change only the derivatives (bits below) */
+       OC_NI };
 
 /* cull reasons */
 #define CULL_NONE 0
@@ -95,6 +97,11 @@ enum { I_RADIUS = 0, I_X0, I_Y0, I_X1, I_Y1, I_TOUCHED, I_CULL, I_EDGE, I_CLAMP,
 #define EDGE_RECT 16
 #define EDGE_LUT 32
 #define EDGE_ELLIPSE 64
+
+/* gradient-only edge bits (I_GEDGE): the image is continuous across these
+ * decisions, its derivative is not */
+#define GEDGE_FRUSTUM 1   /* x/z or y/z within eps of the 1.3 tan(fov/2) clamp */
+#define GEDGE_COLOUR 2    /* a colour channel within eps of the clamp at 0 */
 
 /* ------------------------------------------------------------------------ */
 /* Jets: value plus NJ partial derivatives.                                   */
@@ -275,18 +282,16 @@ static int preprocess_one(const double* mean, const double* log_scale, const dou
   jet m[3];
   for (int k = 0; k < 3; k++) m[k] = jvar(mean[k * n + i], k);
 
-  /* view-space position t = R m + t_cam */
+  /* view-space position t = R m + t_cam.  The edge classes take t as the
+   * fp32 inputs give it exactly (a correctly rounded fp32 evaluation is within
+   * one rounding of it), so each band is eps relative to the magnitudes of the
+   * compared quantities themselves. */
   jet t[3];
-  double tabs[3];
   for (int r = 0; r < 3; r++) {
     t[r] = jc(cam->t[r]);
-    tabs[r] = fabs(cam->t[r]);
-    for (int k = 0; k < 3; k++) {
-      t[r] = jadd(t[r], jscale(m[k], cam->R[r * 3 + k]));
-      tabs[r] += fabs(cam->R[r * 3 + k] * m[k].v);
-    }
+    for (int k = 0; k < 3; k++) t[r] = jadd(t[r], jscale(m[k], cam->R[r * 3 + k]));
   }
-  if (near_edge(t[2].v, cam->near_z, eps, fmax(tabs[2], cam->near_z))) edge |= EDGE_NEAR;
+  if (near_edge(t[2].v, cam->near_z, eps, fmax(fabs(t[2].v), cam->near_z))) edge |= EDGE_NEAR;
   irec[I_EDGE] = edge;
   dbl[F_DEPTH] = t[2].v;
   dbl[F_DEPTH32] = (double)(float)t[2].v;
@@ -323,6 +328,8 @@ static int preprocess_one(const double* mean, const double* log_scale, const dou
   jet txtz = jdiv(t[0], t[2]), tytz = jdiv(t[1], t[2]);
   jet tx = t[0], ty = t[1];
   int fclamp = 0;
+  if (near_edge(fabs(txtz.v), limx, eps, limx) || near_edge(fabs(tytz.v), limy, eps, limy))
+    irec[I_GEDGE] |= GEDGE_FRUSTUM;
   if (txtz.v > limx) { tx = jscale(t[2], limx); fclamp |= 8; }
   else if (txtz.v < -limx) { tx = jscale(t[2], -limx); fclamp |= 8; }
   if (tytz.v > limy) { ty = jscale(t[2], limy); fclamp |= 16; }
@@ -363,8 +370,8 @@ static int preprocess_one(const double* mean, const double* log_scale, const dou
   /* 2D mean (unclamped projection), depth */
   jet u = jaddc(jscale(jmul(t[0], iz), cam->fx), cam->cx);
   jet v = jaddc(jscale(jmul(t[1], iz), cam->fy), cam->cy);
-  double uscale = fabs(cam->fx * t[0].v / t[2].v) + fabs(cam->cx) + cam->fx * tabs[0] / t[2].v;
-  double vscale = fabs(cam->fy * t[1].v / t[2].v) + fabs(cam->cy) + cam->fy * tabs[1] / t[2].v;
+  double uscale = fabs(cam->fx * t[0].v / t[2].v) + fabs(cam->cx);
+  double vscale = fabs(cam->fy * t[1].v / t[2].v) + fabs(cam->cy);
 
   /* opacity */
   jet opac = jdiv(jc(1.0), jaddc(jexp(jscale(jvar(logit[i], 10), -1.0)), 1.0));
@@ -378,7 +385,12 @@ static int preprocess_one(const double* mean, const double* log_scale, const dou
   int clampbits = fclamp;
   for (int c = 0; c < 3; c++) {
     jet acc = jc(0.5);
-    for (int k = 0; k < nc; k++) acc = jadd(acc, jscale(Y[k], sh[(k * 3 + c) * n + i]));
+    double mag = 0.5;
+    for (int k = 0; k < nc; k++) {
+      acc = jadd(acc, jscale(Y[k], sh[(k * 3 + c) * n + i]));
+      mag += fabs(Y[k].v * sh[(k * 3 + c) * n + i]);
+    }
+    if (fabs(acc.v) <= eps * mag) irec[I_GEDGE] |= GEDGE_COLOUR;
     if (acc.v < 0.0) { acc = jc(0.0); clampbits |= 1 << c; }
     rgb[c] = acc;
   }
@@ -816,15 +828,21 @@ void oracle_backward(const double* mean, const double* log_scale, const double* 
                      const double* sh, int64_t n, const oc_camera* cam, const oc_params* par,
                      const int64_t* tile_start, const int32_t* ids, const double* dL_dimage,
                      double* g_mean, double* g_log_scale, double* g_quat, double* g_logit,
-                     double* g_sh, double* g_feat /* [n][9] nullable: u v A B C opac r g b */) {
+                     double* g_sh, double* g_feat /* [n][9] nullable: u v A B C opac r g b */,
+                     double* g_edge /* [n] nullable: near-threshold pixel decisions per Gaussian */,
+                     double* g_budget /* [n][NJ + 48] nullable: flip budget of each raw gradient */) {
   int nc = (par->sh_degree + 1) * (par->sh_degree + 1);
   double* dbl = (double*)malloc(sizeof(double) * OC_NF * (n > 0 ? n : 1));
   int32_t* irec = (int32_t*)malloc(sizeof(int32_t) * OC_NI * (n > 0 ? n : 1));
   gjet* gj = (gjet*)malloc(sizeof(gjet) * (n > 0 ? n : 1));
   double* G = (double*)calloc((size_t)(9 * (n > 0 ? n : 1)), sizeof(double));
+  /* flip budget per feature: what a near-threshold decision of another entry
+   * at a shared pixel can change in this Gaussian's terms there */
+  double* Gb = g_budget ? (double*)calloc((size_t)(9 * (n > 0 ? n : 1)), sizeof(double)) : NULL;
 #pragma omp parallel for schedule(dynamic, 256)
   for (int64_t i = 0; i < n; i++)
     preprocess_one(mean, log_scale, quat, logit, sh, n, i, cam, par, dbl + i * OC_NF, irec + i * OC_NI, gj + i);
+  double cmax = color_max(n, dbl, par);
 
   int width = cam->width, height = cam->height;
   int gx = (width + OC_TILE - 1) / OC_TILE, gy = (height + OC_TILE - 1) / OC_TILE;
@@ -848,14 +866,54 @@ void oracle_backward(const double* mean, const double* log_scale, const double* 
         /* forward: collect the blended entries and their transmittance */
         double T = 1.0;
         int64_t m = 0;
+        /* entries with a near-threshold decision that can change the other
+         * entries' terms: position (blended entries before it), whether it is
+         * blended, the weight of its change to the colour behind the entries
+         * in front of it (alpha T, or T for the stop), and the relative change
+         * of the transmittance of the entries behind it (a / (1 - a)) */
+        enum { MAXF = 16 };
+        int64_t fpos[MAXF];
+        int fbl[MAXF];
+        double fw[MAXF], frho[MAXF];
+        int nflip = 0, foverflow = 0;
         for (int64_t k = 0; k < len; k++) {
           const double* f = dbl + (int64_t)list[k] * OC_NF;
           double dx = f[F_U] - x, dy = f[F_V] - y;
           double p = -0.5 * (f[F_A] * dx * dx + f[F_C] * dy * dy) - f[F_B] * dx * dy;
-          if (p > 0.0) continue;
           double e = exp(p);
           double araw = f[F_OPAC] * e;
           double a = fmin(par->alpha_max, araw);
+          if (g_edge || Gb) {
+            /* decisions within their edge band at this pixel: alpha vs tau (the
+             * image's band), alpha vs its clamp, p vs 0, and the stop test
+             * (T carries one rounding per blend before it) */
+            double gl = fabs(f[F_A] * dx + f[F_B] * dy) + fabs(f[F_B] * dx + f[F_C] * dy);
+            double tol = par->edge_rel + par->pos_err * gl;
+            /* inclusion decisions (alpha vs tau, p vs 0) add or drop the entry;
+             * the clamp decision changes only its own derivative */
+            int incl = (araw > 0.0 && fabs(log(araw / par->tau)) <= tol) || fabs(p) <= par->edge_rel;
+            int clampd = araw > 0.0 && fabs(log(araw / par->alpha_max)) <= tol;
+            int stopd = 0;
+            if (!incl && p <= 0.0 && a >= par->tau) {
+              double tt = T * (1.0 - a);
+              stopd = fabs(log(tt / par->t_min)) <= par->edge_rel + (double)(m + 1) * 1.2e-7 + tol;
+            }
+            if (incl || clampd || stopd) {
+              if (g_edge) atomic_add_double(&g_edge[list[k]], 1.0);
+              if (incl || stopd) {
+                if (nflip < MAXF) {
+                  fpos[nflip] = m;
+                  fbl[nflip] = p <= 0.0 && a >= par->tau && T * (1.0 - a) >= par->t_min;
+                  fw[nflip] = stopd ? T : a * T;
+                  frho[nflip] = stopd ? 0.0 : a / (1.0 - a);
+                  nflip++;
+                } else {
+                  foverflow = 1;
+                }
+              }
+            }
+          }
+          if (p > 0.0) continue;
           if (a < par->tau) continue;
           double test_T = T * (1.0 - a);
           if (test_T < par->t_min) break;
@@ -873,6 +931,33 @@ void oracle_backward(const double* mean, const double* log_scale, const double* 
           for (int ch = 0; ch < 3; ch++) {
             dLda += g[ch] * Ti[j] * (c[ch] - R[ch]);
             atomic_add_double(&G[who[j] * 9 + 6 + ch], g[ch] * al[j] * Ti[j]);
+          }
+          if (Gb && (nflip > 0 || foverflow)) {
+            /* a flipping entry f in front of this one changes T before it by
+             * the factor (1 - a_f)^(-+1) (relatively by rho); one behind it
+             * changes the colour behind it by at most 2 c_max w_f / T_(j+1)
+             * (w_f <= T_(j+1): f lies behind) */
+            double rho = 0.0, dR = 0.0;
+            double Tn = Ti[j] * (1.0 - al[j]);
+            for (int q = 0; q < nflip; q++) {
+              if (fbl[q] ? fpos[q] < j : fpos[q] <= j) rho += frho[q];
+              else if (fpos[q] > j) dR += 2.0 * cmax * fw[q] / Tn;
+            }
+            if (foverflow) { rho += 1.0; dR += 2.0 * cmax; }   /* too many to track: a coarse bound */
+            double bda = 0.0;
+            for (int ch = 0; ch < 3; ch++) {
+              bda += fabs(g[ch]) * Ti[j] * (rho * fabs(c[ch] - R[ch]) + dR);
+              atomic_add_double(&Gb[who[j] * 9 + 6 + ch], fabs(g[ch]) * al[j] * Ti[j] * rho);
+            }
+            if (!clampa[j]) {
+              double dx = dxs[j], dy = dys[j];
+              atomic_add_double(&Gb[who[j] * 9 + 5], bda * ep[j]);
+              atomic_add_double(&Gb[who[j] * 9 + 0], bda * al[j] * fabs(f[F_A] * dx + f[F_B] * dy));
+              atomic_add_double(&Gb[who[j] * 9 + 1], bda * al[j] * fabs(f[F_C] * dy + f[F_B] * dx));
+              atomic_add_double(&Gb[who[j] * 9 + 2], bda * al[j] * 0.5 * dx * dx);
+              atomic_add_double(&Gb[who[j] * 9 + 3], bda * al[j] * fabs(dx * dy));
+              atomic_add_double(&Gb[who[j] * 9 + 4], bda * al[j] * 0.5 * dy * dy);
+            }
           }
           for (int ch = 0; ch < 3; ch++) R[ch] = c[ch] * al[j] + (1.0 - al[j]) * R[ch];
           if (clampa[j]) continue;   /* alpha = alpha_max: no dependence on opacity or power */
@@ -909,8 +994,21 @@ void oracle_backward(const double* mean, const double* log_scale, const double* 
     for (int k = 0; k < nc; k++)
       for (int ch = 0; ch < 3; ch++)
         g_sh[(k * 3 + ch) * n + i] = (live && !gj[i].clamp[ch]) ? Gi[6 + ch] * gj[i].Y[k].v : 0.0;
+    if (Gb) {   /* the feature budgets through the absolute derivatives */
+      double* bo = g_budget + i * (NJ + 48);
+      const double* Bi = Gb + i * 9;
+      memset(bo, 0, sizeof(double) * (NJ + 48));
+      if (live) {
+        const gjet* q = gj + i;
+        const jet* fj[9] = {&q->u, &q->v, &q->A, &q->B, &q->C, &q->opac, &q->rgb[0], &q->rgb[1], &q->rgb[2]};
+        for (int f = 0; f < 9; f++)
+          for (int k = 0; k < NJ; k++) bo[k] += Bi[f] * fabs(fj[f]->d[k]);
+        for (int k = 0; k < nc; k++)
+          for (int ch = 0; ch < 3; ch++) bo[NJ + k * 3 + ch] = gj[i].clamp[ch] ? 0.0 : Bi[6 + ch] * fabs(gj[i].Y[k].v);
+      }
+    }
   }
-  free(dbl); free(irec); free(gj); free(G);
+  free(dbl); free(irec); free(gj); free(G); free(Gb);
 }
 
 int oracle_num_threads(void) {

@@ -766,8 +766,340 @@ def pin_skip_render(orc):
         assert 0 < out["skipped"] < out["blends"]
 
 
+
+# --------------------------------------------------------------------------
+# Edge classes: every discrete decision of the preprocess and the blend is
+# flagged when its decision variable lies within the documented band of its
+# threshold, and only then.  Each pin places one Gaussian (or pixel) at a
+# chosen distance from one threshold -- half the band (flag expected) and
+# twice the band (no flag) on both sides -- with the position computed from
+# the closed forms of an on-axis Gaussian, independently of the oracle.
+# The bands (relative width eps = 1e-5, the oracle's default edge_rel):
+#   near plane  |t_z - near| <= eps * max(t_z, near)
+#   det guard   det <= eps * (|a c| + b^2) of the dilated 2D covariance
+#   Th vs sigma |Th - sigma| <= eps * max(Th, sigma)
+#   radius ceil the ceil changes when lambda_max moves by +-eps relative
+#   rectangle   a tile index changes when u (v) moves by +-eps * (|fx tx/tz| +
+#               |cx|) (the view-space mean taken exactly: no term for the
+#               magnitudes that cancel in R m + t_cam)
+#   LUT bin     |depth/width - edge| <= eps * max(depth/width, 1) at an inner
+#               bin edge (the last bin is open-ended: no decision)
+#   ellipse     |min q over the tile - Q| <= eps max(Q, 1) + 2 pos_err
+#               sqrt((A + C) max(Q, m)) + 2e-6 S (S: the size of q's terms
+#               over the row's part of the square)
+#   pixel alpha |ln(alpha / tau)| <= eps + pos_err |grad ln alpha|, and
+#               |p| <= eps; each adds 2 tau T c_max (2 sigma T c_max) to the
+#               pixel's flip budget
+# --------------------------------------------------------------------------
+EPS = 1e-5
+NEAR32 = float(np.float32(0.2))          # the camera's near plane as the GPU receives it
+
+
+def _edge_bits(orc, sc, cam, **pkw):
+    dbl, irec = orc.preprocess(sc, cam, oracle.params(cam, **pkw))
+    return dbl[0], irec[0]
+
+
+def _iso_scale(lam, f, d):
+    """World scale of an isotropic Gaussian at depth d on the optical axis whose
+    dilated 2D covariance is lam * I: lam = (f s / d)^2 + 0.3."""
+    return d * math.sqrt(lam - 0.3) / f
+
+
+def pin_edge_near_plane(orc):
+    for ctrans in (0.0, 5.0):            # camera at the origin, and 5 units behind it
+        cam = axis_camera(64, 64, 60.0, campos=(0.0, 0.0, -ctrans))
+        for sgn in (1.0, -1.0):
+            for k, want in ((0.5, True), (2.0, False)):
+                tz = NEAR32 * (1.0 + sgn * k * EPS)   # the band's scale is max(t_z, near)
+                sc = one_gaussian((0.0, 0.0, tz - ctrans), (0.01, 0.01, 0.01))
+                _, ir = _edge_bits(orc, sc, cam)
+                got = bool(ir[oracle.I_EDGE] & oracle.EDGE_NEAR)
+                assert got == want, ("near", ctrans, sgn, k, got)
+                assert (ir[oracle.I_CULL] == oracle.CULL_NEAR) == (sgn < 0), ("near cull", ctrans, sgn, k)
+
+
+def pin_edge_det_guard(orc):
+    """A needle at 45 degrees on the optical axis: Sigma2D = k R diag(s1^2, s2^2) R^T
+    + 0.3 I with k = (f/d)^2, so det = (k s1^2 + 0.3)(k s2^2 + 0.3) and
+    a c + b^2 = ((a' + b')/2 + 0.3)^2 + ((a' - b')/2)^2 with a' = k s1^2, b' = k s2^2."""
+    f, d, s2 = 80.0, 2.0, 1e-7
+    kk = (f / d) ** 2
+    cam = axis_camera(65, 65, f)
+    qz = (math.cos(math.pi / 8), 0.0, 0.0, math.sin(math.pi / 8))
+
+    def ratio(s1):
+        a, b = kk * s1 * s1, kk * s2 * s2
+        return (a + 0.3) * (b + 0.3) / (((a + b) / 2 + 0.3) ** 2 + ((a - b) / 2) ** 2)
+
+    for k, want in ((0.5, True), (2.0, False)):
+        lo, hi = 1e-3, 1e3               # ratio falls with s1: bisect for ratio = k eps
+        for _ in range(200):
+            mid = math.sqrt(lo * hi)
+            if ratio(mid) > k * EPS:
+                lo = mid
+            else:
+                hi = mid
+        sc = one_gaussian((0.0, 0.0, d), (lo, s2, s2), quat=qz)
+        g, ir = _edge_bits(orc, sc, cam)
+        np.testing.assert_allclose(g[oracle.F_DET], (kk * lo * lo + 0.3) * (kk * s2 * s2 + 0.3), rtol=1e-9)
+        assert bool(ir[oracle.I_EDGE] & oracle.EDGE_DET) == want, ("det", k)
+
+
+def pin_edge_th_vs_opacity(orc):
+    f, d, lam, sig = 80.0, 2.0, 6.0, 0.6
+    cam = axis_camera(65, 65, f)
+    sc = one_gaussian((0.0, 0.0, d), (_iso_scale(lam, f, d),) * 3, opacity=sig)
+    for sgn in (1.0, -1.0):
+        for k, want in ((0.5, True), (2.0, False)):
+            th = sig * (1.0 + sgn * k * EPS)
+            K = (th - TAU) * 2.0 * math.pi * lam        # Eq. 10 with T_up = 1, sqrt(det) = lam
+            g, ir = _edge_bits(orc, sc, cam, scale_mode=1, K=K)
+            np.testing.assert_allclose(g[oracle.F_TH], th, rtol=1e-12)
+            assert bool(ir[oracle.I_EDGE] & oracle.EDGE_TH) == want, ("th", sgn, k)
+            assert (ir[oracle.I_CULL] == oracle.CULL_TH) == (sgn > 0), ("th cull", sgn, k)
+
+
+def pin_edge_radius_ceil(orc):
+    """Isotropic on axis: lambda_max = lam + sqrt(0.1) (the eigenvalue guard), the
+    plain radius ceil(3 sqrt(lambda_max)); AdaGScale with K -> 0 and opacity 0.9
+    keeps the factor 3 (sqrt(2 ln(0.9 / tau)) > 3)."""
+    f, d, R = 80.0, 2.0, 7
+    cam = axis_camera(65, 65, f)
+    for mode, K in ((0, 0.0), (1, 1e-9)):
+        for sgn in (1.0, -1.0):
+            for k, want in ((0.5, True), (2.0, False)):
+                lam1 = (R / 3.0) ** 2 * (1.0 + sgn * k * EPS)
+                lam = lam1 - math.sqrt(0.1)
+                sc = one_gaussian((0.0, 0.0, d), (_iso_scale(lam, f, d),) * 3, opacity=0.9)
+                g, ir = _edge_bits(orc, sc, cam, scale_mode=mode, K=K)
+                np.testing.assert_allclose(g[oracle.F_LAMBDA], lam1, rtol=1e-12)
+                assert ir[oracle.I_RADIUS] == (R if sgn < 0 else R + 1)
+                assert bool(ir[oracle.I_EDGE] & oracle.EDGE_CEIL) == want, ("ceil", mode, sgn, k)
+
+
+def pin_edge_rect(orc):
+    """On-axis Gaussian with the principal point moved: u = cx exactly, and the
+    band's scale is |cx| (t_x = 0) -- also when t_x = 0 is the difference of two
+    large terms (camera and Gaussian 300 units off the origin along x).  Radius 5
+    (3 sqrt(lambda_max) = 4.5).  The tile index of the left end changes where
+    u - r crosses 16 j - 1 (the first pixel centre moves to the next tile), of
+    the right end where u + r crosses 16 j."""
+    f, d = 60.0, 2.0
+    lam = 2.25 - math.sqrt(0.1)
+    s = _iso_scale(lam, f, d)
+    for off in (0.0, 300.0):
+        for side in ("left", "right", "top"):
+            for sgn in (1.0, -1.0):
+                for k, want in ((0.5, True), (2.0, False)):
+                    cam = axis_camera(80, 80, f, campos=(off, 0.0, 0.0))
+                    base = 31.0 + 5.0 if side != "right" else 48.0 - 5.0     # u - 5 = 31, or u + 5 = 48
+                    c = base
+                    for _ in range(3):
+                        c = base + sgn * k * EPS * abs(c)
+                    if side == "top":
+                        cam["cy"], cam["cx"] = c, 40.0
+                    else:
+                        cam["cx"], cam["cy"] = c, 40.0
+                    sc = one_gaussian((off, 0.0, d), (s, s, s))
+                    g, ir = _edge_bits(orc, sc, cam)
+                    assert ir[oracle.I_RADIUS] == 5
+                    got = bool(ir[oracle.I_EDGE] & oracle.EDGE_RECT)
+                    assert got == want, ("rect", off, side, sgn, k, got)
+                    if side == "top":
+                        lo_t, hi_t = ir[oracle.I_Y0], ir[oracle.I_Y1]
+                    else:
+                        lo_t, hi_t = ir[oracle.I_X0], ir[oracle.I_X1]
+                    if side == "right":
+                        assert hi_t == (4 if sgn > 0 else 3)
+                    else:
+                        assert lo_t == (2 if sgn > 0 else 1)
+
+
+def pin_edge_lut_bin(orc):
+    f = 200.0
+    cam = axis_camera(65, 65, f)
+    for edge_depth, decision in ((5.0, True), (10.0, True), (95.0, True), (100.0, False)):
+        for sgn in (1.0, -1.0):
+            for k in (0.5, 2.0):
+                d = edge_depth * (1.0 + sgn * k * EPS)
+                sc = one_gaussian((0.0, 0.0, d), (_iso_scale(9.0, f, d),) * 3, opacity=0.8)
+                _, ir = _edge_bits(orc, sc, cam, scale_mode=1, K=0.01)
+                want = decision and k < 1.0
+                assert bool(ir[oracle.I_EDGE] & oracle.EDGE_LUT) == want, ("lut", edge_depth, sgn, k)
+
+
+def pin_edge_ellipse(orc):
+    """Isotropic conic (A = C = 1/lam, B = 0), v = 40 mid-row: the tile right of
+    the centre in its row has min q = (48 - u)^2 / lam; every other tile of the
+    square is far from Q = 2 ln(sigma / tau).  pos_err = 0 isolates the other
+    two terms of the band."""
+    f, d, lam, sig, W, H = 60.0, 2.0, 9.0, 0.8, 80, 80
+    Q = 2.0 * math.log(sig / TAU)
+    s = _iso_scale(lam, f, d)
+    for pe in (0.0, 2e-3):
+        for sgn in (1.0, -1.0):
+            for k, want in ((0.5, True), (2.0, False)):
+                u = 48.0 - math.sqrt(lam * Q)
+                for _ in range(4):       # the band depends (weakly) on u through S
+                    r = math.ceil(3.0 * math.sqrt(lam + math.sqrt(0.1)))
+                    x0 = int(math.ceil(u - r)) // 16
+                    x1 = int(math.floor(u + r)) // 16 + 1
+                    X = max(abs(16 * x0 - u), abs(min(16 * x1 - 1, W - 1) - u))
+                    S = (X * X + 8.0 * 8.0) / lam
+                    band = EPS * max(Q, 1.0) + 2.0 * pe * math.sqrt((2.0 / lam) * Q) + 2e-6 * S
+                    m = Q + sgn * k * band
+                    u = 48.0 - math.sqrt(lam * m)
+                cam = axis_camera(W, H, f)
+                cam["cx"], cam["cy"] = u, 40.0
+                sc = one_gaussian((0.0, 0.0, d), (s, s, s), opacity=sig)
+                _, ir = _edge_bits(orc, sc, cam, tile_test=oracle.TILE_ELLIPSE, pos_err=pe)
+                assert bool(ir[oracle.I_EDGE] & oracle.EDGE_ELLIPSE) == want, ("ellipse", pe, sgn, k)
+
+
+def pin_edge_pixel_budget(orc):
+    """One isotropic Gaussian at a pixel centre, alpha = sigma exp(-r^2 / (2 lam)):
+    lam is chosen so that the 4 pixels at distance 4 have ln(alpha / tau) = delta.
+    The flip budget is 2 tau T c_max = 2 tau there (T = 1, colours < 1) when
+    |delta| is within the band and zero there when it is outside (the centre
+    pixel, p = 0 exactly, always carries 2 sigma; every other pixel nothing).  Then the
+    centre moved by e from the pixel: p = -e^2 / (2 lam) against the p <= 0 test."""
+    f, d, sig, W = 80.0, 2.0, 0.7, 65
+    cam = axis_camera(W, W, f)
+    ring = [(32 + 4, 32), (32 - 4, 32), (32, 32 + 4), (32, 32 - 4)]
+    for pe in (0.0, 1e-3):
+        for sgn in (1.0, -1.0):
+            for k, want in ((0.5, True), (2.0, False)):
+                lam = 8.0 / math.log(sig / TAU)
+                for _ in range(4):       # the band's gradient term depends on lam
+                    band = EPS + pe * 4.0 / lam          # |grad ln alpha| = (|A dx| + |C dy|) = 4 / lam
+                    lam = 8.0 / (math.log(sig / TAU) - sgn * k * band)
+                sc = one_gaussian((0.0, 0.0, d), (_iso_scale(lam, f, d),) * 3, opacity=sig)
+                out = orc.render(sc, cam, oracle.params(cam, pos_err=pe))
+                bud = out["budget"]
+                expect = np.zeros_like(bud)
+                expect[32, 32] = 2.0 * sig       # the centre pixel has p = 0 exactly: always in its band
+                if want:
+                    for (x, y) in ring:
+                        expect[y, x] = 2.0 * TAU
+                np.testing.assert_allclose(bud, expect, rtol=1e-12, atol=0, err_msg="alpha-tau %g %g %g" % (pe, sgn, k))
+    lam = 4.0
+    for k, want in ((0.5, True), (2.0, False)):
+        e = math.sqrt(2.0 * lam * k * EPS)
+        cam["cx"] = 32.0 + e
+        sc = one_gaussian((0.0, 0.0, d), (_iso_scale(lam, f, d),) * 3, opacity=sig)
+        out = orc.render(sc, cam, oracle.params(cam, pos_err=0.0))
+        bud = out["budget"]
+        assert (bud[32, 32] == 2.0 * sig) == want and np.count_nonzero(bud) == int(want), ("p", k)
+
+
+def pin_gradient_edges(orc):
+    """Decisions that move only the derivatives are flagged within their bands:
+    a colour channel at the clamp at 0 (|0.5 + C0 dc| <= eps (0.5 + |C0 dc|)),
+    x/z at the 1.3 tan(fov/2) frustum clamp, and per pixel of the backward the
+    alpha-tau ring and the transmittance stop T (1 - alpha) vs 1e-4."""
+    f, d = 80.0, 2.0
+    cam = axis_camera(65, 65, f)
+    for sgn in (1.0, -1.0):
+        for k, want in ((0.5, True), (2.0, False)):
+            # colour: 0.5 + C0 dc = sgn k eps (0.5 + C0 |dc|), dc < 0
+            dc = -(0.5 - sgn * k * EPS * 1.0) / (C0 * (1.0 + sgn * k * EPS))
+            sc = one_gaussian((0.0, 0.0, d), (0.05, 0.05, 0.05), dc=(dc, 0.2, 0.2))
+            _, ir = _edge_bits(orc, sc, cam)
+            assert bool(ir[oracle.I_GEDGE] & oracle.GEDGE_COLOUR) == want, ("colour", sgn, k)
+            assert bool(ir[oracle.I_CLAMP] & 1) == (sgn < 0)
+            # frustum: x/z = lim (1 + sgn k eps), lim = 1.3 W / (2 f)
+            lim = 1.3 * 0.5 * 65 / f
+            x = d * lim * (1.0 + sgn * k * EPS)
+            sc = one_gaussian((x, 0.0, d), (0.05, 0.05, 0.05))
+            _, ir = _edge_bits(orc, sc, cam)
+            assert bool(ir[oracle.I_GEDGE] & oracle.GEDGE_FRUSTUM) == want, ("frustum", sgn, k)
+    # the alpha-tau ring of pin_edge_pixel_budget: 4 ring pixels + the centre (p = 0)
+    sig, W = 0.7, 65
+    for k, want in ((0.5, 5), (2.0, 1)):
+        lam = 8.0 / (math.log(sig / TAU) - k * EPS)
+        sc = one_gaussian((0.0, 0.0, d), (_iso_scale(lam, f, d),) * 3, opacity=sig)
+        par = oracle.params(cam, pos_err=0.0)
+        out = orc.render(sc, cam, par)
+        g = orc.backward(sc, cam, par, out["tile_start"], out["ids"], np.ones((3, W, W)))
+        assert g["edge"][0] == want, ("ring", k, g["edge"][0])
+    # the stop: three isotropic Gaussians stacked on the axis, 0.3 px off the
+    # centre of pixel (32, 32); the third's opacity puts T (1 - alpha_3) at
+    # 1e-4 (1 + delta) there (alpha_i = sigma_i exp(-e^2 / (2 lam_i)))
+    e, s_w = 0.3, 0.05
+    camo = axis_camera(W, W, f)
+    camo["cx"] = 32.0 + e
+    lam_at = lambda dd: (f * s_w / dd) ** 2 + 0.3
+    a_front = [0.95 * math.exp(-e * e / (2 * lam_at(dd))) for dd in (2.0, 2.5)]
+    T2 = (1.0 - a_front[0]) * (1.0 - a_front[1])
+    for k, want in ((0.5, 1), (2.0, 0)):
+        band = EPS + 3 * 1.2e-7
+        a3 = 1.0 - 1e-4 * (1.0 + k * band) / T2
+        sig3 = a3 / math.exp(-e * e / (2 * lam_at(3.0)))
+        sc = concat(one_gaussian((0.0, 0.0, 2.0), (s_w,) * 3, opacity=0.95),
+                    one_gaussian((0.0, 0.0, 2.5), (s_w,) * 3, opacity=0.95),
+                    one_gaussian((0.0, 0.0, 3.0), (s_w,) * 3, opacity=sig3))
+        par = oracle.params(camo, pos_err=0.0)
+        out = orc.render(sc, camo, par)
+        g = orc.backward(sc, camo, par, out["tile_start"], out["ids"], np.ones((3, W, W)))
+        assert g["edge"][2] == want, ("stop", k, g["edge"][2])
+        if want == 0:   # nothing near a threshold anywhere: no budget
+            assert all(not np.any(v) for v in g["budget"].values())
+    # the flip budget bounds what the stop flip does to the two front Gaussians
+    rng = np.random.default_rng(3)
+    wr = rng.normal(size=(3, W, W))
+    gs = []
+    for sgn in (1.0, -1.0):         # third Gaussian blended (+), or the pixel stops before it (-)
+        band = EPS + 3 * 1.2e-7
+        a3 = 1.0 - 1e-4 * (1.0 + sgn * 0.5 * band) / T2
+        sig3 = a3 / math.exp(-e * e / (2 * lam_at(3.0)))
+        sc = concat(one_gaussian((0.0, 0.0, 2.0), (s_w,) * 3, opacity=0.95),
+                    one_gaussian((0.0, 0.0, 2.5), (s_w,) * 3, opacity=0.95),
+                    one_gaussian((0.0, 0.0, 3.0), (s_w,) * 3, opacity=sig3))
+        par = oracle.params(camo, pos_err=0.0)
+        out = orc.render(sc, camo, par)
+        gs.append(orc.backward(sc, camo, par, out["tile_start"], out["ids"], wr))
+    # (the two scenes also differ smoothly: the third opacity by ~1e-5 relative)
+    for key in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        for gg in gs:
+            assert np.all(gg["budget"][key][..., :2] >= 0)
+        diff = np.abs(gs[0][key][..., :2] - gs[1][key][..., :2])
+        bound = np.minimum(gs[0]["budget"][key][..., :2], gs[1]["budget"][key][..., :2])
+        smooth = 1e-4 * np.maximum(np.abs(gs[0][key][..., :2]), np.abs(gs[1][key][..., :2]))
+        assert np.all(diff <= bound + smooth + 1e-15), key
+    # the flip itself moves the front Gaussians' x-gradient far beyond the smooth part
+    dmx = np.abs(gs[0]["mean"][0, :2] - gs[1]["mean"][0, :2])
+    assert np.all(dmx > 1e-3 * np.abs(gs[0]["mean"][0, :2]))
+    # an alpha-tau flip of a small back Gaussian (its ring of pin_edge_pixel_budget)
+    # under a wide front Gaussian whose colour equals the background: the front's
+    # colour-behind changes by about tau |c_back - bg| at the ring although
+    # c_front - R is nearly zero there.  The smooth part is measured between two
+    # scenes on the same side of the flip (0.5 and 0.6 of the band).
+    cam = axis_camera(W, W, f)
+    dc_f = np.array([0.3, -0.2, 0.1])
+    bg = tuple(float(x) for x in dc_f * C0 + 0.5)
+    gs = {}
+    for frac in (0.5, 0.6, -0.5):
+        lam = 8.0 / (math.log(sig / TAU) - frac * EPS)
+        sc = concat(one_gaussian((0.0, 0.0, 1.5), (0.4, 0.4, 0.4), opacity=0.3, dc=dc_f),
+                    one_gaussian((0.0, 0.0, d), (_iso_scale(lam, f, d),) * 3, opacity=sig, dc=(-0.4, 0.6, 0.2)))
+        par = oracle.params(cam, pos_err=0.0, bg=bg)
+        out = orc.render(sc, cam, par)
+        gs[frac] = orc.backward(sc, cam, par, out["tile_start"], out["ids"], wr)
+    assert gs[0.5]["edge"][1] > 0 and gs[-0.5]["edge"][1] > 0
+    moved = 0
+    for key in ("mean", "log_scale", "opacity_logit", "sh"):
+        diff = np.abs(gs[0.5][key][..., 0] - gs[-0.5][key][..., 0])
+        smooth = 20.0 * np.abs(gs[0.5][key][..., 0] - gs[0.6][key][..., 0])
+        bound = np.minimum(gs[0.5]["budget"][key][..., 0], gs[-0.5]["budget"][key][..., 0])
+        assert np.all(diff <= bound + smooth + 1e-15), ("ring", key)
+        moved += int(np.count_nonzero(diff > 10 * smooth + 1e-13))
+    assert moved > 0
+
 ALL_PINS = [pin_isotropic_on_axis, pin_off_axis_jacobian, pin_rotation_conventions, pin_eq9_quadrature,
             pin_eq8_riemann_pixels, pin_sh_basis, pin_sh_colour, pin_rect_enumeration, pin_bruteforce,
             pin_ideal_render, pin_invariants, pin_low_opacity_invisible, pin_max_T, pin_backward_fd,
             pin_ellipse_tiles, pin_ellipse_lossless_plain, pin_peripheral_two_layers, pin_peripheral_closed_form,
-            pin_peripheral_invariants, pin_skip_render]
+            pin_peripheral_invariants, pin_skip_render, pin_edge_near_plane, pin_edge_det_guard,
+            pin_edge_th_vs_opacity, pin_edge_radius_ceil, pin_edge_rect, pin_edge_lut_bin, pin_edge_ellipse,
+            pin_edge_pixel_budget, pin_gradient_edges]

@@ -10,6 +10,8 @@ import torch.multiprocessing as mp
 
 from paper_2604_18980_gb300.multiview import shard_views, sum_gradients
 
+KEYS = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+
 
 def test_shard_views_partition():
     cams = list(range(10))
@@ -46,8 +48,8 @@ def _worker(rank, world, port, out_path):
         par = oracle.params(cam)
         oo = oracle.render(scene, cam, par)
         g = oracle.backward(scene, cam, par, oo["tile_start"], oo["ids"], ws[v])
-        acc = g if acc is None else {k: acc[k] + g[k] for k in acc}
-    grads = {k: torch.from_numpy(np.ascontiguousarray(acc[k])) for k in ("mean", "log_scale", "quat", "opacity_logit", "sh")}
+        acc = g if acc is None else {k: acc[k] + g[k] for k in KEYS}
+    grads = {k: torch.from_numpy(np.ascontiguousarray(acc[k])) for k in KEYS}
     sum_gradients(grads)
     if rank == 0:
         torch.save(grads, out_path)
@@ -69,6 +71,6 @@ def test_gradient_sum_over_two_ranks(tmp_path):
         par = oracle.params(cam)
         oo = oracle.render(scene, cam, par)
         g = oracle.backward(scene, cam, par, oo["tile_start"], oo["ids"], ws[v])
-        ref = g if ref is None else {k: ref[k] + g[k] for k in ref}
+        ref = g if ref is None else {k: ref[k] + g[k] for k in KEYS}
     for k in got:
         np.testing.assert_allclose(got[k].numpy(), ref[k], rtol=1e-12, atol=1e-14)

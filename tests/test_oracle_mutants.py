@@ -67,6 +67,62 @@ MUTANTS = [
      "double c = rule == 0 ? alpha * Ts : weight[list[k]] * alpha;", ["pin_skip_render"]),
     ("skipped_blend_still_occludes", "            Ts *= 1.0 - alpha;\n          }\n",
      "          }\n          Ts *= 1.0 - alpha;\n", ["pin_skip_render"]),
+    # edge classes: each band widened tenfold, narrowed to nothing, or missing a term
+    ("edge_near_x10", "if (near_edge(t[2].v, cam->near_z, eps, fmax(fabs(t[2].v), cam->near_z))) edge |= EDGE_NEAR;",
+     "if (near_edge(t[2].v, cam->near_z, 10 * eps, fmax(fabs(t[2].v), cam->near_z))) edge |= EDGE_NEAR;",
+     ["pin_edge_near_plane"]),
+    ("edge_near_camera_magnitude", "if (near_edge(t[2].v, cam->near_z, eps, fmax(fabs(t[2].v), cam->near_z))) edge |= EDGE_NEAR;",
+     "if (near_edge(t[2].v, cam->near_z, eps, fmax(fabs(t[2].v) + fabs(cam->t[2]), cam->near_z))) edge |= EDGE_NEAR;",
+     ["pin_edge_near_plane"]),
+    ("edge_rect_magnitude_sum", "double uscale = fabs(cam->fx * t[0].v / t[2].v) + fabs(cam->cx);",
+     "double uscale = fabs(cam->fx * t[0].v / t[2].v) + fabs(cam->cx) + cam->fx * fabs(cam->t[0]) / t[2].v;",
+     ["pin_edge_rect"]),
+    ("edge_det_x10", "if (near_edge(det.v, 0.0, eps, fabs(ca.v * cc.v) + cb.v * cb.v)) edge |= EDGE_DET;",
+     "if (near_edge(det.v, 0.0, 10 * eps, fabs(ca.v * cc.v) + cb.v * cb.v)) edge |= EDGE_DET;",
+     ["pin_edge_det_guard"]),
+    ("edge_th_x10", "if (near_edge(th, opac.v, eps, fmax(th, opac.v))) edge |= EDGE_TH;",
+     "if (near_edge(th, opac.v, 10 * eps, fmax(th, opac.v))) edge |= EDGE_TH;", ["pin_edge_th_vs_opacity"]),
+    ("edge_ceil_x10", "rarg_hi = 3.0 * sqrt(lam1 * (1 + eps));", "rarg_hi = 3.0 * sqrt(lam1 * (1 + 10 * eps));",
+     ["pin_edge_radius_ceil"]),
+    ("edge_ceil_dropped", "if ((int)ceil(rarg_hi) != (int)ceil(rarg_lo)) edge |= EDGE_CEIL;", "",
+     ["pin_edge_radius_ceil"]),
+    ("edge_rect_no_slack", "double su = eps * uscale, sv = eps * vscale;", "double su = 0.0, sv = 0.0;",
+     ["pin_edge_rect"]),
+    ("edge_rect_x10", "double su = eps * uscale, sv = eps * vscale;",
+     "double su = 10 * eps * uscale, sv = 10 * eps * vscale;", ["pin_edge_rect"]),
+    ("edge_lut_x10", "near_edge(fb, fr, eps, fmax(fabs(fb), 1.0))", "near_edge(fb, fr, 10 * eps, fmax(fabs(fb), 1.0))",
+     ["pin_edge_lut_bin"]),
+    ("edge_lut_open_end_flagged", "if (fr >= 1.0 && fr <= par->lut_bins - 1 &&", "if (fr >= 1.0 && fr <= par->lut_bins &&",
+     ["pin_edge_lut_bin"]),
+    ("edge_ellipse_x10", "double tol = eps * fmax(Q, 1.0) +", "double tol = 10 * eps * fmax(Q, 1.0) +",
+     ["pin_edge_ellipse"]),
+    ("edge_ellipse_no_size_term", "sqrt((A.v + C.v) * fmax(fmax(Q, m), 0.0)) + 2e-6 * S;",
+     "sqrt((A.v + C.v) * fmax(fmax(Q, m), 0.0));", ["pin_edge_ellipse"]),
+    ("edge_ellipse_no_position_term", "double tol = eps * fmax(Q, 1.0) + 2.0 * par->pos_err *",
+     "double tol = eps * fmax(Q, 1.0) + 0.0 * par->pos_err *", ["pin_edge_ellipse"]),
+    ("edge_budget_alpha_tau_dropped",
+     "if (araw > 0.0 && fabs(log(araw / par->tau)) <= tol) budget += 2.0 * par->tau * T * cmax;", "",
+     ["pin_edge_pixel_budget"]),
+    ("edge_budget_x10", "\n    double tol = par->edge_rel + par->pos_err * gl;\n",
+     "\n    double tol = 10 * par->edge_rel + par->pos_err * gl;\n", ["pin_edge_pixel_budget"]),
+    ("edge_budget_no_gradient_term", "\n    double tol = par->edge_rel + par->pos_err * gl;\n",
+     "\n    double tol = par->edge_rel;\n", ["pin_edge_pixel_budget"]),
+    ("edge_budget_p_term_dropped",
+     "if (fabs(p) <= par->edge_rel && g[F_OPAC] >= par->tau) budget += 2.0 * g[F_OPAC] * T * cmax;", "",
+     ["pin_edge_pixel_budget"]),
+    ("gedge_colour_dropped", "if (fabs(acc.v) <= eps * mag) irec[I_GEDGE] |= GEDGE_COLOUR;", "",
+     ["pin_gradient_edges"]),
+    ("gedge_frustum_x10", "if (near_edge(fabs(txtz.v), limx, eps, limx) || near_edge(fabs(tytz.v), limy, eps, limy))",
+     "if (near_edge(fabs(txtz.v), limx, 10 * eps, limx) || near_edge(fabs(tytz.v), limy, eps, limy))",
+     ["pin_gradient_edges"]),
+    ("gedge_stop_dropped", "stopd = fabs(log(tt / par->t_min)) <=", "stopd = 0 * fabs(log(tt / par->t_min)) >",
+     ["pin_gradient_edges"]),
+    ("gbudget_no_colour_behind_term", "(rho * fabs(c[ch] - R[ch]) + dR)", "(rho * fabs(c[ch] - R[ch]))",
+     ["pin_gradient_edges"]),
+    ("gbudget_flip_not_recorded", "                  nflip++;\n", "",
+     ["pin_gradient_edges"]),
+    ("gbudget_front_behind_swapped", "if (fbl[q] ? fpos[q] < j : fpos[q] <= j) rho += frho[q];",
+     "if (fpos[q] > j) rho += frho[q];", ["pin_gradient_edges"]),
 ]
 
 
