@@ -45,19 +45,23 @@ def metric_for(workload: str, n: int, W: int, H: int, V: int) -> str:
         ("%dM" % (n >> 20)) if n >= 1 << 20 else ("%dK" % (n >> 10)), W, H, V)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# FP32 work per pixel-pair evaluation of Eq. 1-2 counted as the FP32-pipe
-# operations the blend needs: dx, dy (2); the quadratic form (5); exp scale
-# and opacity product (2); alpha clamp and the two threshold compares (3);
-# 1 - alpha and the transmittance product (2); the three colour FMAs and
-# alpha*T (4) = 18.  The exponential itself runs on the SFU.
-RASTER_OPS_PER_EVAL = 18
+# FP32 work per pixel-pair evaluation of Eq. 1-2: dx, dy, the quadratic
+# form, the exponent's scale, T (1 - alpha) and the three colour FMAs (8
+# FMA-pipe operations) plus the alpha >= tau, clamp and stop compares (3);
+# the exponential itself runs on the SFU.  An evaluation is one pixel against
+# one pair of its tile's list, up to the pair at which the pixel stops: the
+# method's own count (the oracle counts the same), not the blend kernel's,
+# whose per-warp culling skips most of them.
+RASTER_OPS_PER_EVAL = 11
 # DRAM bytes (read + write) per view of one raster_kernel<false,false,false>
 # launch, by workload, from ncu captures of that kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of a multi-view launch divided by its views; the
 # kernel's traffic grows with the number of views it renders).  A workload
 # missing here, or any entry after the kernel changed and before it was
 # captured again, reports traffic null.
-RASTER_TRAFFIC_PER_VIEW = {}
+RASTER_TRAFFIC_PER_VIEW = {
+    "c2_clusters1m_1080p": (100.707072e6 + 106.767616e6) / 6,     # 6-view capture
+}
 
 
 def parse():
@@ -277,6 +281,7 @@ def run_ours(args, world, rank, local):
     ada.check()
     evals_per_step = int(ada.stats[0].item())
     blends_per_step = int(ada.stats[1].item())
+    slots_per_step = int(ada.stats[2].item())
     ada_pairs = ada.pairs()
     passes = ada.sort_plan()[0]
     launches_per_step = ada.launches_per_forward()
@@ -569,7 +574,7 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant stage
     pk, pk_src = peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    roof = roofline(dom, stage_ms[dom], ada, evals_per_step, pk, pk_src, passes, clk, workload)
+    roof = roofline(dom, stage_ms[dom], ada, evals_per_step, pk, pk_src, passes, clk, workload, slots_per_step)
     line = {
         "metric": metric_for(workload, ada.n, ada.W, ada.H, V), "value": fps, "unit": "FPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -585,7 +590,8 @@ def run_ours(args, world, rank, local):
         "stage_ms": stage_ms,
         "stage_hbm": stage_frac,
         "roofline": roof,
-        "blend_work": {"evaluations_per_frame": evals_per_step / V, "blended_per_frame": blends_per_step / V},
+        "blend_work": {"evaluations_per_frame": evals_per_step / V, "blended_per_frame": blends_per_step / V,
+                       "executed_pixel_pairs_per_frame": slots_per_step / V},
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
@@ -691,7 +697,7 @@ def stage_bytes(stage, r, passes):
     return n * 44 + any_live * 192 + live * 69 + (G - live) * 17, "preprocess_kernel"
 
 
-def roofline(stage, ms, r, evals, pk, pk_src, passes, clk, workload=WORKLOAD):
+def roofline(stage, ms, r, evals, pk, pk_src, passes, clk, workload=WORKLOAD, slots=None):
     V, n = r.V, r.n
     P = r.pairs()
     if stage == "raster":
@@ -706,7 +712,11 @@ def roofline(stage, ms, r, evals, pk, pk_src, passes, clk, workload=WORKLOAD):
                 "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read+write per view x views" if traffic else
                                   "not captured for this kernel build and workload",
-                "work": "%d pixel-pair evaluations x %d FP32 ops" % (evals, RASTER_OPS_PER_EVAL),
+                "work": "%d Eq. 1-2 evaluations (each pixel against its tile's pairs up to its stop) x %d FP32 "
+                        "ops" % (evals, RASTER_OPS_PER_EVAL),
+                "executed": None if not slots else {
+                    "pixel_pairs": slots, "frac": slots * RASTER_OPS_PER_EVAL / (ms / 1e3) / 1e12 / peak_ops,
+                    "note": "the pixel-pair slots the kernel walks after its per-warp culling"},
                 "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (%s)" % (sms, sm_mhz, pk_src)}
     hbm = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
     byts, kern = stage_bytes(stage, r, passes)

@@ -346,8 +346,12 @@ ags_status ags_sort_tiles(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, ui
  * n_contrib [views][H][W] (1-based position in the tile list of the last
  * blended pair), both nullable (the backward needs them); max_T [views*n]
  * (nullable; zeroed by the caller) receives, per Gaussian, the largest T seen
- * before blending it (calibration, Sec. 3.4); stats (nullable uint64[2])
- * accumulates {pixel-pair evaluations, blended pairs}. */
+ * before blending it (calibration, Sec. 3.4); stats (nullable uint64[3])
+ * accumulates {evaluations of Eq. 1-2 as the method defines them -- each
+ * pixel against the pairs of its tile's list up to the one at which it stops,
+ * or the whole list --, blended pairs, pixel-pair slots the kernel actually
+ * evaluated (its per-warp culling skips the pairs whose alpha >= tau ellipse
+ * misses a warp's 8x16 block)}. */
 ags_status ags_rasterize(const ags_projected* proj, int64_t n, const uint32_t* sorted_vals,
                          const uint32_t* ranges, const ags_camera* cams, int32_t views,
                          const ags_params* params, float* image, float* final_T,

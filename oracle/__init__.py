@@ -200,7 +200,7 @@ class Oracle:
         nc = np.zeros((height, width), dtype=np.int32)
         bud = np.zeros((height, width), dtype=np.float64)
         mT = np.zeros(n, dtype=np.float64) if want_max_T else None
-        st = np.zeros((height, width, 2), dtype=np.int32) if want_state else None
+        st = np.zeros((height, width, 3), dtype=np.int32) if want_state else None
         mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
         ids = np.ascontiguousarray(ids, dtype=np.int32) if len(ids) else np.zeros(1, dtype=np.int32)
         self.L.oracle_rasterize(n, _ptr(_d(dbl)), _ptr(np.ascontiguousarray(tile_start, dtype=np.int64)),

@@ -562,13 +562,14 @@ typedef struct {
   int32_t n_contrib;     /* 1-based position of the last blended entry */
   int32_t n_blend;       /* number of blended entries */
   int32_t n_clamp;       /* number of blended entries with alpha clamped at alpha_max */
+  int32_t n_eval;        /* entries evaluated: up to and including the one it stopped at, else all */
   double budget;         /* bound on the change a near-threshold flip can cause */
 } oc_pix;
 
 static void blend_pixel(double px, double py, const int32_t* list, int64_t len, const double* dbl,
                         const oc_params* par, double cmax, double* maxT, oc_pix* out) {
   double T = 1.0, col[3] = {0, 0, 0}, budget = 0.0;
-  int32_t last = 0, nb = 0, ncl = 0;
+  int32_t last = 0, nb = 0, ncl = 0, nev = (int32_t)len;
   for (int64_t k = 0; k < len; k++) {
     const double* g = dbl + (int64_t)list[k] * OC_NF;
     double dx = g[F_U] - px, dy = g[F_V] - py;
@@ -583,7 +584,7 @@ static void blend_pixel(double px, double py, const int32_t* list, int64_t len, 
     if (p > 0.0) continue;
     if (alpha < par->tau) continue;
     double test_T = T * (1.0 - alpha);
-    if (test_T < par->t_min) break;
+    if (test_T < par->t_min) { nev = (int32_t)(k + 1); break; }
     col[0] += g[F_R] * alpha * T;
     col[1] += g[F_G] * alpha * T;
     col[2] += g[F_BL] * alpha * T;
@@ -609,6 +610,7 @@ static void blend_pixel(double px, double py, const int32_t* list, int64_t len, 
   out->n_contrib = last;
   out->n_blend = nb;
   out->n_clamp = ncl;
+  out->n_eval = nev;
   out->budget = budget;
 }
 
@@ -626,7 +628,7 @@ static double color_max(int64_t n, const double* dbl, const oc_params* par) {
 void oracle_rasterize(int64_t n, const double* dbl, const int64_t* tile_start, const int32_t* ids,
                       int32_t width, int32_t height, const oc_params* par, const uint8_t* tile_mask,
                       double* image, double* final_T, int32_t* n_contrib, double* budget, double* maxT,
-                      int32_t* state /* [H][W][2] nullable: blended count, clamped count */) {
+                      int32_t* state /* [H][W][3] nullable: blended, clamped and evaluated counts */) {
   int gx = (width + OC_TILE - 1) / OC_TILE, gy = (height + OC_TILE - 1) / OC_TILE;
   int64_t nt = (int64_t)gx * gy;
   int64_t hw = (int64_t)width * height;
@@ -645,7 +647,7 @@ void oracle_rasterize(int64_t n, const double* dbl, const int64_t* tile_start, c
         if (final_T) final_T[o] = pix.T;
         if (n_contrib) n_contrib[o] = pix.n_contrib;
         if (budget) budget[o] = pix.budget;
-        if (state) { state[2 * o] = pix.n_blend; state[2 * o + 1] = pix.n_clamp; }
+        if (state) { state[3 * o] = pix.n_blend; state[3 * o + 1] = pix.n_clamp; state[3 * o + 2] = pix.n_eval; }
       }
   }
 }

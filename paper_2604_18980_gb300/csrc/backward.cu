@@ -57,9 +57,9 @@ __device__ __forceinline__ bool pixel_adjoint(const Staged& s, float cbl, const 
                                               float gb, float gc, float& T, float& Ra, float& Rb, float& Rc,
                                               float acc[9]) {
   const float q = splat_qy(s, P, Bx, dy);
-  if (!splat_accept(q, s.b.y)) return false;
-  const float raw = __fmul_rn(bc.tau, fast_exp2(q));
-  const float alpha = fminf(bc.alpha_max, raw);
+  if (!splat_accept(q, bc.l2tau)) return false;
+  float raw;
+  const float alpha = splat_alpha(q, bc.alpha_max, raw);
   const float om = 1.f - alpha;
   T = __fdividef(T, om);                         // transmittance before this splat
   const float w = alpha * T;

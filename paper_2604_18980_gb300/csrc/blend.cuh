@@ -1,23 +1,21 @@
-// blend.cuh -- per-pixel alpha of one splat (Eq. 1) as the blend and its
-// adjoint evaluate it, shared so both take bit-identical decisions.
+// blend.cuh -- per-pixel alpha of one splat (Eq. 1) as the blend, its adjoint
+// and the diagnostics evaluate it, shared so all take bit-identical decisions.
 //
-// The exponent is carried in log2 units relative to tau: with
+// The exponent is carried in log2 units:
 //   a2 = -A log2(e)/2, b2 = -B log2(e), c2 = -C log2(e)/2,
-//   base = log2(opacity / tau),
-//   q  = a2 dx^2 + b2 dx dy + c2 dy^2 + base = log2(opacity e^p / tau),
-// Eq. 1 is alpha = min(alpha_max, tau 2^q); alpha >= tau is q >= 0 and p <= 0 is
-// q <= base, so the threshold test runs before the exponential.
+//   q  = a2 dx^2 + b2 dx dy + c2 dy^2 + log2(opacity) = log2(opacity e^p),
+// so Eq. 1 is alpha = min(alpha_max, 2^q) and alpha >= tau is q >= log2(tau):
+// the threshold test runs before the exponential.  The transmittance after a
+// blended splat is fma(-alpha, T, T), T (1 - alpha) rounded once.
 //
-// The blend and its adjoint cover a 16x16 tile with four warps; warp w owns
-// the 8x8 pixel block rows 8*(w>>1).., columns 8*(w&1)...  For every staged
-// splat the loading thread also computes which of the blocks can hold a pixel with
-// alpha >= tau: its ellipse p >= ln(tau/opacity) must reach the block's
-// rectangle of pixel centres -- a bounding-box test (half-widths
-// sqrt(2 ln(opacity/tau) Sigma_xx), sqrt(2 ln(opacity/tau) Sigma_yy)) and then
-// the exact minimum of the quadratic form over the rectangle, both with a slack
-// far above fp32 rounding.  A warp skips a splat whose bit is clear: those
-// pixels would have rejected it with alpha < tau anyway, so the result is
-// unchanged.
+// For every staged splat the loading thread also computes which blocks of
+// the 16x16 tile can hold a pixel with alpha >= tau: its ellipse
+// p >= ln(tau/opacity) must reach the block's rectangle of pixel centres -- a
+// bounding-box test (half-widths sqrt(2 ln(opacity/tau) Sigma_xx),
+// sqrt(2 ln(opacity/tau) Sigma_yy)) and then the exact minimum of the
+// quadratic form over the rectangle, both with a slack far above fp32
+// rounding.  A block whose bit is clear would have rejected the splat with
+// alpha < tau at every pixel, so skipping it leaves the result unchanged.
 #pragma once
 
 #include <cmath>
@@ -47,9 +45,16 @@ inline BlendConst make_blend_const(const DevParams& dp) {
 
 struct Staged {
   float4 a;      // u, v, a2, b2
-  float4 b;      // c2, l2s - log2(tau), r, g
+  float4 b;      // c2, log2(opacity), r, g
   float c;       // b
 };
+
+// Does the alpha >= tau ellipse of a splat reach the rectangle of pixel
+// centres [x0, x0 + w] x [y0, y0 + h]?  (cu, cv): the splat centre relative to
+// (x0, y0); r2n: 2 ln(opacity / tau) plus slack; Sxx, Syy: the covariance
+// diagonal (half-widths of the ellipse's bounding box); A, B, C: the conic.
+__device__ __forceinline__ bool ellipse_reaches(float cu, float cv, float w, float h, float r2n, float Sxx, float Syy,
+                                                float A, float B, float C);
 
 // Minimum over the rectangle [xl,xh] x [yl,yh] of A x^2 + 2 B x y + C y^2 for a
 // positive-definite (A B; B C): zero when the rectangle holds the origin,
@@ -71,50 +76,63 @@ __device__ __forceinline__ float rect_min_quad(float A, float B, float C, float 
   return m;
 }
 
-// Splat record (48 bytes): u v A B | C opacity r g | b Th Sxx Syy.
+__device__ __forceinline__ bool ellipse_reaches(float cu, float cv, float w, float h, float r2n, float Sxx, float Syy,
+                                                float A, float B, float C) {
+  if (!(r2n > 0.f)) return false;
+  const float hx = sqrtf(r2n * Sxx) * 1.0001f + 0.01f;
+  const float hy = sqrtf(r2n * Syy) * 1.0001f + 0.01f;
+  return cu + hx >= 0.f && cu - hx <= w && cv + hy >= 0.f && cv - hy <= h &&
+         rect_min_quad(A, B, C, -cu, w - cu, -cv, h - cv) <= r2n * 1.0001f;
+}
+
+// The staged form of a splat record (48 bytes: u v A B | C opacity r g | b Th Sxx Syy).
+__device__ __forceinline__ void stage_record(const float4& r0, const float4& r1, const float4& r2, Staged& s) {
+  s.a = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
+  s.b = make_float4(-0.5f * kLog2e * r1.x, __log2f(r1.y), r1.z, r1.w);
+  s.c = r2.x;
+}
+
+// 2 ln(opacity / tau) + slack: the squared Mahalanobis radius of the alpha >= tau ellipse.
+__device__ __forceinline__ float reach_r2n(float l2s, float l2tau) { return 2.f * kLn2 * (l2s - l2tau) + 1e-3f; }
+
 // Mask bit w: the ellipse can reach block w of the tile, blocks being
 // BW x BH pixels in row-major order of (16/BW) x (16/BH).
 template <int BW, int BH>
 __device__ __forceinline__ void stage_splat(const float4* rec, int tx0, int ty0, float l2tau, Staged& s,
                                             uint32_t& mask) {
   const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
-  const float base = __log2f(r1.y) - l2tau;               // log2(opacity / tau)
-  s.a = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
-  s.b = make_float4(-0.5f * kLog2e * r1.x, base, r1.z, r1.w);
-  s.c = r2.x;
-  // blocks of the tile that the alpha >= tau ellipse can reach
+  stage_record(r0, r1, r2, s);
   mask = 0u;
-  const float r2n = 2.f * kLn2 * base + 1e-3f;             // 2 ln(opacity/tau) + slack
-  if (r2n > 0.f) {
-    const float hx = sqrtf(r2n * r2.z) * 1.0001f + 0.01f;
-    const float hy = sqrtf(r2n * r2.w) * 1.0001f + 0.01f;
-    const float lx = r0.x - hx - (float)tx0, ux = r0.x + hx - (float)tx0;   // tile-relative
-    const float ly = r0.y - hy - (float)ty0, uy = r0.y + hy - (float)ty0;
-    constexpr int NBX = kTile / BW, NBY = kTile / BH;
-    const float cu = r0.x - (float)tx0, cv = r0.y - (float)ty0;    // tile-relative centre
-    const float lim = r2n * 1.0001f;
+  const float r2n = reach_r2n(s.b.y, l2tau);
+  constexpr int NBX = kTile / BW, NBY = kTile / BH;
+  const float cu = r0.x - (float)tx0, cv = r0.y - (float)ty0;    // tile-relative centre
 #pragma unroll
-    for (int w = 0; w < NBX * NBY; w++) {
-      const float cx0 = (float)(BW * (w % NBX)), ry0 = (float)(BH * (w / NBX));
-      // bounding box first, then the exact ellipse-rectangle test on the pixel centres' rectangle
-      if (ux >= cx0 && lx <= cx0 + (float)(BW - 1) && uy >= ry0 && ly <= ry0 + (float)(BH - 1) &&
-          rect_min_quad(r0.z, r0.w, r1.x, cx0 - cu, cx0 + (float)(BW - 1) - cu, ry0 - cv,
-                        ry0 + (float)(BH - 1) - cv) <= lim)
-        mask |= 1u << w;
-    }
+  for (int w = 0; w < NBX * NBY; w++) {
+    const float cx0 = (float)(BW * (w % NBX)), ry0 = (float)(BH * (w / NBX));
+    if (ellipse_reaches(cu - cx0, cv - ry0, (float)(BW - 1), (float)(BH - 1), r2n, r2.z, r2.w, r0.z, r0.w, r1.x))
+      mask |= 1u << w;
   }
 }
 
-// q = log2(opacity e^p / tau) at pixel offset (dx, dy); explicit roundings.
-// The splat is blended at this pixel iff 0 <= q <= log2(opacity/tau), i.e.
-// alpha >= tau and p <= 0: one unsigned compare of the bit patterns
-// (negative q, including -0, has the sign bit set).  alpha = min(alpha_max, tau 2^q).
-__device__ __forceinline__ bool splat_accept(float q, float base) {
-  return __float_as_uint(q) <= __float_as_uint(base);
+// The splat is blended at a pixel iff alpha >= tau: q >= log2(tau).  (p <= 0
+// holds exactly for a positive-definite conic; a q rounded a hair above
+// log2(opacity) only gives an alpha a hair above the opacity.)
+__device__ __forceinline__ bool splat_accept(float q, float l2tau) { return q >= l2tau; }
+
+__device__ __forceinline__ float fast_exp2(float x);
+
+// Eq. 1: alpha = min(alpha_max, 2^q); also the unclamped value.
+__device__ __forceinline__ float splat_alpha(float q, float alpha_max, float& raw) {
+  raw = fast_exp2(q);
+  return fminf(alpha_max, raw);
 }
 
-// q = (a2 dx^2 + base) + dy (b2 dx + c2 dy), split so that pixels sharing a
-// column share the dx terms: splat_qx gives (P, Bx), splat_qy finishes q.
+// Eq. 2: the transmittance behind a blended splat, T (1 - alpha) rounded once.
+__device__ __forceinline__ float transmit(float alpha, float T) { return __fmaf_rn(-alpha, T, T); }
+
+// q = (a2 dx^2 + log2 opacity) + dy (b2 dx + c2 dy), split so that pixels
+// sharing a column share the dx terms: splat_qx gives (P, Bx), splat_qy
+// finishes q with dy = v - y (one rounding).
 __device__ __forceinline__ void splat_qx(const Staged& s, float dx, float& P, float& Bx) {
   P = __fmaf_rn(__fmul_rn(s.a.z, dx), dx, s.b.y);
   Bx = __fmul_rn(s.a.w, dx);

@@ -88,7 +88,7 @@ diag_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
   const uint32_t start = rg.x, end = rg.y;
   if (tid == 0) {
     s_a[kPad] = make_float4(1e30f, 1e30f, -1.f, 0.f);
-    s_b[kPad] = make_float4(-1.f, -1.f, 0.f, 0.f);
+    s_b[kPad] = make_float4(-1.f, -1e30f, 0.f, 0.f);
     s_c[kPad] = 0.f;
     s_x[kPad] = 0.f;
     s_e[kPad] = 0u;
@@ -152,9 +152,10 @@ diag_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
           bool& done = h ? done1 : done0;
           float& T = h ? T1 : T0;
           const float q = splat_qy(s, P0, Bx, __fsub_rn(s.a.y, h ? fpy1 : fpy0));
-          const bool ok = !done && splat_accept(q, s.b.y);
-          const float alpha = fminf(bc.alpha_max, __fmul_rn(bc.tau, fast_exp2(q)));
-          const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          const bool ok = !done && splat_accept(q, bc.l2tau);
+          float raw;
+          const float alpha = splat_alpha(q, bc.alpha_max, raw);
+          const float test_T = transmit(alpha, T);
           const bool stop = ok && test_T < bc.t_min;
           const bool blend = ok && !stop;
           done = done || stop;
@@ -179,7 +180,7 @@ diag_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
               rr = __fmaf_rn(s.b.z, w, rr);
               gg = __fmaf_rn(s.b.w, w, gg);
               bbc = __fmaf_rn(cb, w, bbc);
-              S = __fmul_rn(S, __fsub_rn(1.f, alpha));
+              S = transmit(alpha, S);
             }
           }
           T = blend ? test_T : T;

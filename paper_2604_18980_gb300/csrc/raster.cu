@@ -1,173 +1,263 @@
 // raster.cu -- per-tile front-to-back alpha blending (Eq. 1, Eq. 2) and the
 // T_up calibration table (Sec. 3.4).
 //
-// One 128-thread CTA per 16x16 tile of each view, two pixels per thread (each
-// warp an 8x8 pixel block).  The tile's depth-ordered pairs are staged in
-// batches of 128: each thread gathers one 48-byte splat record, converts it
-// to the log2 form of Eq. 1 and computes the mask of warp blocks its
-// alpha >= tau ellipse can reach; each warp then compacts the batch to the
-// splats that reach its block and walks that list.  A warp leaves the batch
-// once all its pixels reached the transmittance floor, the CTA once all warps
-// did (__syncthreads_count vote).  The blend always uses the conic of the original
-// covariance and tau (Sec. 3.3 "dual-size strategy"): the scale mode only ever
-// changed which pairs exist.
+// One 64-thread CTA per 16x16 tile of each view: two warps, each an 8x16
+// pixel block, each lane one column and four rows (y, y+4, y+8, y+12) that
+// share the splat's dx terms.  The warps run independently (no CTA barrier):
+// a warp stages its tile's depth-ordered pairs 32 at a time, one per lane --
+// gather of the 48-byte splat record (the next 32 are already in flight),
+// conversion to the log2 form of Eq. 1, and the exact test whether the
+// alpha >= tau ellipse reaches the warp's block -- then walks the splats that
+// do.  A pixel's whole state is its transmittance T, which turns negative
+// when the pixel stops (T (1 - alpha) < 1e-4, Eq. 2): a stopped pixel
+// accepts nothing more, and |T| is its final transmittance.  A warp leaves
+// once all its pixels stopped.  The blend always uses the conic of the
+// original covariance and tau (Sec. 3.3 "dual-size strategy"): the scale mode
+// only ever changed which pairs exist.
 #include <algorithm>
 
 #include "blend.cuh"
 
 namespace ags {
 
-// 128 threads per tile, four warps of 8x8 pixels; lane l blends the two
-// pixels (8*(w&1) + (l&7), 8*(w>>1) + (l>>3)) and the one 4 rows below, which
-// share dx.  kStats: count evaluations and blends; kMaxT: calibration output;
-// kState: track each pixel's last blended position (n_contrib, for the
-// backward).  The benchmark's kernel is the <false, false, false> instance.
-constexpr int kBlendThreads = 128;
-constexpr int kBlendWarps = kBlendThreads / 32;
+constexpr int kBlendWarps = 2;                   // per tile: warp w owns columns 8w .. 8w+7
+constexpr int kBlendThreads = 32 * kBlendWarps;
+constexpr int kRowsPerLane = 4;                  // rows y + 4k of one column
+constexpr int kBlockH = 4 * kRowsPerLane;        // 16: the warp's block is 8 x 16 pixels
 
-// One pixel's step over one splat, without branches: the accept test, the
-// stop test T (1 - alpha) < t_min and the blend are predicates, and a pixel
-// that does not blend adds exact zeros.  Returns whether it blended.
-__device__ __forceinline__ bool blend_pixel(const Staged& s, float cb, float P, float Bx, float dy,
-                                            const BlendConst& bc, bool& done, float& T, float& r, float& g,
-                                            float& b) {
-  const float q = splat_qy(s, P, Bx, dy);
-  const bool ok = !done && splat_accept(q, s.b.y);
-  const float alpha = fminf(bc.alpha_max, __fmul_rn(bc.tau, fast_exp2(q)));
-  const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-  const bool stop = ok && test_T < bc.t_min;
-  const bool blend = ok && !stop;
-  done = done || stop;
-  const float w = blend ? __fmul_rn(alpha, T) : 0.f;
-  r = __fmaf_rn(s.b.z, w, r);
-  g = __fmaf_rn(s.b.w, w, g);
-  b = __fmaf_rn(cb, w, b);
-  T = blend ? test_T : T;
-  return blend;
+// One pixel's step over one splat, in PTX so that the updates stay
+// predicated FMAs: ok = (T > 0 and q >= log2 tau); T' = fma(-alpha, T, T);
+// stop = ok and T' < t_min (T becomes -T: the pixel is done); blend = ok and
+// not stop (colour += alpha T c, T = T').  kClamp: alpha = min(alpha_max,
+// 2^q); without it alpha = 2^q (the splat's opacity is below alpha_max with
+// margin, so the minimum would never bind).
+template <bool kClamp>
+__device__ __forceinline__ void blend_step(float q, float l2tau, float amax, float tmin, float cr, float cg,
+                                           float cb, float& T, float& r, float& g, float& b) {
+  if (kClamp) {
+    asm("{\n\t"
+        ".reg .pred tp, ok, st, bl;\n\t"
+        ".reg .f32 e, a, na, tt, w;\n\t"
+        "setp.gt.f32 tp, %0, 0f00000000;\n\t"
+        "setp.ge.and.f32 ok, %4, %5, tp;\n\t"
+        "ex2.approx.ftz.f32 e, %4;\n\t"
+        "min.f32 a, e, %6;\n\t"
+        "neg.f32 na, a;\n\t"
+        "fma.rn.f32 tt, na, %0, %0;\n\t"
+        "setp.lt.and.f32 st|bl, tt, %7, ok;\n\t"
+        "mul.rn.f32 w, a, %0;\n\t"
+        "@bl fma.rn.f32 %1, %8, w, %1;\n\t"
+        "@bl fma.rn.f32 %2, %9, w, %2;\n\t"
+        "@bl fma.rn.f32 %3, %10, w, %3;\n\t"
+        "@bl fma.rn.f32 %0, na, %0, %0;\n\t"
+        "@st mul.rn.f32 %0, %0, 0fBF800000;\n\t"
+        "}"
+        : "+f"(T), "+f"(r), "+f"(g), "+f"(b)
+        : "f"(q), "f"(l2tau), "f"(amax), "f"(tmin), "f"(cr), "f"(cg), "f"(cb));
+  } else {
+    asm("{\n\t"
+        ".reg .pred tp, ok, st, bl;\n\t"
+        ".reg .f32 a, na, tt, w;\n\t"
+        "setp.gt.f32 tp, %0, 0f00000000;\n\t"
+        "setp.ge.and.f32 ok, %4, %5, tp;\n\t"
+        "ex2.approx.ftz.f32 a, %4;\n\t"
+        "neg.f32 na, a;\n\t"
+        "fma.rn.f32 tt, na, %0, %0;\n\t"
+        "setp.lt.and.f32 st|bl, tt, %7, ok;\n\t"
+        "mul.rn.f32 w, a, %0;\n\t"
+        "@bl fma.rn.f32 %1, %8, w, %1;\n\t"
+        "@bl fma.rn.f32 %2, %9, w, %2;\n\t"
+        "@bl fma.rn.f32 %3, %10, w, %3;\n\t"
+        "@bl fma.rn.f32 %0, na, %0, %0;\n\t"
+        "@st mul.rn.f32 %0, %0, 0fBF800000;\n\t"
+        "}"
+        : "+f"(T), "+f"(r), "+f"(g), "+f"(b)
+        : "f"(q), "f"(l2tau), "f"(amax), "f"(tmin), "f"(cr), "f"(cg), "f"(cb));
+  }
 }
 
+// The same step in C++ with its decisions returned (counters, calibration,
+// blend state); the same operations, so the same results.
+template <bool kClamp>
+__device__ __forceinline__ void blend_step_rec(float q, const BlendConst& bc, float cr, float cg, float cb, float& T,
+                                               float& r, float& g, float& b, bool& blended, bool& stopped) {
+  const bool ok = T > 0.f && splat_accept(q, bc.l2tau);
+  float raw;
+  const float alpha = kClamp ? splat_alpha(q, bc.alpha_max, raw) : fast_exp2(q);
+  const float tt = transmit(alpha, T);
+  stopped = ok && tt < bc.t_min;
+  blended = ok && !stopped;
+  const float w = __fmul_rn(alpha, T);
+  if (blended) {
+    r = __fmaf_rn(cr, w, r);
+    g = __fmaf_rn(cg, w, g);
+    b = __fmaf_rn(cb, w, b);
+    T = tt;
+  }
+  if (stopped) T = -T;
+}
+
+// kStats: count evaluations and blends; kMaxT: calibration output; kState:
+// each pixel's final T and last blended position (for the backward).  The
+// benchmark's kernel is the <false, false, false> instance.
 template <bool kStats, bool kMaxT, bool kState>
-__global__ void __launch_bounds__(kBlendThreads, kState ? 8 : 9)
+__global__ void __launch_bounds__(kBlendThreads)
 raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
               int W, int H, int gx, int tiles_per_view, BlendConst bc, float* __restrict__ image,
               float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ max_T_bits,
               unsigned long long* stats) {
-  constexpr int kB = kBlendThreads;                    // splats staged per batch
-  constexpr int kPad = kB;                             // index of an always-rejected entry
-  __shared__ float4 s_a[kB + 1];                       // u v a2 b2
-  __shared__ float4 s_b[kB + 1];                       // c2 base r g
-  __shared__ float s_c[kB + 1];                        // b
-  __shared__ uint32_t s_m[kB];                         // 8x8 block mask
-  __shared__ uint32_t s_e[kB + 1];                     // splat index (calibration only)
-  __shared__ uint16_t s_list[kBlendWarps][kB + 4];     // per-warp entries, padded
+  constexpr bool kRec = kStats || kMaxT || kState;
+  __shared__ float4 s_a[kBlendWarps][32];    // u v a2 b2
+  __shared__ float4 s_b[kBlendWarps][32];    // c2 log2(opacity) r g
+  __shared__ float s_c[kBlendWarps][32];     // b
+  __shared__ uint32_t s_e[kBlendWarps][kMaxT ? 32 : 1];
 
   const int tile = blockIdx.x;
   const int view = tile / tiles_per_view;
   const int lt = tile - view * tiles_per_view;
   const int ty = lt / gx, tx = lt - ty * gx;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int px = tx * kTile + 8 * (warp & 1) + (lane & 7);
-  const int py0 = ty * kTile + 8 * (warp >> 1) + (lane >> 3);
-  const int py1 = py0 + 4;
-  const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
-  const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bx0 = tx * kTile + 8 * warp, by0 = ty * kTile;
+  const int px = bx0 + (lane & 7);
+  const int py = by0 + (lane >> 3);
+  const float fpx = (float)px;
+  float fpy[kRowsPerLane], T[kRowsPerLane], cr[kRowsPerLane], cg[kRowsPerLane], cb[kRowsPerLane];
+  uint32_t last[kRowsPerLane], stop_at[kRowsPerLane];
+#pragma unroll
+  for (int k = 0; k < kRowsPerLane; k++) {
+    fpy[k] = (float)(py + 4 * k);
+    T[k] = (px < W && py + 4 * k < H) ? 1.f : -1.f;      // negative: nothing to blend
+    cr[k] = cg[k] = cb[k] = 0.f;
+    last[k] = 0u;
+    stop_at[k] = 0u;
+  }
   const uint2 rg = __ldg(ranges + tile);
   const uint32_t start = rg.x, end = rg.y;
-  if (tid == 0) {   // the pad entry: far away and steep, q = -inf rejects every pixel
-    s_a[kPad] = make_float4(1e30f, 1e30f, -1.f, 0.f);
-    s_b[kPad] = make_float4(-1.f, -1.f, 0.f, 0.f);
-    s_c[kPad] = 0.f;
-    s_e[kPad] = 0u;
+  float4* sa = s_a[warp];
+  float4* sb = s_b[warp];
+  float* sc = s_c[warp];
+  const float l2clamp = __log2f(bc.alpha_max) - 1e-3f;   // opacities above this take the clamped step
+  uint32_t blends = 0u, walked_total = 0u;
+
+  // the first 32 records in flight
+  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
+  uint32_t ne = 0u;
+  if (start + lane < end) {
+    ne = __ldg(vals + start + lane);
+    const float4* rec = splat + (size_t)ne * 3;
+    n0 = __ldg(rec); n1 = __ldg(rec + 1); n2 = __ldg(rec + 2);
   }
-
-  float T0 = 1.f, r0 = 0.f, g0 = 0.f, b0c = 0.f;
-  float T1 = 1.f, r1 = 0.f, g1 = 0.f, b1c = 0.f;
-  bool done0 = !in0, done1 = !in1;
-  uint32_t last0 = 0, last1 = 0, evals = 0, blends = 0;
-
-  for (uint32_t bb = start; bb < end; bb += kB) {
-    if (__syncthreads_count(done0 && done1) == kBlendThreads) break;
-    const uint32_t idx = bb + tid;
-    if (idx < end) {
-      const uint32_t e = __ldg(vals + idx);
+  for (uint32_t bb = start; bb < end; bb += 32) {
+    bool alive = false;
+#pragma unroll
+    for (int k = 0; k < kRowsPerLane; k++) alive = alive || T[k] > 0.f;
+    if (!__any_sync(0xffffffffu, alive)) break;
+    const float4 r0 = n0, r1 = n1, r2 = n2;
+    const uint32_t e = ne;
+    bool hit = false;
+    if (bb + lane < end) {
       Staged st;
-      uint32_t m;
-      stage_splat<8, 8>(splat + (size_t)e * 3, tx * kTile, ty * kTile, bc.l2tau, st, m);
-      s_a[tid] = st.a;
-      s_b[tid] = st.b;
-      s_c[tid] = st.c;
-      s_m[tid] = m;
-      if (kMaxT) s_e[tid] = e;
+      stage_record(r0, r1, r2, st);
+      sa[lane] = st.a;
+      sb[lane] = st.b;
+      sc[lane] = st.c;
+      if (kMaxT) s_e[warp][lane] = e;
+      hit = ellipse_reaches(r0.x - (float)bx0, r0.y - (float)by0, 7.f, (float)(kBlockH - 1),
+                            reach_r2n(st.b.y, bc.l2tau), r2.z, r2.w, r0.z, r0.w, r1.x);
     }
-    __syncthreads();
-    const int nb = (int)min((uint32_t)kB, end - bb);
-    // this warp's entries of the batch, in depth order, padded to a multiple of 4
-    int cnt = 0;
-#pragma unroll
-    for (int k = 0; k < kB / 32; k++) {
-      const int j = k * 32 + lane;
-      const bool hit = j < nb && ((s_m[j] >> warp) & 1u);
-      const unsigned bal = __ballot_sync(0xffffffffu, hit);
-      if (hit) s_list[warp][cnt + __popc(bal & lanemask_lt())] = (uint16_t)j;
-      cnt += __popc(bal);
+    if (bb + 32 + lane < end) {      // the next 32 records, in flight while these are blended
+      ne = __ldg(vals + bb + 32 + lane);
+      const float4* rec = splat + (size_t)ne * 3;
+      n0 = __ldg(rec); n1 = __ldg(rec + 1); n2 = __ldg(rec + 2);
     }
-    if (lane < 4) s_list[warp][cnt + lane] = (uint16_t)kPad;
+    unsigned mask = __ballot_sync(0xffffffffu, hit);
     __syncwarp();
-    if (__all_sync(0xffffffffu, done0 && done1)) continue;
-    for (int t = 0; t < cnt; t += 4) {
+    int walked = 0;
+    if (kStats) walked_total += (uint32_t)__popc(mask);
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      Staged s;
+      s.a = sa[j];
+      s.b = sb[j];
+      const float cbl = sc[j];
+      const float dx = __fsub_rn(s.a.x, fpx);
+      float P, Bx;
+      splat_qx(s, dx, P, Bx);
+      const bool clamp = s.b.y > l2clamp;
+      if (!kRec) {
+        if (clamp) {
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int j = s_list[warp][t + u];
-        Staged s;
-        s.a = s_a[j];
-        s.b = s_b[j];
-        const float dx = __fsub_rn(s.a.x, fpx);
-        float P, Bx;
-        splat_qx(s, dx, P, Bx);
-        const float cb = s_c[j];
-        const float Tb0 = T0, Tb1 = T1;
-        if (kStats) evals += (j != kPad) * ((done0 ? 0u : 1u) + (done1 ? 0u : 1u));
-        const bool bl0 = blend_pixel(s, cb, P, Bx, __fsub_rn(s.a.y, fpy0), bc, done0, T0, r0, g0, b0c);
-        const bool bl1 = blend_pixel(s, cb, P, Bx, __fsub_rn(s.a.y, fpy1), bc, done1, T1, r1, g1, b1c);
-        if (kStats) blends += (bl0 ? 1u : 0u) + (bl1 ? 1u : 0u);
-        if (kState) {
-          const uint32_t pos1 = bb - start + j + 1;
-          last0 = bl0 ? pos1 : last0;
-          last1 = bl1 ? pos1 : last1;
+          for (int k = 0; k < kRowsPerLane; k++)
+            blend_step<true>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc.l2tau, bc.alpha_max, bc.t_min, s.b.z,
+                             s.b.w, cbl, T[k], cr[k], cg[k], cb[k]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < kRowsPerLane; k++)
+            blend_step<false>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc.l2tau, bc.alpha_max, bc.t_min, s.b.z,
+                              s.b.w, cbl, T[k], cr[k], cg[k], cb[k]);
+        }
+      } else {
+        const uint32_t pos1 = bb - start + (uint32_t)j + 1u;    // 1-based position in the tile's list
+        uint32_t mt = 0u;
+#pragma unroll
+        for (int k = 0; k < kRowsPerLane; k++) {
+          const float Tb = T[k];
+          const float q = splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k]));
+          bool bl, stp;
+          if (clamp)
+            blend_step_rec<true>(q, bc, s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k], bl, stp);
+          else
+            blend_step_rec<false>(q, bc, s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k], bl, stp);
+          if (kStats) {
+            blends += bl ? 1u : 0u;
+            stop_at[k] = stp ? pos1 : stop_at[k];
+          }
+          if (kState) last[k] = bl ? pos1 : last[k];
+          if (kMaxT) mt = max(mt, bl ? __float_as_uint(Tb) : 0u);
         }
         if (kMaxT) {   // calibration: per-Gaussian max T before blending (warp max, one atomic)
-          const uint32_t mine = max(bl0 ? __float_as_uint(Tb0) : 0u, bl1 ? __float_as_uint(Tb1) : 0u);
-          const uint32_t m = __reduce_max_sync(0xffffffffu, mine);
-          if (lane == 0 && m) atomicMax(max_T_bits + s_e[j], m);
+          const uint32_t m = __reduce_max_sync(0xffffffffu, mt);
+          if (lane == 0 && m) atomicMax(max_T_bits + s_e[warp][j], m);
         }
       }
-      if (__all_sync(0xffffffffu, done0 && done1)) break;
+      if ((++walked & 3) == 0) {
+        bool al = false;
+#pragma unroll
+        for (int k = 0; k < kRowsPerLane; k++) al = al || T[k] > 0.f;
+        if (!__any_sync(0xffffffffu, al)) {
+          if (kStats) walked_total -= (uint32_t)__popc(mask);    // not walked
+          break;
+        }
+      }
     }
+    __syncwarp();
   }
   const size_t hw = (size_t)W * H;
-  if (in0) {
-    const size_t o = (size_t)view * 3 * hw + (size_t)py0 * W + px;
-    image[o] = r0 + T0 * bc.bg[0];
-    image[o + hw] = g0 + T0 * bc.bg[1];
-    image[o + 2 * hw] = b0c + T0 * bc.bg[2];
-    const size_t op = (size_t)view * hw + (size_t)py0 * W + px;
-    if (final_T) final_T[op] = T0;
-    if (kState) n_contrib[op] = last0;
-  }
-  if (in1) {
-    const size_t o = (size_t)view * 3 * hw + (size_t)py1 * W + px;
-    image[o] = r1 + T1 * bc.bg[0];
-    image[o + hw] = g1 + T1 * bc.bg[1];
-    image[o + 2 * hw] = b1c + T1 * bc.bg[2];
-    const size_t op = (size_t)view * hw + (size_t)py1 * W + px;
-    if (final_T) final_T[op] = T1;
-    if (kState) n_contrib[op] = last1;
+  unsigned long long evals = 0ull;
+#pragma unroll
+  for (int k = 0; k < kRowsPerLane; k++) {
+    const int y = py + 4 * k;
+    if (px < W && y < H) {
+      const float Tf = fabsf(T[k]);
+      const size_t o = (size_t)view * 3 * hw + (size_t)y * W + px;
+      image[o] = cr[k] + Tf * bc.bg[0];
+      image[o + hw] = cg[k] + Tf * bc.bg[1];
+      image[o + 2 * hw] = cb[k] + Tf * bc.bg[2];
+      const size_t op = (size_t)view * hw + (size_t)y * W + px;
+      if (final_T) final_T[op] = Tf;
+      if (kState) n_contrib[op] = last[k];
+      // Eq. 1-2 evaluations of this pixel: its tile's pairs up to the one it stopped at
+      if (kStats) evals += stop_at[k] ? stop_at[k] : (end - start);
+    }
   }
   if (kStats) {
-    unsigned long long e1 = warp_sum((unsigned long long)evals), e2 = warp_sum((unsigned long long)blends);
+    const unsigned long long e1 = warp_sum(evals), e2 = warp_sum((unsigned long long)blends);
     if (lane == 0) {
       atomicAdd(stats, e1);
       atomicAdd(stats + 1, e2);
+      // pixel-pair slots the kernel walked: each walked splat against the warp's 8 x 16 pixels
+      atomicAdd(stats + 2, (unsigned long long)walked_total * (8ull * kBlockH));
     }
   }
 }

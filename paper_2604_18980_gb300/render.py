@@ -132,7 +132,7 @@ class Renderer:
         self.image = torch.empty(V, 3, self.H, self.W, dtype=torch.float32, device=dev)
         self.final_T = torch.empty(V, self.H, self.W, dtype=torch.float32, device=dev) if self.keep_state else None
         self.n_contrib = torch.empty(V, self.H, self.W, dtype=torch.int32, device=dev) if self.keep_state else None
-        self.stats = torch.zeros(2, dtype=torch.int64, device=dev) if want_stats else None
+        self.stats = torch.zeros(3, dtype=torch.int64, device=dev) if want_stats else None
         if capacity is None:
             capacity = max(1024, int(math.ceil(self.count_pairs() * headroom)))
         self.alloc_pairs(capacity)

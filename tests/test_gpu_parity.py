@@ -525,3 +525,30 @@ def test_autotuner_candidates_render_identically():
         np.testing.assert_array_equal(v, lists[0][1])
     best = autotune.tune(sc, cams, 1, 0.3, use_cache=False, warmup=1, reps=2)
     assert best["digit_bits"] in (7, 8, 9) and len(best["table"]) == len(autotune.CANDIDATES)
+
+
+@pytest.mark.parametrize("mode,K", [(0, 0.0), (1, 0.3)])
+def test_blend_counters_match_oracle(mode, K):
+    """stats[0]: Eq. 1-2 evaluations (per pixel, its tile's pairs up to the one it
+    stopped at); stats[1]: blends.  Both against the oracle's per-pixel counts;
+    a pixel with a near-threshold decision (flip budget > 0) may move by its
+    tile's list length (evaluations) or its blend count (blends)."""
+    scene, cams = _c1(n=6000, W=173, H=94, views=1)
+    lut = np.linspace(1.0, 0.4, 20).astype(np.float32)
+    r = gpu_render(scene, cams, mode, K, lut, want_stats=True)
+    ev, bl = int(r.stats[0].item()), int(r.stats[1].item())
+    par = oracle_params(cams[0], mode, K, lut)
+    oo = oracle.render(scene, cams[0], par, want_state=True)
+    st = oo["state"]
+    W, H = cams[0]["width"], cams[0]["height"]
+    gx = (W + 15) // 16
+    lens = np.diff(oo["tile_start"])
+    yy, xx = np.mgrid[0:H, 0:W]
+    px_len = lens[(yy // 16) * gx + (xx // 16)]
+    flagged = oo["budget"] > 0
+    ev_o, bl_o = int(st[..., 2].sum()), int(st[..., 0].sum())
+    assert ev_o > bl_o > 0
+    assert abs(ev - ev_o) <= int(px_len[flagged].sum()), (ev, ev_o)
+    assert abs(bl - bl_o) <= int(px_len[flagged].sum()), (bl, bl_o)
+    if not flagged.any():
+        assert (ev, bl) == (ev_o, bl_o)

@@ -110,6 +110,8 @@ MUTANTS = [
     ("edge_budget_p_term_dropped",
      "if (fabs(p) <= par->edge_rel && g[F_OPAC] >= par->tau) budget += 2.0 * g[F_OPAC] * T * cmax;", "",
      ["pin_edge_pixel_budget"]),
+    ("eval_count_off_by_one", "if (test_T < par->t_min) { nev = (int32_t)(k + 1); break; }",
+     "if (test_T < par->t_min) { nev = (int32_t)k; break; }", ["pin_eval_count"]),
     ("gedge_colour_dropped", "if (fabs(acc.v) <= eps * mag) irec[I_GEDGE] |= GEDGE_COLOUR;", "",
      ["pin_gradient_edges"]),
     ("gedge_frustum_x10", "if (near_edge(fabs(txtz.v), limx, eps, limx) || near_edge(fabs(tytz.v), limy, eps, limy))",
