@@ -36,8 +36,10 @@
  * Conventions (all entry points):
  *  - Every pointer is a DEVICE pointer owned by the caller unless it is marked
  *    "host".  The library allocates no memory and keeps no mutable global
- *    state; scratch memory ("workspace") is passed in by the caller, sized by
- *    the matching *_workspace_bytes() call.
+ *    state -- with one exception, ags_emit_pairs_noalloc's static device
+ *    scratch array and its cached device address; scratch memory
+ *    ("workspace") is passed in by the caller, sized by the matching
+ *    *_workspace_bytes() call.
  *  - `stream` is a cudaStream_t passed as void*.  Every call only enqueues
  *    work on that stream and returns without synchronising, so a sequence of
  *    calls can be captured in a CUDA graph.
@@ -218,6 +220,11 @@ size_t ags_emit_tile_workspace_bytes(int64_t n, int32_t views);
 #define AGS_EMIT_SINGLE_PASS 1  /* ags_emit_tile_pairs flag: one fused scan-and-emit pass over
                                    partitions of Gaussian-views (faster when the tile counts
                                    are spread evenly along the order) */
+#define AGS_EMIT_TEST_STALL 256 /* emission flag, for testing the bounded wait only: partition 1
+                                   of the look-back never publishes its sums, so the partitions
+                                   after it give up after 2 ms (instead of 200 ms), record
+                                   AGS_ERR_TIMEOUT with detail 1 (emission) and finish with every
+                                   store inside capacity; the pairs are then meaningless */
 #define AGS_EMIT_VIEW_SHIFT 4   /* ags_emit_tile_pairs flag: key = (view << tile_bits) | tile,
                                    tile_bits = the bits of tiles_per_view - 1 (at least 1), for
                                    ags_sort_tiles; with an `order` that lists each view's
@@ -267,11 +274,13 @@ int64_t ags_emit_pairs_noalloc_max_gaussians(void);
  * the library until the process exits; views*n above
  * ags_emit_pairs_noalloc_max_gaussians() is rejected with
  * AGS_ERR_INVALID_ARG.  The first call on a device looks up that array's
- * device address (with the device current) and caches it, so make the first
- * call on each device before any stream capture.  Every call zeroes the part
- * of the array it uses on `stream`; calls whose work overlaps on the GPU (on
- * different streams) share the array and race: serialise them.  No call
- * allocates or frees memory. */
+ * device address (with the device current) and caches it per CUDA context, so
+ * make the first call on each device before any stream capture, and again
+ * first after a device reset (a reset destroys the context and its copy of the
+ * array; the next call sees a new context and looks the address up anew).
+ * Every call zeroes the part of the array it uses on `stream`; calls whose
+ * work overlaps on the GPU (on different streams) share the array and race:
+ * serialise them.  No call allocates or frees memory. */
 ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t n, int32_t views,
                                   const ags_camera* cams, const uint32_t* order,
                                   uint64_t* keys, uint32_t* vals, int64_t capacity,
@@ -284,6 +293,11 @@ size_t ags_sort_workspace_bytes(int64_t capacity);
 #define AGS_SORT_DISCARD_KEYS 2      /* sort flag: the last digit pass writes no keys, so the
                                         key buffer that would hold the result is left
                                         unspecified (values and ranges only) */
+#define AGS_SORT_TEST_STALL 256      /* sort flag, for testing the bounded wait only: partition 1
+                                        of each digit pass's look-back never publishes, so the
+                                        partitions after it give up after 2 ms, record
+                                        AGS_ERR_TIMEOUT with detail 2 (sort) and write only inside
+                                        the count; the order is then meaningless */
 #define AGS_SORT_RANK_OR 4           /* sort flag: rank a warp's equal digits with shared-memory
                                         atomic-OR peer masks instead of warp match; same result,
                                         faster when a warp's keys mostly carry distinct digits

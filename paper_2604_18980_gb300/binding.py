@@ -246,6 +246,7 @@ def ags_emit_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, w
 
 AGS_EMIT_SINGLE_PASS = 1
 AGS_EMIT_VIEW_SHIFT = 4
+AGS_EMIT_TEST_STALL = 256     # tests only: a look-back partition that never publishes
 
 
 def ags_emit_tile_pairs(proj, n, cams, keys, vals, capacity, d_num_pairs, d_status, ws, order=None,
@@ -293,6 +294,7 @@ def ags_sort_workspace_bytes(capacity: int) -> int:
 AGS_SORT_IDENTITY_VALUES = 1
 AGS_SORT_DISCARD_KEYS = 2
 AGS_SORT_RANK_OR = 4
+AGS_SORT_TEST_STALL = 256     # tests only: a look-back partition that never publishes
 
 
 def ags_sort(keys, vals, keys_alt, vals_alt, d_num_pairs, capacity, begin_bit, end_bit, digit_bits, ranges,

@@ -9,9 +9,12 @@ from __future__ import annotations
 
 import concurrent.futures
 import glob
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
+import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -37,20 +40,44 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+STAMP = LIB + ".src-sha256"
+_reported = False     # "up to date" is logged once per process
+
+
+def source_digest(extra_flags=None) -> str:
+    """SHA-256 over every source and header, the flags, the architecture and
+    the host machine: a library whose stamp matches was built from exactly
+    these sources here (a copied or stale binary has no matching stamp)."""
+    h = hashlib.sha256()
+    for p in sorted(_deps()):
+        h.update(os.path.relpath(p, HERE).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(ARCH + FLAGS + list(extra_flags or [])).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
+def up_to_date(extra_flags=None) -> bool:
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(p) <= t for p in _deps())
+    with open(STAMP) as f:
+        return f.read().strip() == source_digest(extra_flags)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile and link libags.so; returns its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=None, quiet: bool = False) -> str:
+    """Compile and link libags.so unless the stamped build matches the sources;
+    returns its path and logs which of the two happened (stderr)."""
+    global _reported
+    if not force and up_to_date(extra_flags):
+        if not quiet and not _reported:
+            print("libags: up to date (%s)" % LIB, file=sys.stderr)
+            _reported = True
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     flags = FLAGS + list(extra_flags or [])
+    digest = source_digest(extra_flags)
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
@@ -70,11 +97,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP + ".tmp", "w") as f:
+        f.write(digest)
+    os.replace(STAMP + ".tmp", STAMP)
+    if not quiet:
+        print("libags: compiled %d translation units (%s)" % (len(objs), LIB), file=sys.stderr)
     return LIB
 
 
 if __name__ == "__main__":
-    import sys
-
     print(build(force="--force" in sys.argv, verbose=True,
                 extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))

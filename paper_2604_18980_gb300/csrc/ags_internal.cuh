@@ -13,6 +13,17 @@ constexpr int kTile = AGS_TILE;
 constexpr int kSplatFloats = 12;            // u v A B | C opacity r g | b Th Sxx Syy
 constexpr uint8_t kFlagCulled = 0x80;
 constexpr uint64_t kWaitLimitNs = 200ull * 1000ull * 1000ull;   // bounded spin: 200 ms
+constexpr uint64_t kTestWaitLimitNs = 2ull * 1000ull * 1000ull;  // with a test stall: 2 ms
+
+// Look-back wait settings of one launch: the partition that never publishes
+// its flags (test stall; 0xffffffff: none) and the spin limit.
+struct WaitHook {
+  uint32_t withhold;
+  uint64_t limit_ns;
+};
+inline WaitHook wait_hook(bool test_stall) {
+  return test_stall ? WaitHook{1u, kTestWaitLimitNs} : WaitHook{0xffffffffu, kWaitLimitNs};
+}
 
 // Stage ids reported as the detail word of AGS_ERR_TIMEOUT.
 enum : int64_t { kStageEmit = 1, kStageSort = 2, kStageVisible = 3 };

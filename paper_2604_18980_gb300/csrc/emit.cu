@@ -58,7 +58,7 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
             K* __restrict__ keys,
             uint32_t* __restrict__ vals, int64_t capacity, int64_t* d_num_pairs, int64_t* status,
             uint64_t* part_status, uint32_t* counter, uint4* __restrict__ recs,
-            uint32_t* __restrict__ chunk_start, EllipseSrc ell) {
+            uint32_t* __restrict__ chunk_start, EllipseSrc ell, WaitHook hook) {
   __shared__ uint32_t s_base[kEmitPart];   // key high word of the rectangle's first tile
   __shared__ uint32_t s_w[kEmitPart];      // rectangle width in tiles
   __shared__ uint32_t s_dbits[kEmitPart];  // depth bits
@@ -135,10 +135,11 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
   // 3. decoupled look-back (warp 0) for the partition's global offset
   if (warp == 0) {
     uint64_t excl = 0;
+    const bool publish = part != hook.withhold;
     if (part == 0) {
-      if (lane == 0) st_relaxed_u64(part_status, kInc | (uint64_t)agg);
+      if (lane == 0 && publish) st_relaxed_u64(part_status, kInc | (uint64_t)agg);
     } else {
-      if (lane == 0) st_relaxed_u64(part_status + part, kAgg | (uint64_t)agg);
+      if (lane == 0 && publish) st_relaxed_u64(part_status + part, kAgg | (uint64_t)agg);
       int64_t top = (int64_t)part - 1;
       const uint64_t t0 = globaltimer_ns();
       bool timed_out = false;
@@ -151,7 +152,7 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
         int first_inc = inc_mask ? __ffs(inc_mask) - 1 : 32;
         unsigned upto = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
         if ((inv_mask & upto) && !timed_out) {
-          if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          if (globaltimer_ns() - t0 > hook.limit_ns) {
             timed_out = true;
             if (lane == 0) set_status(status, AGS_ERR_TIMEOUT, kStageEmit);
           }
@@ -162,7 +163,7 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
         if (first_inc < 32 || timed_out) break;
         top -= 32;
       }
-      if (lane == 0) st_relaxed_u64(part_status + part, kInc | ((excl + agg) & kValMask));
+      if (lane == 0 && publish) st_relaxed_u64(part_status + part, kInc | ((excl + agg) & kValMask));
     }
     if (lane == 0) s_prefix = excl;
   }
@@ -498,7 +499,7 @@ static ags_status ellipse_src(const ags_projected* proj, const CamBatch& cb, int
 }  // namespace ags
 
 extern "C" size_t ags_emit_workspace_bytes(int64_t n, int32_t views) {
-  if (n < 0 || views < 1) return 0;
+  if (n < 0 || views < 1 || n > (((int64_t)1 << 32) - 1) / views) return 0;
   return 256 + 8 * ags::emit_parts(n * (int64_t)views);
 }
 
@@ -512,12 +513,12 @@ extern "C" ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32
   CamBatch cb;
   ags_status s = build_cams(cams, views, &cb);
   if (s != AGS_OK) return s;
+  if (n > (((int64_t)1 << 32) - 1) / views) return AGS_ERR_INVALID_ARG;   // before multiplying
   const int64_t total = n * (int64_t)views;
-  if (total >= ((int64_t)1 << 32)) return AGS_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (flags & ~(AGS_EMIT_ELLIPSE | AGS_EMIT_TEST_STALL)) return AGS_ERR_INVALID_ARG;
   if (total == 0) return launch_status(cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st));
   if (!proj->rect || !proj->depth || (capacity > 0 && (!keys || !vals))) return AGS_ERR_INVALID_ARG;
-  if (flags & ~AGS_EMIT_ELLIPSE) return AGS_ERR_INVALID_ARG;
   EllipseSrc ell;
   s = ellipse_src(proj, cb, flags, &ell);
   if (s != AGS_OK) return s;
@@ -531,12 +532,13 @@ extern "C" ags_status ags_emit_pairs(const ags_projected* proj, int64_t n, int32
   uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
   emit_kernel<uint64_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
       reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, nullptr, (uint32_t)n, tiles_per_view,
-      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr, ell);
+      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr, ell,
+      wait_hook(flags & AGS_EMIT_TEST_STALL));
   return launch_status(cudaGetLastError());
 }
 
 extern "C" size_t ags_emit_tile_workspace_bytes(int64_t n, int32_t views) {
-  if (n < 0 || views < 1) return 0;
+  if (n < 0 || views < 1 || n > (((int64_t)1 << 32) - 1) / views) return 0;
   const int64_t total = n * (int64_t)views;
   return (256 + 8 * ags::emit_parts(total) + 15) / 16 * 16 + 16 * (size_t)total + 4 * (size_t)ags::kTileChunksMax;
 }
@@ -552,12 +554,13 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
   CamBatch cb;
   ags_status s = build_cams(cams, views, &cb);
   if (s != AGS_OK) return s;
+  if (n > (((int64_t)1 << 32) - 1) / views) return AGS_ERR_INVALID_ARG;   // before multiplying
   const int64_t total = n * (int64_t)views;
-  if (total >= ((int64_t)1 << 32)) return AGS_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (flags & ~(AGS_EMIT_SINGLE_PASS | AGS_EMIT_ELLIPSE | AGS_EMIT_VIEW_SHIFT | AGS_EMIT_TEST_STALL))
+    return AGS_ERR_INVALID_ARG;
   if (total == 0) return launch_status(cudaMemsetAsync(d_num_pairs, 0, sizeof(int64_t), st));
   if (!proj->rect || (capacity > 0 && (!keys || !vals))) return AGS_ERR_INVALID_ARG;
-  if (flags & ~(AGS_EMIT_SINGLE_PASS | AGS_EMIT_ELLIPSE | AGS_EMIT_VIEW_SHIFT)) return AGS_ERR_INVALID_ARG;
   EllipseSrc ell;
   s = ellipse_src(proj, cb, flags, &ell);
   if (s != AGS_OK) return s;
@@ -582,14 +585,14 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
     emit_kernel<uint32_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
         reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, d_entries, (uint32_t)n,
         tiles_per_view, (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter,
-        nullptr, nullptr, ell);
+        nullptr, nullptr, ell, wait_hook(flags & AGS_EMIT_TEST_STALL));
     return launch_status(cudaGetLastError());
   }
   // phase 1: per-entry records and the pair count
   emit_kernel<uint32_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
       reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, d_entries, (uint32_t)n, tiles_per_view,
       (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, recs, chunk_start,
-      ell);
+      ell, wait_hook(flags & AGS_EMIT_TEST_STALL));
   e = cudaGetLastError();
   if (e != cudaSuccess || capacity == 0) return launch_status(e);
   // phase 2: the pairs, in blocks of kTileChunk (grid-stride over the device count)
@@ -614,7 +617,9 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
 // The look-back state lives in a library-owned device array instead of a
 // caller workspace.  In host code `g_emit_scratch` names a host-side stand-in,
 // not a device address, so the device address is looked up with
-// cudaGetSymbolAddress once per device (with that device current) and cached.
+// cudaGetSymbolAddress (with the device current) and cached per CUDA context:
+// a device reset creates a new context, whose id differs, so the address is
+// looked up again there instead of reusing the old context's.
 // ---------------------------------------------------------------------------
 namespace ags {
 
@@ -623,17 +628,49 @@ constexpr size_t kNoAllocScratchBytes = 256 + 8 * (size_t)(kNoAllocMaxGaussianVi
 
 static __device__ __align__(256) unsigned char g_emit_scratch[kNoAllocScratchBytes];
 
+// The current context's unique id, through the driver entry points the
+// runtime exposes (no link against the driver library).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+static bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    resolved = true;
+  }
+  void* ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
 static std::mutex g_scratch_mutex;
-static void* g_scratch_ptr[256];          // device address per CUDA device ordinal (nullptr: not set up)
+static void* g_scratch_ptr[256];                  // device address per device ordinal (nullptr: not set up)
+static unsigned long long g_scratch_ctx[256];     // the context it was looked up in
 
 static ags_status scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return AGS_ERR_CUDA;
+  unsigned long long ctx = 0;
+  const bool have_ctx = current_context_id(&ctx);   // false before the runtime set up any context
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
+  if (!have_ctx || !g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
+    void* p = nullptr;   // the lookup also sets up the device's primary context if needed
     if (cudaGetSymbolAddress(&p, g_emit_scratch) != cudaSuccess || !p) return AGS_ERR_CUDA;
+    if (!have_ctx && !current_context_id(&ctx)) return AGS_ERR_CUDA;
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return AGS_OK;
@@ -653,8 +690,8 @@ extern "C" ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t 
   CamBatch cb;
   ags_status s = build_cams(cams, views, &cb);
   if (s != AGS_OK) return s;
+  if (n > kNoAllocMaxGaussianViews / views) return AGS_ERR_INVALID_ARG;   // beyond the static scratch
   const int64_t total = n * (int64_t)views;
-  if (total > kNoAllocMaxGaussianViews) return AGS_ERR_INVALID_ARG;   // beyond the static scratch
   cudaStream_t st = (cudaStream_t)stream;
   void* ws = nullptr;
   s = scratch_address(&ws);
@@ -672,6 +709,6 @@ extern "C" ags_status ags_emit_pairs_noalloc(const ags_projected* proj, int64_t 
   emit_kernel<uint64_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
       reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, nullptr, (uint32_t)n, tiles_per_view,
       (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, nullptr, nullptr,
-      EllipseSrc{nullptr, nullptr, cb.c[0].W, cb.c[0].H});
+      EllipseSrc{nullptr, nullptr, cb.c[0].W, cb.c[0].H}, wait_hook(false));
   return launch_status(cudaGetLastError());
 }

@@ -270,12 +270,12 @@ extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* c
   if (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->sh) return AGS_ERR_INVALID_ARG;
   if (!out->splat || !out->depth || !out->rect || !out->flags) return AGS_ERR_INVALID_ARG;
   if (((uintptr_t)out->splat & 15u) || ((uintptr_t)out->rect & 7u)) return AGS_ERR_INVALID_ARG;
+  if (dp.tile_test == AGS_TILE_ELLIPSE && !out->tiles_touched) return AGS_ERR_INVALID_ARG;
   PreIn in{g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
   PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags, out->depth_key};
   preprocess_kernel<<<(unsigned)((g->n + kPreThreads - 1) / kPreThreads), kPreThreads, 0, (cudaStream_t)stream>>>(
       in, g->n, views, cb, dp, po, d_status);
   if (dp.tile_test == AGS_TILE_ELLIPSE) {
-    if (!out->tiles_touched) return AGS_ERR_INVALID_ARG;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return launch_status(e);
     const int64_t total = (int64_t)views * g->n;

@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 3 : 2)
 onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
                 uint32_t* __restrict__ vout, const int64_t* count_ptr, int64_t capacity, int identity, int shift,
                 uint32_t mask, int rank_or, const uint32_t* __restrict__ gprefix, uint32_t* lookback,
-                uint32_t* counter, int64_t* status, uint32_t* ranges, uint32_t num_ranges, RangeMap rmap) {
+                uint32_t* counter, int64_t* status, uint32_t* ranges, uint32_t num_ranges, RangeMap rmap,
+                WaitHook hook) {
   using Sm = SortSmem<RADIX, K>;
   constexpr int kWarps = Sm::kWarps;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,7 +263,7 @@ onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* 
       S.u.r.warp_hist[w][tid] = (uint16_t)tot;
       tot += v;
     }
-    st_relaxed_u32(lb + tid, (part == 0 ? kLbInc : kLbAgg) | tot);
+    if (part != hook.withhold) st_relaxed_u32(lb + tid, (part == 0 ? kLbInc : kLbAgg) | tot);
   }
   uint32_t incl = tot;
 #pragma unroll
@@ -318,12 +319,12 @@ onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* 
           if (flag == 2u) { found = true; break; }
         }
         p -= used;
-        if (!found && used < kLookWindow && globaltimer_ns() - t0 > kWaitLimitNs) {
+        if (!found && used < kLookWindow && globaltimer_ns() - t0 > hook.limit_ns) {
           set_status(status, AGS_ERR_TIMEOUT, kStageSort);
           break;
         }
       }
-      st_relaxed_u32(lb + tid, kLbInc | ((excl + tot) & kLbMask));
+      if (part != hook.withhold) st_relaxed_u32(lb + tid, kLbInc | ((excl + tot) & kLbMask));
     }
     S.gbase[tid] = gp + excl - doff;
   }
@@ -408,7 +409,7 @@ static cudaError_t launch_passes(K*& kin, uint32_t*& vin, K* kout, uint32_t* vou
     onesweep_kernel<RADIX, K><<<(unsigned)parts, kSortThreads, smem, st>>>(
         kin, vin, ko, vout, d_num_pairs, capacity, identity, sh, mask, rank_or, ghist + p * RADIX, lookback,
         counters + p,
-        d_status, last ? ranges : nullptr, (uint32_t)num_ranges, rmap);
+        d_status, last ? ranges : nullptr, (uint32_t)num_ranges, rmap, wait_hook(flags & AGS_SORT_TEST_STALL));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     std::swap(kin, kout);
@@ -441,7 +442,8 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
   if (!d_num_pairs || !d_status || capacity < 0 || capacity >= AGS_MAX_PAIRS) return AGS_ERR_INVALID_ARG;
   if (begin_bit < 0 || end_bit > kKeyBits || begin_bit > end_bit || digit_bits < 4 || digit_bits > 9)
     return AGS_ERR_INVALID_ARG;
-  if (flags & ~(AGS_SORT_IDENTITY_VALUES | AGS_SORT_DISCARD_KEYS | AGS_SORT_RANK_OR)) return AGS_ERR_INVALID_ARG;
+  if (flags & ~(AGS_SORT_IDENTITY_VALUES | AGS_SORT_DISCARD_KEYS | AGS_SORT_RANK_OR | AGS_SORT_TEST_STALL))
+    return AGS_ERR_INVALID_ARG;
   const int passes = (end_bit - begin_bit + digit_bits - 1) / digit_bits;
   if (passes > kMaxPasses) return AGS_ERR_INVALID_ARG;
   if (ranges && (num_ranges <= 0 || num_ranges > ((int64_t)1 << 32) - 1)) return AGS_ERR_INVALID_ARG;

@@ -139,6 +139,8 @@ class Renderer:
         self.ws_bwd = None
         if want_backward:
             self.ws_bwd = torch.empty(B.ags_backward_workspace_bytes(n, V), dtype=torch.uint8, device=dev)
+        self.generation = 0          # forwards enqueued so far (the blend state belongs to the last one)
+        self.headroom = headroom
 
     # -- configuration -------------------------------------------------------
     def set_params(self, scale_mode=None, K=None, lut=None, sh_degree=None, bg=None):
@@ -253,12 +255,29 @@ class Renderer:
 
     def forward(self, max_T=None):
         """Enqueue the whole frame on the current stream; returns the image tensor."""
+        self.generation += 1
         self.preprocess()
         self.depth_sort()
         self.emit()
         self.sort()
         self.rasterize(max_T)
         return self.image
+
+    def forward_fitted(self, max_T=None):
+        """forward(), then synchronise and check the status block; when the
+        pairs overflowed the capacity (the scene moved since the buffers were
+        sized), grow the capacity to the needed count times the headroom and
+        render again.  Raises on any other device-side error."""
+        img = self.forward(max_T)
+        code, detail = B.ags_check(self.status, raise_on_error=False)
+        if code == B.AGS_ERR_CAPACITY:
+            B.ags_status_reset(self.status)
+            self.alloc_pairs(max(int(math.ceil(int(detail) * self.headroom)), self.capacity + 1))
+            img = self.forward(max_T)
+            code, detail = B.ags_check(self.status, raise_on_error=False)
+        if code not in (B.AGS_OK, B.AGS_ERR_NUMERIC):
+            raise B.AgsError(code, "render", detail)
+        return img
 
     def capture(self) -> "torch.cuda.CUDAGraph":
         """Capture one whole forward (every stage, all views) in a CUDA graph.
@@ -365,18 +384,34 @@ class HostPipeline:
 
 
 class AgsRender(torch.autograd.Function):
-    """image = render(params); backward through libags with the pair lists of the forward held fixed."""
+    """image = render(params) through libags; the backward runs the blend and
+    preprocess adjoints with the pair lists of this forward held fixed (the
+    AdaGScale selection is piecewise constant in the parameters).
+
+    The forward synchronises once to check the status block (growing the
+    pair capacity and rendering again if the pairs overflowed it).  The blend
+    state the backward needs lives in the renderer, so the renderer must not
+    run another forward between this forward and its backward: the backward
+    raises if it did."""
 
     @staticmethod
     def forward(ctx, mean, log_scale, quat, opacity_logit, sh, renderer: Renderer):
+        if not renderer.keep_state:
+            raise RuntimeError("AgsRender needs a renderer built with keep_state=True (or want_backward=True)")
         renderer.scene = dict(mean=mean.detach().contiguous(), log_scale=log_scale.detach().contiguous(),
                               quat=quat.detach().contiguous(), opacity_logit=opacity_logit.detach().contiguous(),
                               sh=sh.detach().contiguous())
-        img = renderer.forward()
+        img = renderer.forward_fitted()
         ctx.renderer = renderer
+        ctx.generation = renderer.generation
         return img.clone()
 
     @staticmethod
     def backward(ctx, grad_image):
-        g = ctx.renderer.backward(grad_image)
+        r = ctx.renderer
+        if r.generation != ctx.generation:
+            raise RuntimeError("the renderer ran another forward after this one: its blend state belongs to that "
+                               "frame now; render the frames to differentiate with separate renderers")
+        g = r.backward(grad_image)
+        r.check()
         return g["mean"], g["log_scale"], g["quat"], g["opacity_logit"], g["sh"], None

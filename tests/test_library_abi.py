@@ -125,6 +125,24 @@ def test_invalid_arguments_rejected_on_host(lib):
                             1 << 20, None) == 1
     assert L.ags_emit_tile_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, None, 0, npairs, st, 0, None, 0,
                                  None) == 1
+    # views * n beyond 32 bits (or wrapping int64) is rejected before the product is formed
+    cam2 = B.cameras([dict(width=64, height=48, fx=50.0, fy=50.0, cx=31.5, cy=23.5,
+                           viewmat=[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], campos=[0, 0, 0])] * 2)
+    for big in (1 << 31, (1 << 62) + 1):
+        assert L.ags_emit_pairs(ctypes.byref(pr), big, 2, cam2, None, None, None, 0, npairs, st, 0,
+                                ctypes.c_void_p(256), 1 << 40, None) == 1
+        assert L.ags_emit_tile_pairs(ctypes.byref(pr), big, 2, cam2, None, None, None, None, 0, npairs, st, 0,
+                                     ctypes.c_void_p(256), 1 << 40, None) == 1
+        assert L.ags_emit_pairs_noalloc(ctypes.byref(pr), big, 2, cam2, None, None, None, 0, npairs, st, None) == 1
+        assert B.ags_emit_workspace_bytes(big, 2) == 0
+        assert B.ags_emit_tile_workspace_bytes(big, 2) == 0
+    # the allocation-free emission: one more Gaussian-view than its scratch holds, over two views
+    limit = int(L.ags_emit_pairs_noalloc_max_gaussians())
+    assert L.ags_emit_pairs_noalloc(ctypes.byref(pr), limit // 2 + 1, 2, cam2, None, None, None, 0, npairs, st,
+                                    None) == 1
+    # unknown emission flag
+    assert L.ags_emit_pairs(ctypes.byref(pr), 10, 1, cam, None, None, None, 0, npairs, st, 1 << 12,
+                            ctypes.c_void_p(256), 1 << 20, None) == 1
     # compaction: zero views, missing workspace, unaligned flags
     assert L.ags_compact_visible(ctypes.byref(pr), 10, 0, None, None, npairs, st, None, 0, None) == 1
     pr2 = B.AgsProjected()

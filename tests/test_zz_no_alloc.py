@@ -51,6 +51,13 @@ def test_noalloc_emit_matches_workspace_emit_twice():
     B.ags_check(st)
     n_ref = int(np_ref.item())
     assert n_ref > 0
+    # the workspace call in Gaussian-id order (no `order`), the other reference
+    keys_id = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    vals_id = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    st.zero_()
+    B.ags_emit_pairs(r.proj, r.n, r.cams, keys_id, vals_id, cap, np_ref, st, r.ws_emit)
+    B.ags_check(st)
+    assert int(np_ref.item()) == n_ref
     for order in (order_full, None, order_full):   # several calls in a row share the scratch array
         keys = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
         vals = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
@@ -59,12 +66,9 @@ def test_noalloc_emit_matches_workspace_emit_twice():
         assert _noalloc(L, r, order, keys, vals, cap, npairs, st) == B.AGS_OK
         B.ags_check(st)
         assert int(npairs.item()) == n_ref
-        if order is None:
-            # Gaussian-id order: same pairs, same count; compare as multisets
-            assert torch.equal(torch.sort(keys[:n_ref]).values, torch.sort(keys_ref[:n_ref]).values)
-        else:
-            assert torch.equal(keys[:n_ref], keys_ref[:n_ref])
-            assert torch.equal(vals[:n_ref], vals_ref[:n_ref])
+        ek, ev = (keys_id, vals_id) if order is None else (keys_ref, vals_ref)
+        assert torch.equal(keys[:n_ref], ek[:n_ref])
+        assert torch.equal(vals[:n_ref], ev[:n_ref])
 
 
 def test_noalloc_emit_rejects_sizes_beyond_its_scratch():
@@ -82,4 +86,33 @@ def test_noalloc_emit_rejects_sizes_beyond_its_scratch():
     cs = B.cameras(r.cams)
     code = L.ags_emit_pairs_noalloc(ctypes.byref(pr), limit + 1, 1, cs, None, B.ptr(r.keys), B.ptr(r.vals), 1024,
                                     B.ptr(npairs), B.ptr(st), B.stream_handle())
+    assert code == B.AGS_ERR_INVALID_ARG
+
+
+def test_noalloc_emit_takes_exactly_its_limit_over_two_views():
+    """2 views of limit/2 Gaussians fill the whole static scratch (every
+    look-back partition in use): accepted; all culled, so no pairs.  One more
+    Gaussian per view is rejected."""
+    from paper_2604_18980_gb300 import build
+    build.build()
+    L = B.lib()
+    limit = int(L.ags_emit_pairs_noalloc_max_gaussians())
+    n = limit // 2
+    _, cams, _ = synth.workload("c1_cube16k_256", n=64, width=64, height=48, views=2)
+    proj = dict(splat=torch.zeros(16, dtype=torch.float32, device="cuda"),
+                depth=torch.zeros(limit, dtype=torch.float32, device="cuda"),
+                rect=torch.zeros(4 * limit, dtype=torch.int16, device="cuda"),       # empty rectangles
+                tiles_touched=torch.zeros(limit, dtype=torch.int32, device="cuda"),
+                flags=torch.full((limit,), 0x80, dtype=torch.uint8, device="cuda"))
+    npairs = torch.full((1,), -5, dtype=torch.int64, device="cuda")
+    st = torch.zeros(4, dtype=torch.int64, device="cuda")
+    pr = B.projected(proj)
+    cs = B.cameras(cams)
+    code = L.ags_emit_pairs_noalloc(ctypes.byref(pr), n, 2, cs, None, None, None, 0, B.ptr(npairs), B.ptr(st),
+                                    B.stream_handle())
+    assert code == B.AGS_OK
+    B.ags_check(st)
+    assert int(npairs.item()) == 0
+    code = L.ags_emit_pairs_noalloc(ctypes.byref(pr), n + 1, 2, cs, None, None, None, 0, B.ptr(npairs), B.ptr(st),
+                                    B.stream_handle())
     assert code == B.AGS_ERR_INVALID_ARG
