@@ -566,6 +566,34 @@ def run_ours(args, world, rank, local):
         extras["fwd_bwd_ms_eager"] = fb_eager_ms
         del fb, grads, target, g_fb
 
+        # data-parallel training step over the workload's views: each rank renders
+        # its shard in one batch, back-propagates the L2 loss against the perturbed
+        # scene's plain render, and the gradients are summed over the ranks
+        from paper_2604_18980_gb300 import multiview as MV
+        mine = MV.shard_views(list(range(V)), rank, world)
+        if mine:
+            pert = R.scene_to_device(synth.perturb_scene(scene_np, 5005))
+            tgt_r = R.Renderer(pert, [cams[v] for v in mine], B.AGS_SCALE_PLAIN, keep_state=False)
+            targets = tgt_r.forward().clone()
+            del tgt_r, pert
+            tr = R.Renderer(sc, [cams[v] for v in mine], B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"],
+                            want_backward=True)
+            fn = MV.renderer_grads(tr, targets, 1.0 / (V * 3 * ada.H * ada.W))
+            for _ in range(max(2, args.warmup)):
+                MV.train_step(mine, fn)
+            barrier()
+            a.record(stream)
+            n_ts = max(3, args.steps // 2)
+            for _ in range(n_ts):
+                ts_loss, _ = MV.train_step(mine, fn)
+            b.record(stream)
+            barrier()
+            extras["train_step"] = {"ms_per_step": max_over_ranks(a.elapsed_time(b)) / n_ts, "ranks": world,
+                                    "views_per_rank": len(mine), "views": V, "loss": ts_loss,
+                                    "allreduce_bytes": sum(v.numel() * 4 for v in sc.values()) if world > 1 else 0,
+                                    "step": "forward (status checked) + L2 loss + backward + gradient sum"}
+            del tr, targets, fn
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

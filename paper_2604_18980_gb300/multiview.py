@@ -1,9 +1,11 @@
-"""Host-side logic for rendering many views on several GPUs.
+"""Host-side logic for rendering and training over many views on several GPUs.
 
 Views are independent in the forward pass (each GPU holds a replica of the
 scene and renders its own views; no exchange).  Training over views needs one
 exchange: the sum of the per-view parameter gradients.  This module holds the
-view partition and that sum; with one GPU it is the identity.
+view partition, that sum, and the data-parallel training step built on them
+(`train_step`, with `renderer_grads` as the libags renderer's part); with one
+GPU the sum is the identity.
 """
 from __future__ import annotations
 
@@ -41,3 +43,41 @@ def sum_gradients(grads: dict, group=None) -> dict:
             grads[k].copy_(flat[off:off + n].view_as(grads[k]))
             off += n
     return grads
+
+
+GRAD_KEYS = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+
+
+def train_step(my_views: list, view_grads, group=None) -> tuple:
+    """One data-parallel step over views: `view_grads(my_views)` returns
+    (loss, grads) summed over this rank's views -- normally renderer_grads
+    over one batched render -- then the loss and every gradient tensor are
+    summed over the ranks of `group` (one all-reduce for the gradients, one
+    for the loss).  Returns (total loss, gradients of the whole view set)."""
+    import torch
+    import torch.distributed as dist
+    loss, grads = view_grads(my_views)
+    grads = {k: grads[k] for k in GRAD_KEYS}
+    sum_gradients(grads, group)
+    lt = torch.tensor([float(loss)], dtype=torch.float64,
+                      device=grads["mean"].device if grads["mean"].is_cuda else "cpu")
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(lt, op=dist.ReduceOp.SUM, group=group)
+    return float(lt.item()), grads
+
+
+def renderer_grads(renderer, targets, inv_count: float):
+    """view_grads for train_step over one libags Renderer that holds this
+    rank's views: render them (one batch), take L = inv_count * sum (image -
+    target)^2 and run the hand-written backward with the pair lists of this
+    render (the AdaGScale selection held fixed).  Returns (L, grads)."""
+    import torch
+
+    def fn(_views):
+        img = renderer.forward_fitted()
+        diff = img - targets
+        loss = float(torch.sum(diff * diff).item()) * inv_count
+        g = renderer.backward(diff * (2.0 * inv_count))
+        renderer.check()
+        return loss, g
+    return fn

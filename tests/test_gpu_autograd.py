@@ -89,3 +89,36 @@ def test_finetune_with_adagscale_in_the_loop_lowers_the_loss():
     assert all(b <= a * (1 + 1e-3) for a, b in zip(L, L[1:])), L
     assert L[-1] < 0.6 * L[0], L
     assert len(set(out["pairs"])) > 1          # the selection followed the parameters
+
+
+def test_train_step_one_rank_matches_the_batched_backward_and_oracle():
+    """multiview.train_step over one rank with the libags renderer: the loss
+    and gradients of one batched render of all views, and the oracle's
+    gradient summed over the views."""
+    from paper_2604_18980_gb300 import multiview as MV
+    scene, cams, _ = synth.workload("c1_cube16k_256", n=3000, width=96, height=80, views=3)
+    pert = synth.perturb_scene(scene, 31)
+    tgt = R.Renderer(R.scene_to_device(pert), cams, B.AGS_SCALE_PLAIN).forward().clone()
+    inv = 1.0 / tgt.numel()
+    r = R.Renderer(R.scene_to_device(scene), cams, B.AGS_SCALE_ADAGSCALE, 0.2, want_backward=True)
+    loss, g = MV.train_step([0, 1, 2], MV.renderer_grads(r, tgt, inv))
+    r2 = R.Renderer(R.scene_to_device(scene), cams, B.AGS_SCALE_ADAGSCALE, 0.2, want_backward=True)
+    img = r2.forward()
+    assert abs(loss - float(((img - tgt) ** 2).sum().item()) * inv) <= 1e-6 * loss
+    ref = r2.backward((img - tgt) * (2.0 * inv))
+    for k in GRAD_KEYS:
+        torch.testing.assert_close(g[k], ref[k], rtol=1e-5, atol=1e-6 * float(ref[k].abs().max()), msg=k)
+    tot, edge = None, None
+    timg = tgt.cpu().numpy().astype(np.float64)
+    for v, cam in enumerate(cams):
+        par = oracle_params(cam, 1, 0.2)
+        oo = oracle.render(scene, cam, par)
+        og = oracle.backward(scene, cam, par, oo["tile_start"], oo["ids"], 2.0 * inv * (oo["image"] - timg[v]))
+        e = gradient_edge_gaussians(oo, og)
+        if tot is None:
+            tot, edge = og, e
+        else:
+            tot = dict({k: tot[k] + og[k] for k in GRAD_KEYS},
+                       budget={k: tot["budget"][k] + og["budget"][k] for k in GRAD_KEYS})
+            edge = edge | e
+    compare_gradients(g, tot, skip=edge)
