@@ -7,7 +7,8 @@
 //
 // "Onesweep" organisation: one kernel reads every key once and builds the
 // histograms of all digits; then each digit pass is a single kernel in which
-// each block (512 threads x 8 keys) ranks its keys with warp-level match/ballot
+// each block (512 threads x 8 keys; 256 x 16 for 32-bit keys and digits of up
+// to 8 bits, lean_kernel) ranks its keys with warp-level match/ballot
 // (per-warp digit counters in shared memory), publishes its digit counts,
 // places its keys in shared memory in block-sorted order, obtains each digit's
 // global offset by a decoupled look-back over the preceding blocks (bounded
@@ -381,6 +382,239 @@ __global__ void ranges_kernel(const K* __restrict__ keys, const int64_t* count_p
   }
 }
 
+// ---------------------------------------------------------------------------
+// Digit pass for 32-bit keys and digits of up to 8 bits (the depth pre-sort
+// and the tile-key pair sort): the same algorithm as onesweep_kernel with 256
+// threads x 16 keys per 4096-key partition (fewer warps to merge per digit,
+// no register spills), the ranking method fixed at compile time, and the
+// tile ranges of the last pass found from each staged key's neighbours.
+// ---------------------------------------------------------------------------
+constexpr int kLT = 256, kLI = 16, kLW = kLT / 32;
+static_assert(kLT * kLI == kSortPart, "partition size");
+
+template <int RADIX, bool kOr>
+struct LeanSmem {
+  uint32_t bstart[RADIX];
+  uint32_t gbase[RADIX];
+  uint32_t wtot[kLW];
+  uint32_t part;
+  union {
+    struct {
+      uint16_t wh[kLW][RADIX + 2];
+      uint32_t bins[kOr ? kLW : 1][RADIX + 1];
+    } r;
+    struct {
+      uint32_t keys[kStageWords];
+      uint32_t vals[kStageWords];
+    } st;
+  } u;
+};
+
+__device__ __forceinline__ uint32_t bfe32(uint32_t k, int shift, int bits) {
+  uint32_t d;
+  asm("bfe.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(k), "r"(shift), "r"(bits));
+  return d;
+}
+
+template <int RADIX, bool kOr>
+__global__ void __launch_bounds__(kLT, 4)
+lean_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+            uint32_t* __restrict__ vout, const int64_t* count_ptr, int64_t capacity, int identity, int shift,
+            int bits, const uint32_t* __restrict__ gprefix, uint32_t* lookback, uint32_t* counter, int64_t* status,
+            uint32_t* ranges, uint32_t num_ranges, RangeMap rmap, WaitHook hook) {
+  using Sm = LeanSmem<RADIX, kOr>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sm& S = *reinterpret_cast<Sm*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) S.part = atomicAdd(counter, 1u);
+  {
+    uint32_t* wz = reinterpret_cast<uint32_t*>(&S.u.r.wh[0][0]);
+    for (int i = tid; i < kLW * (RADIX + 2) / 2; i += kLT) wz[i] = 0u;
+    if (kOr) {
+      uint32_t* bz = &S.u.r.bins[0][0];
+      for (int i = tid; i < kLW * (RADIX + 1); i += kLT) bz[i] = 0u;
+    }
+  }
+  const bool dthread = tid < RADIX;
+  const uint32_t gp = dthread ? __ldg(gprefix + tid) : 0u;
+  __syncthreads();
+  const uint32_t part = S.part;
+  const uint32_t count = clamped_count(count_ptr, capacity);
+  if (part >= (count + kSortPart - 1) / kSortPart) return;
+  const uint32_t base = part * kSortPart;
+  const uint32_t ibase = base + (uint32_t)warp * (32u * kLI) + (uint32_t)lane;   // item i at ibase + 32 i
+  const bool full = base + kSortPart <= count;
+
+  uint32_t key[kLI], val[kLI], rank[kLI];
+  if (full) {
+#pragma unroll
+    for (int i = 0; i < kLI; i++) key[i] = __ldcs(kin + ibase + 32 * i);
+#pragma unroll
+    for (int i = 0; i < kLI; i++) val[i] = identity ? ibase + 32 * i : __ldcs(vin + ibase + 32 * i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kLI; i++) {
+      const uint32_t idx = ibase + 32 * i;
+      key[i] = idx < count ? __ldcs(kin + idx) : 0u;
+      val[i] = idx < count ? (identity ? idx : __ldcs(vin + idx)) : 0u;
+    }
+  }
+  uint16_t* wh = S.u.r.wh[warp];
+  uint32_t* bins = kOr ? S.u.r.bins[warp] : nullptr;
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kLI; i++) {
+    const uint32_t d = (full || ibase + 32 * i < count) ? bfe32(key[i], shift, bits) : (uint32_t)RADIX;
+    unsigned peers;
+    if (kOr) {
+      atomicOr(bins + d, 1u << lane);
+      __syncwarp();
+      peers = bins[d];
+    } else {
+      peers = __match_any_sync(0xffffffffu, d);
+    }
+    const uint32_t before = wh[d];
+    const uint32_t below = (uint32_t)__popc(peers & lt);
+    __syncwarp();
+    if (below == 0u) {
+      wh[d] = (uint16_t)(before + __popc(peers));
+      if (kOr) bins[d] = 0u;
+    }
+    __syncwarp();
+    rank[i] = before + below;
+  }
+  __syncthreads();
+  uint32_t tot = 0;
+  if (dthread) {
+#pragma unroll
+    for (int w = 0; w < kLW; w++) {
+      const uint32_t v = S.u.r.wh[w][tid];
+      S.u.r.wh[w][tid] = (uint16_t)tot;
+      tot += v;
+    }
+    if (part != hook.withhold) st_relaxed_u32(lookback + (size_t)part * RADIX + tid, (part == 0 ? kLbInc : kLbAgg) | tot);
+  }
+  uint32_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) S.wtot[warp] = incl;
+  __syncthreads();
+  uint32_t wpre = 0;
+#pragma unroll
+  for (int w = 0; w < kLW; w++) wpre += w < warp ? S.wtot[w] : 0u;
+  const uint32_t doff = wpre + incl - tot;
+  if (dthread) S.bstart[tid] = doff;
+  __syncthreads();
+  uint32_t pos[kLI];
+#pragma unroll
+  for (int i = 0; i < kLI; i++) {
+    const uint32_t d = bfe32(key[i], shift, bits);
+    pos[i] = (full || ibase + 32 * i < count) ? S.bstart[d] + wh[d] + rank[i] : 0xffffffffu;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kLI; i++) {
+    if (full || pos[i] != 0xffffffffu) {
+      const uint32_t si = stage_index(pos[i]);
+      S.u.st.keys[si] = key[i];
+      S.u.st.vals[si] = val[i];
+    }
+  }
+  if (dthread) {
+    uint32_t excl = 0;
+    if (part > 0) {
+      const uint64_t t0 = globaltimer_ns();
+      int32_t p = (int32_t)part - 1;
+      bool found = false;
+      while (!found) {
+        uint32_t sv[kLookWindow];
+#pragma unroll
+        for (int q = 0; q < kLookWindow; q++)
+          sv[q] = (p - q >= 0) ? ld_relaxed_u32(lookback + (size_t)(p - q) * RADIX + tid) : kLbInc;
+        int used = 0;
+#pragma unroll
+        for (int q = 0; q < kLookWindow; q++) {
+          const uint32_t flag = sv[q] >> 30;
+          if (flag == 0u) break;
+          excl += sv[q] & kLbMask;
+          used = q + 1;
+          if (flag == 2u) { found = true; break; }
+        }
+        p -= used;
+        if (!found && used < kLookWindow && globaltimer_ns() - t0 > hook.limit_ns) {
+          set_status(status, AGS_ERR_TIMEOUT, kStageSort);
+          break;
+        }
+      }
+      if (part != hook.withhold)
+        st_relaxed_u32(lookback + (size_t)part * RADIX + tid, kLbInc | ((excl + tot) & kLbMask));
+    }
+    S.gbase[tid] = gp + excl - doff;
+  }
+  __syncthreads();
+  const uint32_t nvalid = full ? (uint32_t)kSortPart : count - base;
+#pragma unroll 4
+  for (int t = 0; t < kLI; t++) {
+    const uint32_t j = (uint32_t)(t * kLT + tid);
+    if (!full && j >= nvalid) break;
+    const uint32_t k = S.u.st.keys[stage_index(j)];
+    const uint32_t d = bfe32(k, shift, bits);
+    const uint32_t dst = S.gbase[d] + j;
+    if (dst >= count) continue;   // only after a look-back that gave up: stay inside the output
+    if (kout) kout[dst] = k;
+    vout[dst] = S.u.st.vals[stage_index(j)];
+    if (ranges) {
+      // the staged keys are sorted; within one digit's run here the outputs
+      // are consecutive, so a range boundary inside the run is this block's
+      // alone (plain stores); the ends of a run may continue in other blocks
+      // (atomics against the (0xffffffff, 0) initialisation)
+      const uint32_t r = key_range(k, rmap);
+      const bool first = j == 0 || bfe32(S.u.st.keys[stage_index(j - 1)], shift, bits) != d;
+      const bool last = j + 1 >= nvalid || bfe32(S.u.st.keys[stage_index(j + 1)], shift, bits) != d;
+      if (r < num_ranges) {
+        if (first) {
+          atomicMin(ranges + 2 * (size_t)r, dst);
+        } else {
+          const uint32_t rp = key_range(S.u.st.keys[stage_index(j - 1)], rmap);
+          if (rp != r) {
+            ranges[2 * (size_t)r] = dst;
+            if (rp < num_ranges) ranges[2 * (size_t)rp + 1] = dst;
+          }
+        }
+        if (last) atomicMax(ranges + 2 * (size_t)r + 1, dst + 1);
+      }
+    }
+  }
+}
+
+template <int RADIX>
+static cudaError_t launch_lean(bool rank_or, dim3 grid, cudaStream_t st, const uint32_t* kin, const uint32_t* vin,
+                               uint32_t* kout, uint32_t* vout, const int64_t* count_ptr, int64_t capacity, int identity,
+                               int shift, int bits, const uint32_t* gprefix, uint32_t* lookback, uint32_t* counter,
+                               int64_t* status, uint32_t* ranges, uint32_t num_ranges, RangeMap rmap, WaitHook hook) {
+  cudaError_t e;
+  if (rank_or) {
+    auto kern = lean_kernel<RADIX, true>;
+    const int smem = (int)sizeof(LeanSmem<RADIX, true>);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kLT, smem, st>>>(kin, vin, kout, vout, count_ptr, capacity, identity, shift, bits, gprefix, lookback,
+                                  counter, status, ranges, num_ranges, rmap, hook);
+  } else {
+    auto kern = lean_kernel<RADIX, false>;
+    const int smem = (int)sizeof(LeanSmem<RADIX, false>);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kLT, smem, st>>>(kin, vin, kout, vout, count_ptr, capacity, identity, shift, bits, gprefix, lookback,
+                                  counter, status, ranges, num_ranges, rmap, hook);
+  }
+  return cudaGetLastError();
+}
+
+
 static size_t sort_parts(int64_t capacity) { return (size_t)((capacity + kSortPart - 1) / kSortPart); }
 
 template <int RADIX, typename K>
@@ -406,6 +640,18 @@ static cudaError_t launch_passes(K*& kin, uint32_t*& vin, K* kout, uint32_t* vou
     const int identity = (p == 0 && (flags & AGS_SORT_IDENTITY_VALUES)) ? 1 : 0;
     const bool last = p == passes - 1;
     K* ko = (last && (flags & AGS_SORT_DISCARD_KEYS)) ? nullptr : kout;
+    if (sizeof(K) == 4 && RADIX <= 256) {
+      e = launch_lean<RADIX <= 256 ? RADIX : 256>(rank_or != 0, dim3((unsigned)parts), st,
+                                                  reinterpret_cast<const uint32_t*>(kin), vin,
+                                                  reinterpret_cast<uint32_t*>(ko), vout, d_num_pairs, capacity,
+                                                  identity, sh, __builtin_popcount(mask), ghist + p * RADIX,
+                                                  lookback, counters + p, d_status, last ? ranges : nullptr,
+                                                  (uint32_t)num_ranges, rmap, wait_hook(flags & AGS_SORT_TEST_STALL));
+      if (e != cudaSuccess) return e;
+      std::swap(kin, kout);
+      std::swap(vin, vout);
+      continue;
+    }
     onesweep_kernel<RADIX, K><<<(unsigned)parts, kSortThreads, smem, st>>>(
         kin, vin, ko, vout, d_num_pairs, capacity, identity, sh, mask, rank_or, ghist + p * RADIX, lookback,
         counters + p,
