@@ -734,18 +734,23 @@ def roofline(stage, ms, r, evals, pk, pk_src, passes, clk, workload=WORKLOAD, sl
         import torch
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12           # FP32 lanes x clock, Tops/s
-        achieved = evals * RASTER_OPS_PER_EVAL / (ms / 1e3) / 1e12
         tpv = RASTER_TRAFFIC_PER_VIEW.get(workload)
         traffic = None if tpv is None else tpv * V
+        # the work the kernel performs: each walked splat against its warp's
+        # 8x16 pixels; the method's own count (every pixel against its tile's
+        # pairs up to its stop) is far larger, because the exact per-warp
+        # ellipse cull skips most of it, so it is reported as context only
+        work = slots if slots else evals
+        achieved = work * RASTER_OPS_PER_EVAL / (ms / 1e3) / 1e12
+        alg = evals * RASTER_OPS_PER_EVAL / (ms / 1e3) / 1e12
         return {"kernel": "raster_kernel", "bound": "alu", "achieved": achieved, "peak": peak_ops,
                 "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read+write per view x views" if traffic else
                                   "not captured for this kernel build and workload",
-                "work": "%d Eq. 1-2 evaluations (each pixel against its tile's pairs up to its stop) x %d FP32 "
-                        "ops" % (evals, RASTER_OPS_PER_EVAL),
-                "executed": None if not slots else {
-                    "pixel_pairs": slots, "frac": slots * RASTER_OPS_PER_EVAL / (ms / 1e3) / 1e12 / peak_ops,
-                    "note": "the pixel-pair slots the kernel walks after its per-warp culling"},
+                "work": "%d pixel-pair slots the kernel evaluates x %d FP32 ops" % (work, RASTER_OPS_PER_EVAL),
+                "algorithmic": {"evaluations": evals, "achieved": alg, "frac": alg / peak_ops,
+                                "note": "Eq. 1-2 evaluations as the method defines them (each pixel against its "
+                                        "tile's pairs up to its stop); the kernel's cull skips most of them"},
                 "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (%s)" % (sms, sm_mhz, pk_src)}
     hbm = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
     byts, kern = stage_bytes(stage, r, passes)

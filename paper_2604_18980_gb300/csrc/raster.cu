@@ -76,25 +76,106 @@ __device__ __forceinline__ void blend_step(float q, float l2tau, float amax, flo
   }
 }
 
-// The same step in C++ with its decisions returned (counters, calibration,
-// blend state); the same operations, so the same results.
+// The same step returning its decisions (blended, stopped: 0 or 1) for the
+// instances that count, calibrate or record the blend state: the same
+// instructions plus two selects.
 template <bool kClamp>
 __device__ __forceinline__ void blend_step_rec(float q, const BlendConst& bc, float cr, float cg, float cb, float& T,
-                                               float& r, float& g, float& b, bool& blended, bool& stopped) {
-  const bool ok = T > 0.f && splat_accept(q, bc.l2tau);
-  float raw;
-  const float alpha = kClamp ? splat_alpha(q, bc.alpha_max, raw) : fast_exp2(q);
-  const float tt = transmit(alpha, T);
-  stopped = ok && tt < bc.t_min;
-  blended = ok && !stopped;
-  const float w = __fmul_rn(alpha, T);
-  if (blended) {
-    r = __fmaf_rn(cr, w, r);
-    g = __fmaf_rn(cg, w, g);
-    b = __fmaf_rn(cb, w, b);
-    T = tt;
+                                               float& r, float& g, float& b, uint32_t& blended, uint32_t& stopped) {
+  if (kClamp) {
+    asm("{\n\t"
+        ".reg .pred tp, ok, st, bl;\n\t"
+        ".reg .f32 e, a, na, tt, w;\n\t"
+        "setp.gt.f32 tp, %0, 0f00000000;\n\t"
+        "setp.ge.and.f32 ok, %6, %7, tp;\n\t"
+        "ex2.approx.ftz.f32 e, %6;\n\t"
+        "min.f32 a, e, %8;\n\t"
+        "neg.f32 na, a;\n\t"
+        "fma.rn.f32 tt, na, %0, %0;\n\t"
+        "setp.lt.and.f32 st|bl, tt, %9, ok;\n\t"
+        "mul.rn.f32 w, a, %0;\n\t"
+        "@bl fma.rn.f32 %1, %10, w, %1;\n\t"
+        "@bl fma.rn.f32 %2, %11, w, %2;\n\t"
+        "@bl fma.rn.f32 %3, %12, w, %3;\n\t"
+        "@bl fma.rn.f32 %0, na, %0, %0;\n\t"
+        "@st mul.rn.f32 %0, %0, 0fBF800000;\n\t"
+        "selp.u32 %4, 1, 0, bl;\n\t"
+        "selp.u32 %5, 1, 0, st;\n\t"
+        "}"
+        : "+f"(T), "+f"(r), "+f"(g), "+f"(b), "=r"(blended), "=r"(stopped)
+        : "f"(q), "f"(bc.l2tau), "f"(bc.alpha_max), "f"(bc.t_min), "f"(cr), "f"(cg), "f"(cb));
+  } else {
+    asm("{\n\t"
+        ".reg .pred tp, ok, st, bl;\n\t"
+        ".reg .f32 a, na, tt, w;\n\t"
+        "setp.gt.f32 tp, %0, 0f00000000;\n\t"
+        "setp.ge.and.f32 ok, %6, %7, tp;\n\t"
+        "ex2.approx.ftz.f32 a, %6;\n\t"
+        "neg.f32 na, a;\n\t"
+        "fma.rn.f32 tt, na, %0, %0;\n\t"
+        "setp.lt.and.f32 st|bl, tt, %9, ok;\n\t"
+        "mul.rn.f32 w, a, %0;\n\t"
+        "@bl fma.rn.f32 %1, %10, w, %1;\n\t"
+        "@bl fma.rn.f32 %2, %11, w, %2;\n\t"
+        "@bl fma.rn.f32 %3, %12, w, %3;\n\t"
+        "@bl fma.rn.f32 %0, na, %0, %0;\n\t"
+        "@st mul.rn.f32 %0, %0, 0fBF800000;\n\t"
+        "selp.u32 %4, 1, 0, bl;\n\t"
+        "selp.u32 %5, 1, 0, st;\n\t"
+        "}"
+        : "+f"(T), "+f"(r), "+f"(g), "+f"(b), "=r"(blended), "=r"(stopped)
+        : "f"(q), "f"(bc.l2tau), "f"(bc.alpha_max), "f"(bc.t_min), "f"(cr), "f"(cg), "f"(cb));
   }
-  if (stopped) T = -T;
+}
+
+// The step for the instance that records the blend state for the backward:
+// the pixel's last blended position becomes pos1 under the blend predicate.
+template <bool kClamp>
+__device__ __forceinline__ void blend_step_state(float q, const BlendConst& bc, float cr, float cg, float cb,
+                                                 float& T, float& r, float& g, float& b, uint32_t& last,
+                                                 uint32_t pos1) {
+  if (kClamp) {
+    asm("{\n\t"
+        ".reg .pred tp, ok, st, bl;\n\t"
+        ".reg .f32 e, a, na, tt, w;\n\t"
+        "setp.gt.f32 tp, %0, 0f00000000;\n\t"
+        "setp.ge.and.f32 ok, %6, %7, tp;\n\t"
+        "ex2.approx.ftz.f32 e, %6;\n\t"
+        "min.f32 a, e, %8;\n\t"
+        "neg.f32 na, a;\n\t"
+        "fma.rn.f32 tt, na, %0, %0;\n\t"
+        "setp.lt.and.f32 st|bl, tt, %9, ok;\n\t"
+        "mul.rn.f32 w, a, %0;\n\t"
+        "@bl fma.rn.f32 %1, %10, w, %1;\n\t"
+        "@bl fma.rn.f32 %2, %11, w, %2;\n\t"
+        "@bl fma.rn.f32 %3, %12, w, %3;\n\t"
+        "@bl fma.rn.f32 %0, na, %0, %0;\n\t"
+        "@bl mov.u32 %4, %5;\n\t"
+        "@st mul.rn.f32 %0, %0, 0fBF800000;\n\t"
+        "}"
+        : "+f"(T), "+f"(r), "+f"(g), "+f"(b), "+r"(last)
+        : "r"(pos1), "f"(q), "f"(bc.l2tau), "f"(bc.alpha_max), "f"(bc.t_min), "f"(cr), "f"(cg), "f"(cb));
+  } else {
+    asm("{\n\t"
+        ".reg .pred tp, ok, st, bl;\n\t"
+        ".reg .f32 a, na, tt, w;\n\t"
+        "setp.gt.f32 tp, %0, 0f00000000;\n\t"
+        "setp.ge.and.f32 ok, %6, %7, tp;\n\t"
+        "ex2.approx.ftz.f32 a, %6;\n\t"
+        "neg.f32 na, a;\n\t"
+        "fma.rn.f32 tt, na, %0, %0;\n\t"
+        "setp.lt.and.f32 st|bl, tt, %9, ok;\n\t"
+        "mul.rn.f32 w, a, %0;\n\t"
+        "@bl fma.rn.f32 %1, %10, w, %1;\n\t"
+        "@bl fma.rn.f32 %2, %11, w, %2;\n\t"
+        "@bl fma.rn.f32 %3, %12, w, %3;\n\t"
+        "@bl fma.rn.f32 %0, na, %0, %0;\n\t"
+        "@bl mov.u32 %4, %5;\n\t"
+        "@st mul.rn.f32 %0, %0, 0fBF800000;\n\t"
+        "}"
+        : "+f"(T), "+f"(r), "+f"(g), "+f"(b), "+r"(last)
+        : "r"(pos1), "f"(q), "f"(bc.l2tau), "f"(bc.alpha_max), "f"(bc.t_min), "f"(cr), "f"(cg), "f"(cb));
+  }
 }
 
 // kStats: count evaluations and blends; kMaxT: calibration output; kState:
@@ -197,6 +278,19 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
             blend_step<false>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc.l2tau, bc.alpha_max, bc.t_min, s.b.z,
                               s.b.w, cbl, T[k], cr[k], cg[k], cb[k]);
         }
+      } else if (kState && !kStats && !kMaxT) {   // the backward's forward: last blended position only
+        const uint32_t pos1 = bb - start + (uint32_t)j + 1u;
+        if (clamp) {
+#pragma unroll
+          for (int k = 0; k < kRowsPerLane; k++)
+            blend_step_state<true>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc, s.b.z, s.b.w, cbl, T[k], cr[k],
+                                   cg[k], cb[k], last[k], pos1);
+        } else {
+#pragma unroll
+          for (int k = 0; k < kRowsPerLane; k++)
+            blend_step_state<false>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc, s.b.z, s.b.w, cbl, T[k], cr[k],
+                                    cg[k], cb[k], last[k], pos1);
+        }
       } else {
         const uint32_t pos1 = bb - start + (uint32_t)j + 1u;    // 1-based position in the tile's list
         uint32_t mt = 0u;
@@ -204,13 +298,13 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
         for (int k = 0; k < kRowsPerLane; k++) {
           const float Tb = T[k];
           const float q = splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k]));
-          bool bl, stp;
+          uint32_t bl, stp;
           if (clamp)
             blend_step_rec<true>(q, bc, s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k], bl, stp);
           else
             blend_step_rec<false>(q, bc, s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k], bl, stp);
           if (kStats) {
-            blends += bl ? 1u : 0u;
+            blends += bl;
             stop_at[k] = stp ? pos1 : stop_at[k];
           }
           if (kState) last[k] = bl ? pos1 : last[k];
