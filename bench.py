@@ -258,8 +258,7 @@ def run_ours(args, world, rank, local):
     # launch parameters from the autotuner (untimed set-up; identical results for every candidate)
     from paper_2604_18980_gb300 import autotune
     tuned = autotune.tune(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"])
-    knobs = dict(digit_bits=tuned["digit_bits"], presort=tuned["presort"], pair_rank_or=tuned["pair_rank_or"],
-                 emit_two_pass=tuned.get("emit_two_pass", True))
+    knobs = {k: tuned[k] for k in autotune.KNOBS}
     ada = R.Renderer(sc, cams, B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_stats=True, keep_state=False,
                      **knobs)
     stream = torch.cuda.current_stream()

@@ -114,7 +114,15 @@ typedef struct {
   float lut[AGS_MAX_LUT_BINS]; /* T_up per depth bin (Sec. 3.2 Eq. 7, Sec. 3.4) */
   float bg[3];              /* background colour added with the final transmittance */
   int32_t tile_test;        /* ags_tile_test */
+  int32_t blend_flags;      /* launch shape of the blend: 0 (8x16-pixel warp blocks, 32-splat
+                             * batches) or AGS_BLEND_* bits; any other bit is invalid.  The
+                             * image, final_T, n_contrib, max_T and stats do not depend on it. */
 } ags_params;
+
+#define AGS_BLEND_ROWS2 1     /* blend_flags: 8x8-pixel warp blocks (four warps a tile, two rows a
+                               * lane) instead of 8x16 (two warps, four rows a lane) */
+#define AGS_BLEND_BATCH64 2   /* blend_flags: each warp stages 64 of its tile's splats a round
+                               * (two a lane) instead of 32 */
 
 /* Gaussian parameters (pointers to device memory, SoA fp32). */
 typedef struct {
@@ -302,6 +310,11 @@ size_t ags_sort_workspace_bytes(int64_t capacity);
                                         atomic-OR peer masks instead of warp match; same result,
                                         faster when a warp's keys mostly carry distinct digits
                                         (tile keys in emission order) */
+#define AGS_SORT_WIDE_BLOCK 8        /* sort flag: the digit passes over 32-bit keys with digits of
+                                        up to 8 bits use 512-thread partitions of 8 keys a thread
+                                        instead of 256 threads of 16 keys (4096 keys either way);
+                                        same result.  64-bit keys and 9-bit digits always take the
+                                        512-thread pass. */
 
 /* Stable LSD radix sort of (keys, vals) by key bits [begin_bit, end_bit)
  * (Sec. 2.1 sorting stage): one global-histogram pass, then one single-pass
@@ -311,7 +324,8 @@ size_t ags_sort_workspace_bytes(int64_t capacity);
  * Keys already stably ordered by their bits below begin_bit stay so ordered
  * within equal [begin_bit, end_bit) fields: pairs emitted in depth order
  * need only the tile digits, with the same result as a sort of all bits.
- * flags: AGS_SORT_IDENTITY_VALUES, AGS_SORT_DISCARD_KEYS, AGS_SORT_RANK_OR.  `keys` must be
+ * flags: AGS_SORT_IDENTITY_VALUES, AGS_SORT_DISCARD_KEYS, AGS_SORT_RANK_OR, AGS_SORT_WIDE_BLOCK
+ * (any other bit but AGS_SORT_TEST_STALL is invalid).  `keys` must be
  * 16-byte aligned when a digit pass runs (read 16 bytes at a time).
  * The sorted result lands in (keys, vals) when the number of digit passes is
  * even and in (keys_alt, vals_alt) when it is odd; *result_in_alt (host)

@@ -1,14 +1,21 @@
 """Autotuner for the launch parameters of a rendering workload.
 
-The knobs are the digit width of the radix sorts (7, 8 or 9 bits: fewer,
-wider passes against more contention and larger look-back tables), whether
-the Gaussians are depth-sorted before emission (the pair sort then runs only
-the tile digits, on 32-bit keys), how the pair sort ranks a warp's equal
-digits (warp match, or atomic-OR peer masks in shared memory) and whether the
-tile-key emission runs as one fused pass or as two passes balanced by pairs.  Every candidate renders the same frames through
-the same kernels -- results are identical -- and the fastest one (CUDA-event
-time of a whole forward, after warm-up) is kept.  Results are cached in a JSON
-file keyed by GPU name and workload shape.
+The knobs of the sort and emission stages are the digit width of the radix
+sorts (7, 8 or 9 bits: fewer, wider passes against more contention and larger
+look-back tables), whether the Gaussians are depth-sorted before emission
+(the pair sort then runs only the tile digits, on 32-bit keys), how the pair
+sort ranks a warp's equal digits (warp match, or atomic-OR peer masks in
+shared memory) and whether the tile-key emission runs as one fused pass or as
+two passes balanced by pairs.  The block shapes come second, on the best of
+those: the blend's warp block (8x16 pixels, two warps a tile and four rows a
+lane, or 8x8, four warps and two rows), its tile batch (32 or 64 splats
+staged per warp and round) and the partition shape of the 32-bit sort passes
+(256 threads of 16 keys or 512 of 8).  The stages do not interact, so the two
+rounds find the best combination with 26 timings instead of 144.  Every
+candidate renders the same frames through the same kernels -- results are
+identical -- and the fastest one (CUDA-event time of a whole forward, after
+warm-up) is kept.  Results are cached in a JSON file keyed by GPU name and
+workload shape.
 """
 from __future__ import annotations
 
@@ -24,6 +31,10 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 CANDIDATES = ([dict(digit_bits=d, presort=True, pair_rank_or=o, emit_two_pass=t) for t in (True, False)
                for o in (True, False) for d in (9, 8, 7)]
               + [dict(digit_bits=d, presort=False, pair_rank_or=o) for o in (True, False) for d in (9, 8, 7)])
+SHAPES = [dict(blend_flags=f, sort_wide=w) for w in (False, True)
+          for f in (0, B.AGS_BLEND_ROWS2, B.AGS_BLEND_BATCH64, B.AGS_BLEND_ROWS2 | B.AGS_BLEND_BATCH64)]
+KNOBS = ("digit_bits", "presort", "pair_rank_or", "emit_two_pass", "blend_flags", "sort_wide")
+DEFAULTS = dict(emit_two_pass=True, blend_flags=0, sort_wide=False)
 
 
 def workload_key(scene: dict, cams: list, scale_mode: int) -> str:
@@ -47,8 +58,9 @@ def _time_forward(r: R.Renderer, warmup: int, reps: int) -> float:
 
 
 def tune(scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_ADAGSCALE, K: float = 0.0, lut=None,
-         warmup: int = 2, reps: int = 5, use_cache: bool = True, candidates=None) -> dict:
-    """Fastest configuration for this workload: {"digit_bits", "presort", "pair_rank_or", "ms", "table"}."""
+         warmup: int = 2, reps: int = 5, use_cache: bool = True, candidates=None, shapes=None) -> dict:
+    """Fastest configuration for this workload: the KNOBS, "ms" and "table"
+    (every timed candidate with its ms, the stage knobs first, then the shapes)."""
     key = workload_key(scene, cams, scale_mode)
     cache = {}
     if use_cache and os.path.exists(CACHE):
@@ -56,19 +68,25 @@ def tune(scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_ADAGSCALE, K: fl
             cache = json.load(open(CACHE))
         except (OSError, ValueError):
             cache = {}
-        if key in cache:
+        if key in cache and all(k in cache[key] for k in KNOBS):
             return cache[key]
     table = []
     capacity = None
-    for cand in candidates or CANDIDATES:
+
+    def timed(cand):
+        nonlocal capacity
         r = R.Renderer(scene, cams, scale_mode, K, lut, capacity=capacity, keep_state=False, **cand)
         capacity = r.capacity
         ms = _time_forward(r, warmup, reps)
-        table.append(dict(cand, ms=ms))
         del r
-    best = min(table, key=lambda t: t["ms"])
-    out = dict(digit_bits=best["digit_bits"], presort=best["presort"], pair_rank_or=best["pair_rank_or"],
-               emit_two_pass=best.get("emit_two_pass", True), ms=best["ms"], table=table)
+        table.append(dict(cand, ms=ms))
+        return ms
+
+    best = min((dict(DEFAULTS, **c) for c in (candidates or CANDIDATES)), key=timed)
+    stage = {k: best[k] for k in KNOBS if k not in ("blend_flags", "sort_wide")}
+    best = min((dict(stage, **sh) for sh in (shapes if shapes is not None else SHAPES)), key=timed)
+    ms = min(t["ms"] for t in table if all(t.get(k, DEFAULTS.get(k)) == best[k] for k in KNOBS))
+    out = dict({k: best[k] for k in KNOBS}, ms=ms, table=table)
     if use_cache:
         cache[key] = out
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)

@@ -22,6 +22,7 @@ AGS_MAX_LUT_BINS = 32
 AGS_MAX_PAIRS = 1 << 30
 AGS_SCALE_PLAIN, AGS_SCALE_ADAGSCALE = 0, 1
 AGS_TILE_SQUARE, AGS_TILE_ELLIPSE = 0, 1
+AGS_BLEND_ROWS2, AGS_BLEND_BATCH64 = 1, 2     # ags_params.blend_flags (launch shape of the blend)
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "pair capacity exceeded", 3: "bounded device wait timed out",
                 4: "CUDA error", 5: "non-finite Gaussian parameters culled"}
 AGS_OK, AGS_ERR_INVALID_ARG, AGS_ERR_CAPACITY, AGS_ERR_TIMEOUT, AGS_ERR_CUDA, AGS_ERR_NUMERIC = range(6)
@@ -50,7 +51,7 @@ class AgsCamera(ctypes.Structure):
 class AgsParams(ctypes.Structure):
     _fields_ = [("scale_mode", _I32), ("sh_degree", _I32), ("lut_bins", _I32), ("K", _F), ("tau", _F),
                 ("t_min", _F), ("alpha_max", _F), ("lut_depth_max", _F), ("lut", _F * AGS_MAX_LUT_BINS),
-                ("bg", _F * 3), ("tile_test", _I32)]
+                ("bg", _F * 3), ("tile_test", _I32), ("blend_flags", _I32)]
 
 
 class AgsGaussians(ctypes.Structure):
@@ -160,10 +161,10 @@ def cameras(cams) -> ctypes.Array:
 
 def params(scale_mode: int = AGS_SCALE_PLAIN, K: float = 0.0, lut=None, sh_degree: int = 3, bg=(0.0, 0.0, 0.0),
            tau: float = 1.0 / 255.0, t_min: float = 1e-4, alpha_max: float = 0.99, lut_bins: int = 20,
-           lut_depth_max: float = 100.0, tile_test: int = AGS_TILE_SQUARE) -> AgsParams:
+           lut_depth_max: float = 100.0, tile_test: int = AGS_TILE_SQUARE, blend_flags: int = 0) -> AgsParams:
     p = AgsParams()
     p.scale_mode, p.sh_degree, p.lut_bins = int(scale_mode), int(sh_degree), int(lut_bins)
-    p.tile_test = int(tile_test)
+    p.tile_test, p.blend_flags = int(tile_test), int(blend_flags)
     p.K, p.tau, p.t_min, p.alpha_max, p.lut_depth_max = float(K), float(tau), float(t_min), float(alpha_max), \
         float(lut_depth_max)
     lut = np.ones(lut_bins, dtype=np.float32) if lut is None else np.asarray(lut, dtype=np.float32)
@@ -294,6 +295,7 @@ def ags_sort_workspace_bytes(capacity: int) -> int:
 AGS_SORT_IDENTITY_VALUES = 1
 AGS_SORT_DISCARD_KEYS = 2
 AGS_SORT_RANK_OR = 4
+AGS_SORT_WIDE_BLOCK = 8       # 32-bit key passes on 512 x 8 partitions instead of 256 x 16
 AGS_SORT_TEST_STALL = 256     # tests only: a look-back partition that never publishes
 
 

@@ -45,7 +45,7 @@ struct CamBatch {
 };
 
 struct DevParams {
-  int scale_mode, sh_degree, lut_bins, tile_test;
+  int scale_mode, sh_degree, lut_bins, tile_test, blend_flags;
   float K, tau, t_min, alpha_max, lut_scale;   // lut_scale = lut_bins / lut_depth_max
   float lut[AGS_MAX_LUT_BINS];
   float bg[3];

@@ -42,6 +42,7 @@ ags_status build_params(const ags_params* p, DevParams* out) {
   if (p->sh_degree < 0 || p->sh_degree > 3) return AGS_ERR_INVALID_ARG;
   if (p->lut_bins < 1 || p->lut_bins > AGS_MAX_LUT_BINS) return AGS_ERR_INVALID_ARG;
   if (p->tile_test != AGS_TILE_SQUARE && p->tile_test != AGS_TILE_ELLIPSE) return AGS_ERR_INVALID_ARG;
+  if (p->blend_flags & ~(AGS_BLEND_ROWS2 | AGS_BLEND_BATCH64)) return AGS_ERR_INVALID_ARG;
   if (!(p->K >= 0.f) || !std::isfinite(p->K)) return AGS_ERR_INVALID_ARG;
   if (!(p->tau > 0.f) || !(p->t_min >= 0.f) || !(p->alpha_max > 0.f) || !(p->lut_depth_max > 0.f))
     return AGS_ERR_INVALID_ARG;
@@ -50,6 +51,7 @@ ags_status build_params(const ags_params* p, DevParams* out) {
   out->sh_degree = p->sh_degree;
   out->lut_bins = p->lut_bins;
   out->tile_test = p->tile_test;
+  out->blend_flags = p->blend_flags;
   out->K = p->K; out->tau = p->tau; out->t_min = p->t_min; out->alpha_max = p->alpha_max;
   out->lut_scale = (float)p->lut_bins / p->lut_depth_max;
   for (int i = 0; i < AGS_MAX_LUT_BINS; i++) out->lut[i] = p->lut[i];

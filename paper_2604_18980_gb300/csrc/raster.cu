@@ -3,7 +3,9 @@
 //
 // One 64-thread CTA per 16x16 tile of each view: two warps, each an 8x16
 // pixel block, each lane one column and four rows (y, y+4, y+8, y+12) that
-// share the splat's dx terms.  The warps run independently (no CTA barrier):
+// share the splat's dx terms (ags_params.blend_flags selects 8x8 blocks --
+// four warps, two rows a lane -- and 64-splat batches instead, for the
+// autotuner).  The warps run independently (no CTA barrier):
 // a warp stages its tile's depth-ordered pairs 32 at a time, one per lane --
 // gather of the 48-byte splat record (the next 32 are already in flight),
 // conversion to the log2 form of Eq. 1, and the exact test whether the
@@ -19,11 +21,6 @@
 #include "blend.cuh"
 
 namespace ags {
-
-constexpr int kBlendWarps = 2;                   // per tile: warp w owns columns 8w .. 8w+7
-constexpr int kBlendThreads = 32 * kBlendWarps;
-constexpr int kRowsPerLane = 4;                  // rows y + 4k of one column
-constexpr int kBlockH = 4 * kRowsPerLane;        // 16: the warp's block is 8 x 16 pixels
 
 // One pixel's step over one splat, in PTX so that the updates stay
 // predicated FMAs: ok = (T > 0 and q >= log2 tau); T' = fma(-alpha, T, T);
@@ -180,32 +177,38 @@ __device__ __forceinline__ void blend_step_state(float q, const BlendConst& bc, 
 
 // kStats: count evaluations and blends; kMaxT: calibration output; kState:
 // each pixel's final T and last blended position (for the backward).  The
-// benchmark's kernel is the <false, false, false> instance.
-template <bool kStats, bool kMaxT, bool kState>
-__global__ void __launch_bounds__(kBlendThreads)
+// shape: kRows rows per lane (4: 8x16-pixel warp blocks, two warps a tile;
+// 2: 8x8 blocks, four warps) and kBatch splats staged per lane and round (the
+// warp's tile batch is 32 kBatch splats, the next batch in flight meanwhile).
+// The benchmark's kernel is the <false, false, false, 4, 1> instance.
+template <bool kStats, bool kMaxT, bool kState, int kRows, int kBatch>
+__global__ void __launch_bounds__(256 / kRows)
 raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
               int W, int H, int gx, int tiles_per_view, BlendConst bc, float* __restrict__ image,
               float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ max_T_bits,
               unsigned long long* stats) {
   constexpr bool kRec = kStats || kMaxT || kState;
-  __shared__ float4 s_a[kBlendWarps][32];    // u v a2 b2
-  __shared__ float4 s_b[kBlendWarps][32];    // c2 log2(opacity) r g
-  __shared__ float s_c[kBlendWarps][32];     // b
-  __shared__ uint32_t s_e[kBlendWarps][kMaxT ? 32 : 1];
+  constexpr int kWarps = 8 / kRows;
+  constexpr int kBH = 4 * kRows;                 // warp block: 8 columns x kBH rows
+  constexpr int kStage = 32 * kBatch;
+  __shared__ float4 s_a[kWarps][kStage];    // u v a2 b2
+  __shared__ float4 s_b[kWarps][kStage];    // c2 log2(opacity) r g
+  __shared__ float s_c[kWarps][kStage];     // b
+  __shared__ uint32_t s_e[kWarps][kMaxT ? kStage : 1];
 
   const int tile = blockIdx.x;
   const int view = tile / tiles_per_view;
   const int lt = tile - view * tiles_per_view;
   const int ty = lt / gx, tx = lt - ty * gx;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int bx0 = tx * kTile + 8 * warp, by0 = ty * kTile;
+  const int bx0 = tx * kTile + 8 * (warp & 1), by0 = ty * kTile + kBH * (warp >> 1);
   const int px = bx0 + (lane & 7);
   const int py = by0 + (lane >> 3);
   const float fpx = (float)px;
-  float fpy[kRowsPerLane], T[kRowsPerLane], cr[kRowsPerLane], cg[kRowsPerLane], cb[kRowsPerLane];
-  uint32_t last[kRowsPerLane], stop_at[kRowsPerLane];
+  float fpy[kRows], T[kRows], cr[kRows], cg[kRows], cb[kRows];
+  uint32_t last[kRows], stop_at[kRows];
 #pragma unroll
-  for (int k = 0; k < kRowsPerLane; k++) {
+  for (int k = 0; k < kRows; k++) {
     fpy[k] = (float)(py + 4 * k);
     T[k] = (px < W && py + 4 * k < H) ? 1.f : -1.f;      // negative: nothing to blend
     cr[k] = cg[k] = cb[k] = 0.f;
@@ -220,117 +223,135 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
   const float l2clamp = __log2f(bc.alpha_max) - 1e-3f;   // opacities above this take the clamped step
   uint32_t blends = 0u, walked_total = 0u;
 
-  // the first 32 records in flight
-  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
-  uint32_t ne = 0u;
-  if (start + lane < end) {
-    ne = __ldg(vals + start + lane);
-    const float4* rec = splat + (size_t)ne * 3;
-    n0 = __ldg(rec); n1 = __ldg(rec + 1); n2 = __ldg(rec + 2);
+  // the first batch in flight
+  float4 n0[kBatch], n1[kBatch], n2[kBatch];
+  uint32_t ne[kBatch];
+#pragma unroll
+  for (int i = 0; i < kBatch; i++) {
+    n0[i] = n1[i] = n2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    ne[i] = 0u;
+    if (start + 32 * i + lane < end) {
+      ne[i] = __ldg(vals + start + 32 * i + lane);
+      const float4* rec = splat + (size_t)ne[i] * 3;
+      n0[i] = __ldg(rec); n1[i] = __ldg(rec + 1); n2[i] = __ldg(rec + 2);
+    }
   }
-  for (uint32_t bb = start; bb < end; bb += 32) {
+  for (uint32_t bb = start; bb < end; bb += kStage) {
     bool alive = false;
 #pragma unroll
-    for (int k = 0; k < kRowsPerLane; k++) alive = alive || T[k] > 0.f;
+    for (int k = 0; k < kRows; k++) alive = alive || T[k] > 0.f;
     if (!__any_sync(0xffffffffu, alive)) break;
-    const float4 r0 = n0, r1 = n1, r2 = n2;
-    const uint32_t e = ne;
-    bool hit = false;
-    if (bb + lane < end) {
-      Staged st;
-      stage_record(r0, r1, r2, st);
-      sa[lane] = st.a;
-      sb[lane] = st.b;
-      sc[lane] = st.c;
-      if (kMaxT) s_e[warp][lane] = e;
-      hit = ellipse_reaches(r0.x - (float)bx0, r0.y - (float)by0, 7.f, (float)(kBlockH - 1),
-                            reach_r2n(st.b.y, bc.l2tau), r2.z, r2.w, r0.z, r0.w, r1.x);
+    unsigned m[kBatch];
+#pragma unroll
+    for (int i = 0; i < kBatch; i++) {
+      bool hit = false;
+      if (bb + 32 * i + lane < end) {
+        const float4 r0 = n0[i], r1 = n1[i], r2 = n2[i];
+        Staged st;
+        stage_record(r0, r1, r2, st);
+        sa[32 * i + lane] = st.a;
+        sb[32 * i + lane] = st.b;
+        sc[32 * i + lane] = st.c;
+        if (kMaxT) s_e[warp][32 * i + lane] = ne[i];
+        hit = ellipse_reaches(r0.x - (float)bx0, r0.y - (float)by0, 7.f, (float)(kBH - 1),
+                              reach_r2n(st.b.y, bc.l2tau), r2.z, r2.w, r0.z, r0.w, r1.x);
+      }
+      m[i] = __ballot_sync(0xffffffffu, hit);
     }
-    if (bb + 32 + lane < end) {      // the next 32 records, in flight while these are blended
-      ne = __ldg(vals + bb + 32 + lane);
-      const float4* rec = splat + (size_t)ne * 3;
-      n0 = __ldg(rec); n1 = __ldg(rec + 1); n2 = __ldg(rec + 2);
+#pragma unroll
+    for (int i = 0; i < kBatch; i++) {   // the next batch, in flight while this one is blended
+      if (bb + kStage + 32 * i + lane < end) {
+        ne[i] = __ldg(vals + bb + kStage + 32 * i + lane);
+        const float4* rec = splat + (size_t)ne[i] * 3;
+        n0[i] = __ldg(rec); n1[i] = __ldg(rec + 1); n2[i] = __ldg(rec + 2);
+      }
     }
-    unsigned mask = __ballot_sync(0xffffffffu, hit);
     __syncwarp();
     int walked = 0;
-    if (kStats) walked_total += (uint32_t)__popc(mask);
-    while (mask) {
-      const int j = __ffs(mask) - 1;
-      mask &= mask - 1;
-      Staged s;
-      s.a = sa[j];
-      s.b = sb[j];
-      const float cbl = sc[j];
-      const float dx = __fsub_rn(s.a.x, fpx);
-      float P, Bx;
-      splat_qx(s, dx, P, Bx);
-      const bool clamp = s.b.y > l2clamp;
-      if (!kRec) {
-        if (clamp) {
+    bool done = false;
 #pragma unroll
-          for (int k = 0; k < kRowsPerLane; k++)
-            blend_step<true>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc.l2tau, bc.alpha_max, bc.t_min, s.b.z,
-                             s.b.w, cbl, T[k], cr[k], cg[k], cb[k]);
-        } else {
+    for (int i = 0; i < kBatch; i++) {
+      unsigned mask = m[i];
+      if (kStats) walked_total += (uint32_t)__popc(mask);
+      while (mask) {
+        const int j = 32 * i + __ffs(mask) - 1;
+        mask &= mask - 1;
+        Staged s;
+        s.a = sa[j];
+        s.b = sb[j];
+        const float cbl = sc[j];
+        const float dx = __fsub_rn(s.a.x, fpx);
+        float P, Bx;
+        splat_qx(s, dx, P, Bx);
+        const bool clamp = s.b.y > l2clamp;
+        if (!kRec) {
+          if (clamp) {
 #pragma unroll
-          for (int k = 0; k < kRowsPerLane; k++)
-            blend_step<false>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc.l2tau, bc.alpha_max, bc.t_min, s.b.z,
-                              s.b.w, cbl, T[k], cr[k], cg[k], cb[k]);
-        }
-      } else if (kState && !kStats && !kMaxT) {   // the backward's forward: last blended position only
-        const uint32_t pos1 = bb - start + (uint32_t)j + 1u;
-        if (clamp) {
+            for (int k = 0; k < kRows; k++)
+              blend_step<true>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc.l2tau, bc.alpha_max, bc.t_min,
+                               s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k]);
+          } else {
 #pragma unroll
-          for (int k = 0; k < kRowsPerLane; k++)
-            blend_step_state<true>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc, s.b.z, s.b.w, cbl, T[k], cr[k],
-                                   cg[k], cb[k], last[k], pos1);
-        } else {
-#pragma unroll
-          for (int k = 0; k < kRowsPerLane; k++)
-            blend_step_state<false>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc, s.b.z, s.b.w, cbl, T[k], cr[k],
-                                    cg[k], cb[k], last[k], pos1);
-        }
-      } else {
-        const uint32_t pos1 = bb - start + (uint32_t)j + 1u;    // 1-based position in the tile's list
-        uint32_t mt = 0u;
-#pragma unroll
-        for (int k = 0; k < kRowsPerLane; k++) {
-          const float Tb = T[k];
-          const float q = splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k]));
-          uint32_t bl, stp;
-          if (clamp)
-            blend_step_rec<true>(q, bc, s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k], bl, stp);
-          else
-            blend_step_rec<false>(q, bc, s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k], bl, stp);
-          if (kStats) {
-            blends += bl;
-            stop_at[k] = stp ? pos1 : stop_at[k];
+            for (int k = 0; k < kRows; k++)
+              blend_step<false>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc.l2tau, bc.alpha_max, bc.t_min,
+                                s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k]);
           }
-          if (kState) last[k] = bl ? pos1 : last[k];
-          if (kMaxT) mt = max(mt, bl ? __float_as_uint(Tb) : 0u);
-        }
-        if (kMaxT) {   // calibration: per-Gaussian max T before blending (warp max, one atomic)
-          const uint32_t m = __reduce_max_sync(0xffffffffu, mt);
-          if (lane == 0 && m) atomicMax(max_T_bits + s_e[warp][j], m);
-        }
-      }
-      if ((++walked & 3) == 0) {
-        bool al = false;
+        } else if (kState && !kStats && !kMaxT) {   // the backward's forward: last blended position only
+          const uint32_t pos1 = bb - start + (uint32_t)j + 1u;
+          if (clamp) {
 #pragma unroll
-        for (int k = 0; k < kRowsPerLane; k++) al = al || T[k] > 0.f;
-        if (!__any_sync(0xffffffffu, al)) {
-          if (kStats) walked_total -= (uint32_t)__popc(mask);    // not walked
-          break;
+            for (int k = 0; k < kRows; k++)
+              blend_step_state<true>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc, s.b.z, s.b.w, cbl, T[k],
+                                     cr[k], cg[k], cb[k], last[k], pos1);
+          } else {
+#pragma unroll
+            for (int k = 0; k < kRows; k++)
+              blend_step_state<false>(splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k])), bc, s.b.z, s.b.w, cbl, T[k],
+                                      cr[k], cg[k], cb[k], last[k], pos1);
+          }
+        } else {
+          const uint32_t pos1 = bb - start + (uint32_t)j + 1u;    // 1-based position in the tile's list
+          uint32_t mt = 0u;
+#pragma unroll
+          for (int k = 0; k < kRows; k++) {
+            const float Tb = T[k];
+            const float q = splat_qy(s, P, Bx, __fsub_rn(s.a.y, fpy[k]));
+            uint32_t bl, stp;
+            if (clamp)
+              blend_step_rec<true>(q, bc, s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k], bl, stp);
+            else
+              blend_step_rec<false>(q, bc, s.b.z, s.b.w, cbl, T[k], cr[k], cg[k], cb[k], bl, stp);
+            if (kStats) {
+              blends += bl;
+              stop_at[k] = stp ? pos1 : stop_at[k];
+            }
+            if (kState) last[k] = bl ? pos1 : last[k];
+            if (kMaxT) mt = max(mt, bl ? __float_as_uint(Tb) : 0u);
+          }
+          if (kMaxT) {   // calibration: per-Gaussian max T before blending (warp max, one atomic)
+            const uint32_t mx = __reduce_max_sync(0xffffffffu, mt);
+            if (lane == 0 && mx) atomicMax(max_T_bits + s_e[warp][j], mx);
+          }
+        }
+        if ((++walked & 3) == 0) {
+          bool al = false;
+#pragma unroll
+          for (int k = 0; k < kRows; k++) al = al || T[k] > 0.f;
+          if (!__any_sync(0xffffffffu, al)) {
+            if (kStats) walked_total -= (uint32_t)__popc(mask);    // not walked
+            done = true;
+            break;
+          }
         }
       }
+      if (done) break;     // the later masks of this batch were never counted
     }
     __syncwarp();
   }
   const size_t hw = (size_t)W * H;
   unsigned long long evals = 0ull;
 #pragma unroll
-  for (int k = 0; k < kRowsPerLane; k++) {
+  for (int k = 0; k < kRows; k++) {
     const int y = py + 4 * k;
     if (px < W && y < H) {
       const float Tf = fabsf(T[k]);
@@ -350,10 +371,24 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
     if (lane == 0) {
       atomicAdd(stats, e1);
       atomicAdd(stats + 1, e2);
-      // pixel-pair slots the kernel walked: each walked splat against the warp's 8 x 16 pixels
-      atomicAdd(stats + 2, (unsigned long long)walked_total * (8ull * kBlockH));
+      // pixel-pair slots the kernel walked: each walked splat against the warp's 8 x kBH pixels
+      atomicAdd(stats + 2, (unsigned long long)walked_total * (8ull * kBH));
     }
   }
+}
+
+typedef void (*RasterFn)(const float4*, const uint32_t*, const uint2*, int, int, int, int, BlendConst, float*, float*,
+                         uint32_t*, uint32_t*, unsigned long long*);
+
+template <int kRows, int kBatch>
+RasterFn pick_raster(bool st, bool mt, bool state) {
+  if (state)
+    return st ? (mt ? raster_kernel<true, true, true, kRows, kBatch> : raster_kernel<true, false, true, kRows, kBatch>)
+              : (mt ? raster_kernel<false, true, true, kRows, kBatch>
+                    : raster_kernel<false, false, true, kRows, kBatch>);
+  return st ? (mt ? raster_kernel<true, true, false, kRows, kBatch> : raster_kernel<true, false, false, kRows, kBatch>)
+            : (mt ? raster_kernel<false, true, false, kRows, kBatch>
+                  : raster_kernel<false, false, false, kRows, kBatch>);
 }
 
 __global__ void lut_kernel(const float* __restrict__ max_T, const float* __restrict__ depth, int64_t count, int bins,
@@ -395,11 +430,16 @@ extern "C" ags_status ags_rasterize(const ags_projected* proj, int64_t n, const 
   if ((uintptr_t)proj->splat & 15u) return AGS_ERR_INVALID_ARG;
   const int tiles_per_view = cb.c[0].gx * cb.c[0].gy;
   BlendConst bc = make_blend_const(dp);
-  auto kern = n_contrib ? (stats ? (max_T ? raster_kernel<true, true, true> : raster_kernel<true, false, true>)
-                                 : (max_T ? raster_kernel<false, true, true> : raster_kernel<false, false, true>))
-                       : (stats ? (max_T ? raster_kernel<true, true, false> : raster_kernel<true, false, false>)
-                                : (max_T ? raster_kernel<false, true, false> : raster_kernel<false, false, false>));
-  kern<<<(unsigned)(tiles_per_view * views), kBlendThreads, 0, (cudaStream_t)stream>>>(
+  const bool st = stats != nullptr, mt = max_T != nullptr, state = n_contrib != nullptr;
+  RasterFn kern;
+  switch (dp.blend_flags) {
+    case AGS_BLEND_ROWS2: kern = pick_raster<2, 1>(st, mt, state); break;
+    case AGS_BLEND_BATCH64: kern = pick_raster<4, 2>(st, mt, state); break;
+    case AGS_BLEND_ROWS2 | AGS_BLEND_BATCH64: kern = pick_raster<2, 2>(st, mt, state); break;
+    default: kern = pick_raster<4, 1>(st, mt, state); break;
+  }
+  const unsigned threads = (dp.blend_flags & AGS_BLEND_ROWS2) ? 128u : 64u;   // 256 / rows per lane
+  kern<<<(unsigned)(tiles_per_view * views), threads, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const float4*>(proj->splat), sorted_vals, reinterpret_cast<const uint2*>(ranges),
       cb.c[0].W, cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, image, final_T, n_contrib,
       reinterpret_cast<uint32_t*>(max_T), reinterpret_cast<unsigned long long*>(stats));

@@ -640,7 +640,7 @@ static cudaError_t launch_passes(K*& kin, uint32_t*& vin, K* kout, uint32_t* vou
     const int identity = (p == 0 && (flags & AGS_SORT_IDENTITY_VALUES)) ? 1 : 0;
     const bool last = p == passes - 1;
     K* ko = (last && (flags & AGS_SORT_DISCARD_KEYS)) ? nullptr : kout;
-    if (sizeof(K) == 4 && RADIX <= 256) {
+    if (sizeof(K) == 4 && RADIX <= 256 && !(flags & AGS_SORT_WIDE_BLOCK)) {
       e = launch_lean<RADIX <= 256 ? RADIX : 256>(rank_or != 0, dim3((unsigned)parts), st,
                                                   reinterpret_cast<const uint32_t*>(kin), vin,
                                                   reinterpret_cast<uint32_t*>(ko), vout, d_num_pairs, capacity,
@@ -688,7 +688,8 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
   if (!d_num_pairs || !d_status || capacity < 0 || capacity >= AGS_MAX_PAIRS) return AGS_ERR_INVALID_ARG;
   if (begin_bit < 0 || end_bit > kKeyBits || begin_bit > end_bit || digit_bits < 4 || digit_bits > 9)
     return AGS_ERR_INVALID_ARG;
-  if (flags & ~(AGS_SORT_IDENTITY_VALUES | AGS_SORT_DISCARD_KEYS | AGS_SORT_RANK_OR | AGS_SORT_TEST_STALL))
+  if (flags & ~(AGS_SORT_IDENTITY_VALUES | AGS_SORT_DISCARD_KEYS | AGS_SORT_RANK_OR | AGS_SORT_WIDE_BLOCK |
+                AGS_SORT_TEST_STALL))
     return AGS_ERR_INVALID_ARG;
   const int passes = (end_bit - begin_bit + digit_bits - 1) / digit_bits;
   if (passes > kMaxPasses) return AGS_ERR_INVALID_ARG;

@@ -86,7 +86,8 @@ class Renderer:
                  sh_degree: int = 3, bg=(0.0, 0.0, 0.0), capacity: int | None = None, digit_bits: int = 9,
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
                  presort: bool = True, pair_rank_or: bool = True, emit_two_pass: bool = True,
-                 keep_state: bool = True, tile_test: int = B.AGS_TILE_SQUARE, view_major: bool | None = None):
+                 keep_state: bool = True, tile_test: int = B.AGS_TILE_SQUARE, view_major: bool | None = None,
+                 blend_flags: int = 0, sort_wide: bool = False):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -99,6 +100,8 @@ class Renderer:
         self.pair_rank_or = pair_rank_or
         self.emit_two_pass = emit_two_pass
         self.tile_test = tile_test
+        self.blend_flags = int(blend_flags)      # AGS_BLEND_*: launch shape of the blend
+        self.sort_flags = B.AGS_SORT_WIDE_BLOCK if sort_wide else 0
         self.emit_flags = B.AGS_EMIT_ELLIPSE if tile_test == B.AGS_TILE_ELLIPSE else 0
         self.tile_bits = max(1, (self.T - 1).bit_length())
         if view_major is None:
@@ -145,11 +148,12 @@ class Renderer:
     # -- configuration -------------------------------------------------------
     def set_params(self, scale_mode=None, K=None, lut=None, sh_degree=None, bg=None):
         prev = getattr(self, "_pargs", dict(scale_mode=B.AGS_SCALE_PLAIN, K=0.0, lut=None, sh_degree=3,
-                                            bg=(0.0, 0.0, 0.0), tile_test=getattr(self, "tile_test", 0)))
+                                            bg=(0.0, 0.0, 0.0), tile_test=getattr(self, "tile_test", 0),
+                                            blend_flags=getattr(self, "blend_flags", 0)))
         args = dict(scale_mode=prev["scale_mode"] if scale_mode is None else scale_mode,
                     K=prev["K"] if K is None else K, lut=prev["lut"] if lut is None else lut,
                     sh_degree=prev["sh_degree"] if sh_degree is None else sh_degree,
-                    bg=prev["bg"] if bg is None else bg, tile_test=prev["tile_test"])
+                    bg=prev["bg"] if bg is None else bg, tile_test=prev["tile_test"], blend_flags=prev["blend_flags"])
         self._pargs = args
         self.params = B.params(**args)
 
@@ -210,7 +214,7 @@ class Renderer:
             passes, db = digit_plan(self.dsort_end, self.digit_bits)
             alt = B.ags_sort32(self.dkey, self.order, self.dkey_alt, self.order_alt, self.n_visible,
                                self.V * self.n, 0, self.dsort_end, db, None, 0, self.status, self.ws_dsort,
-                               flags=B.AGS_SORT_DISCARD_KEYS)
+                               flags=B.AGS_SORT_DISCARD_KEYS | self.sort_flags)
             self.emit_order = self.order_alt if alt else self.order
             if self.view_major:
                 # then stably by view: the views one after the other, each in
@@ -220,7 +224,7 @@ class Renderer:
                 B.ags_view_keys(self.emit_order, self.n_visible, self.V * self.n, self.n, self.dkey)
                 alt2 = B.ags_sort32(self.dkey, self.emit_order, self.dkey_alt, other, self.n_visible, self.V * self.n,
                                     0, vb, min(9, max(4, vb)), None, 0, self.status, self.ws_dsort,
-                                    flags=B.AGS_SORT_DISCARD_KEYS)
+                                    flags=B.AGS_SORT_DISCARD_KEYS | self.sort_flags)
                 self.emit_order = other if alt2 else self.emit_order
 
     def emit(self):
@@ -238,7 +242,7 @@ class Renderer:
         """Stable sort of the pairs by tile (and depth); only the values and the
         per-tile ranges are kept."""
         _, db = self.sort_plan()
-        flags = B.AGS_SORT_DISCARD_KEYS | (B.AGS_SORT_RANK_OR if self.pair_rank_or else 0)
+        flags = B.AGS_SORT_DISCARD_KEYS | (B.AGS_SORT_RANK_OR if self.pair_rank_or else 0) | self.sort_flags
         if self.view_major:
             alt = B.ags_sort_tiles(self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_pairs, self.capacity,
                                    self.tile_bits, db, self.ranges, self.V, self.T, self.status, self.ws_sort,

@@ -524,7 +524,39 @@ def test_autotuner_candidates_render_identically():
         np.testing.assert_array_equal(k, lists[0][0])
         np.testing.assert_array_equal(v, lists[0][1])
     best = autotune.tune(sc, cams, 1, 0.3, use_cache=False, warmup=1, reps=2)
-    assert best["digit_bits"] in (7, 8, 9) and len(best["table"]) == len(autotune.CANDIDATES)
+    assert best["digit_bits"] in (7, 8, 9)
+    assert len(best["table"]) == len(autotune.CANDIDATES) + len(autotune.SHAPES)
+    assert all(k in best for k in autotune.KNOBS)
+
+
+@pytest.mark.parametrize("digit_bits", [8, 9])
+def test_launch_shapes_give_identical_outputs(digit_bits):
+    """The block shapes the autotuner sweeps -- the blend's 8x16 or 8x8 warp
+    blocks and 32- or 64-splat batches, the 32-bit sort passes on 256 x 16 or
+    512 x 8 partitions -- change no output: image, final T, last blended
+    position, calibration max T, the evaluation and blend counts, and the
+    sorted pair lists, bit for bit.  A ragged frame (tiles cut at the right and
+    bottom edges), two views, and tiles long enough for several batches."""
+    from paper_2604_18980_gb300 import autotune
+    scene, cams = _c1(n=12000, W=200, H=150, views=2)
+    sc = R.scene_to_device(scene)
+    ref = None
+    for sh in autotune.SHAPES:
+        r = R.Renderer(sc, cams, 1, 0.3, want_stats=True, digit_bits=digit_bits, **sh)
+        max_T = torch.zeros(r.V * r.n, dtype=torch.float32, device="cuda")
+        img = r.forward(max_T=max_T).clone()
+        r.check()
+        out = dict(img=img, T=r.final_T.clone(), nc=r.n_contrib.clone(), maxT=max_T, st=r.stats[:2].clone(),
+                   lists=gpu_pairs(r))
+        if ref is None:
+            ref = out
+            rg = r.ranges.view(-1, 2).long()
+            assert int(ref["st"][0]) > 0 and int((rg[:, 1] - rg[:, 0]).max()) > 2 * 64   # several batches a tile
+            continue
+        for k in ("img", "T", "nc", "maxT", "st"):
+            assert torch.equal(out[k], ref[k]), (sh, k)
+        np.testing.assert_array_equal(out["lists"][0], ref["lists"][0])
+        np.testing.assert_array_equal(out["lists"][1], ref["lists"][1])
 
 
 @pytest.mark.parametrize("mode,K", [(0, 0.0), (1, 0.3)])

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_header(lib):
     # sizes implied by the header's field lists (all 4- or 8-byte fields)
     assert ctypes.sizeof(B.AgsCamera) == 4 * (2 + 4 + 12 + 3 + 1)
-    assert ctypes.sizeof(B.AgsParams) == 4 * (3 + 5 + 32 + 3 + 1)
+    assert ctypes.sizeof(B.AgsParams) == 4 * (3 + 5 + 32 + 3 + 2)
     assert ctypes.sizeof(B.AgsGaussians) == 8 * 6
     assert ctypes.sizeof(B.AgsProjected) == 8 * 6
 
@@ -93,6 +93,10 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
     bad = B.params(tile_test=2)
     assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
+    bad = B.params(blend_flags=4)      # a launch-shape bit the blend does not know
+    assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(bad), ctypes.byref(pr), st, None) == 1
+    assert L.ags_rasterize(ctypes.byref(pr), 0, None, ctypes.c_void_p(256), cam, 1, ctypes.byref(bad),
+                           ctypes.c_void_p(512), None, None, None, None, st, None) == 1
     # null outputs
     assert L.ags_preprocess(ctypes.byref(g), cam, 1, ctypes.byref(par), ctypes.byref(pr), st, None) == 1
     # sort: bad digit width, capacity beyond the limit, missing workspace
@@ -104,7 +108,7 @@ def test_invalid_arguments_rejected_on_host(lib):
                       None, 0, None) == 1
     assert L.ags_sort(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
                       10, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st, None, 0, None) == 1
-    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 8, 8, None, 0, ctypes.byref(alt), st, None, 0,
+    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 8, 16, None, 0, ctypes.byref(alt), st, None, 0,
                       None) == 1
     # 32-bit sort: end bit beyond the key, unknown flag, unaligned keys
     assert L.ags_sort32(None, None, None, None, npairs, 10, 0, 33, 8, 0, None, 0, ctypes.byref(alt), st, None, 0,
