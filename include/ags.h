@@ -75,8 +75,20 @@ typedef enum {
   AGS_ERR_CAPACITY = 2,     /* more pairs than `capacity`; detail = pairs needed */
   AGS_ERR_TIMEOUT = 3,      /* a bounded device wait gave up; detail = stage id */
   AGS_ERR_CUDA = 4,         /* a CUDA launch or runtime call failed */
-  AGS_ERR_NUMERIC = 5       /* non-finite Gaussian parameters were culled; detail = count */
+  AGS_ERR_NUMERIC = 5,      /* non-finite Gaussian parameters were culled; detail = count */
+  AGS_ERR_BOUNDS = 6        /* debug builds (AGS_DEBUG) only: an index read from the inputs
+                             * (a pair value, a tile range, an emission order entry) was out
+                             * of range and its access skipped; detail = the first failed
+                             * check's id (AGS_CHECK_*), d_status[3] = bit (1 << id) of every
+                             * check that failed */
 } ags_status;
+
+/* Check ids of AGS_ERR_BOUNDS. */
+#define AGS_CHECK_BLEND_RANGE 1      /* ags_rasterize: a tile range with start > end */
+#define AGS_CHECK_BLEND_VALUE 2      /* ags_rasterize: a pair value >= views * n */
+#define AGS_CHECK_BACKWARD_RANGE 3   /* ags_rasterize_backward: a tile range with start > end */
+#define AGS_CHECK_BACKWARD_VALUE 4   /* ags_rasterize_backward: a pair value >= views * n */
+#define AGS_CHECK_EMIT_ORDER 5       /* emission: an order entry >= views * n */
 
 typedef enum { AGS_SCALE_PLAIN = 0, AGS_SCALE_ADAGSCALE = 1 } ags_scale_mode;
 
@@ -156,7 +168,8 @@ typedef struct {
                                ags_emit_tile_pairs. */
 } ags_projected;
 
-/* Device status block: int64_t[4] = {status code, detail, non-finite count, reserved}. */
+/* Device status block: int64_t[4] = {status code, detail, non-finite count,
+ * failed-check bits (AGS_DEBUG builds; zero otherwise)}. */
 
 /* ---------------------------------------------------------------------- */
 

@@ -24,8 +24,12 @@ AGS_SCALE_PLAIN, AGS_SCALE_ADAGSCALE = 0, 1
 AGS_TILE_SQUARE, AGS_TILE_ELLIPSE = 0, 1
 AGS_BLEND_ROWS2, AGS_BLEND_BATCH64 = 1, 2     # ags_params.blend_flags (launch shape of the blend)
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "pair capacity exceeded", 3: "bounded device wait timed out",
-                4: "CUDA error", 5: "non-finite Gaussian parameters culled"}
-AGS_OK, AGS_ERR_INVALID_ARG, AGS_ERR_CAPACITY, AGS_ERR_TIMEOUT, AGS_ERR_CUDA, AGS_ERR_NUMERIC = range(6)
+                4: "CUDA error", 5: "non-finite Gaussian parameters culled",
+                6: "index out of range (debug build check)"}
+AGS_OK, AGS_ERR_INVALID_ARG, AGS_ERR_CAPACITY, AGS_ERR_TIMEOUT, AGS_ERR_CUDA, AGS_ERR_NUMERIC, AGS_ERR_BOUNDS = range(7)
+# check ids of AGS_ERR_BOUNDS (debug builds)
+AGS_CHECK_BLEND_RANGE, AGS_CHECK_BLEND_VALUE, AGS_CHECK_BACKWARD_RANGE, AGS_CHECK_BACKWARD_VALUE, \
+    AGS_CHECK_EMIT_ORDER = 1, 2, 3, 4, 5
 
 _P = ctypes.c_void_p
 _F = ctypes.c_float
@@ -103,7 +107,8 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libags.so, or the index-checking libags_debug.so when AGS_DEBUG=1."""
+    return _build.DEBUG_LIB if os.environ.get("AGS_DEBUG") == "1" else _build.LIB
 
 
 def lib():

@@ -4,6 +4,13 @@ Each translation unit in ``csrc/`` is compiled by its own nvcc process (in
 parallel), then linked with ``nvcc -shared``.  The result goes to
 ``paper_2604_18980_gb300/_build/libags.so``; the CUDA runtime is linked
 statically, so the library needs only the driver at run time.
+
+``build(debug=True)`` makes ``libags_debug.so`` beside it, compiled with
+``-DAGS_DEBUG``: every index the kernels read from their inputs (pair
+values, tile ranges, emission order entries) is checked before it is used; a
+failed check records AGS_ERR_BOUNDS in the status block and skips the access
+instead of trapping.  The binding loads it when the environment sets
+AGS_DEBUG=1.
 """
 from __future__ import annotations
 
@@ -21,6 +28,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libags.so")
+DEBUG_LIB = os.path.join(BUILD, "libags_debug.so")
+DEBUG_FLAGS = ["-DAGS_DEBUG"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "--expt-relaxed-constexpr"]
 
@@ -40,8 +49,11 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-STAMP = LIB + ".src-sha256"
-_reported = False     # "up to date" is logged once per process
+_reported = set()     # "up to date" is logged once per process and library
+
+
+def _stamp(lib_path: str) -> str:
+    return lib_path + ".src-sha256"
 
 
 def source_digest(extra_flags=None) -> str:
@@ -58,29 +70,34 @@ def source_digest(extra_flags=None) -> str:
     return h.hexdigest()
 
 
-def up_to_date(extra_flags=None) -> bool:
-    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
+def up_to_date(extra_flags=None, lib_path: str = LIB) -> bool:
+    stamp = _stamp(lib_path)
+    if not (os.path.exists(lib_path) and os.path.exists(stamp)):
         return False
-    with open(STAMP) as f:
+    with open(stamp) as f:
         return f.read().strip() == source_digest(extra_flags)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None, quiet: bool = False) -> str:
-    """Compile and link libags.so unless the stamped build matches the sources;
-    returns its path and logs which of the two happened (stderr)."""
-    global _reported
-    if not force and up_to_date(extra_flags):
-        if not quiet and not _reported:
-            print("libags: up to date (%s)" % LIB, file=sys.stderr)
-            _reported = True
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra_flags=None, quiet: bool = False,
+          debug: bool = False) -> str:
+    """Compile and link libags.so (libags_debug.so with debug=True) unless the
+    stamped build matches the sources; returns its path and logs which of the
+    two happened (stderr)."""
+    lib_path = DEBUG_LIB if debug else LIB
+    extra_flags = (DEBUG_FLAGS if debug else []) + list(extra_flags or [])
+    if not force and up_to_date(extra_flags, lib_path):
+        if not quiet and lib_path not in _reported:
+            print("libags: up to date (%s)" % lib_path, file=sys.stderr)
+            _reported.add(lib_path)
+        return lib_path
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    flags = FLAGS + list(extra_flags or [])
+    flags = FLAGS + extra_flags
     digest = source_digest(extra_flags)
+    suffix = ".debug.o" if debug else ".o"
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(BUILD, os.path.basename(src) + suffix)
         cmd = [cc] + ARCH + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -91,20 +108,21 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, quiet: b
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib_path + ".tmp%d" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    with open(STAMP + ".tmp", "w") as f:
+    os.replace(tmp, lib_path)
+    stamp = _stamp(lib_path)
+    with open(stamp + ".tmp", "w") as f:
         f.write(digest)
-    os.replace(STAMP + ".tmp", STAMP)
+    os.replace(stamp + ".tmp", stamp)
     if not quiet:
-        print("libags: compiled %d translation units (%s)" % (len(objs), LIB), file=sys.stderr)
-    return LIB
+        print("libags: compiled %d translation units (%s)" % (len(objs), lib_path), file=sys.stderr)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv,
                 extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))

@@ -64,6 +64,24 @@ __device__ __forceinline__ void set_status(int64_t* st, int64_t code, int64_t de
     atomicCAS(s + 1, 0ull, (unsigned long long)detail);
 }
 
+// Index checks of AGS_DEBUG builds, on the indices that come from the inputs
+// (pair values, tile ranges, emission order entries): a failed check records
+// AGS_ERR_BOUNDS with its id as detail, sets bit (1 << id) in word 3 of the
+// status block, and returns false so that the caller skips the access.  In
+// release builds AGS_DCHECK is the constant true and the checks compile away.
+__device__ __forceinline__ bool debug_check(bool ok, int64_t* st, int id) {
+  if (!ok) {
+    set_status(st, AGS_ERR_BOUNDS, id);
+    atomicOr(reinterpret_cast<unsigned long long*>(st + 3), 1ull << id);
+  }
+  return ok;
+}
+#ifdef AGS_DEBUG
+#define AGS_DCHECK(cond, st, id) (::ags::debug_check((cond), (st), (id)))
+#else
+#define AGS_DCHECK(cond, st, id) true
+#endif
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -90,10 +90,15 @@ const char* ags_status_string(ags_status s) {
     case AGS_ERR_TIMEOUT: return "bounded device wait timed out";
     case AGS_ERR_CUDA: return "CUDA error";
     case AGS_ERR_NUMERIC: return "non-finite Gaussian parameters culled";
+    case AGS_ERR_BOUNDS: return "index out of range (debug build check)";
   }
   return "unknown status";
 }
 
+#ifdef AGS_DEBUG
+const char* ags_version(void) { return "ags 0.1 (sm_103a, AGS_DEBUG index checks)"; }
+#else
 const char* ags_version(void) { return "ags 0.1 (sm_103a)"; }
+#endif
 
 }  // extern "C"

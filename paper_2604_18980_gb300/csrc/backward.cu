@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(128)
 raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
                        const uint2* __restrict__ ranges, int W, int H, int gx, int tiles_per_view, BlendConst bc,
                        const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
-                       const float* __restrict__ dL_dimage, float* __restrict__ gsplat) {
+                       const float* __restrict__ dL_dimage, float* __restrict__ gsplat, uint32_t n_splats,
+                       int64_t* status) {
   constexpr int kB = 128;
   __shared__ float4 s_a[kB];      // u v a2 b2
   __shared__ float4 s_b[kB];      // c2 base r g
@@ -114,7 +115,8 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
   const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
   const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
   const uint2 rg = __ldg(ranges + tile);
-  const uint32_t start = rg.x, end = rg.y;
+  const uint32_t start = rg.x;
+  const uint32_t end = AGS_DCHECK(rg.x <= rg.y, status, AGS_CHECK_BACKWARD_RANGE) ? rg.y : rg.x;
   const size_t hw = (size_t)W * H;
 
   float T0 = 1.f, T1 = 1.f, g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f;
@@ -147,7 +149,11 @@ raster_backward_kernel(const float4* __restrict__ splat, const uint32_t* __restr
     const int32_t bbeg = max(0, bend - kB);
     const int nb = bend - bbeg;
     __syncthreads();
-    if (tid < nb) {
+    // (a debug build skips a pair value out of range: no warp walks it)
+    if (tid < nb && !AGS_DCHECK(__ldg(vals + start + bbeg + tid) < n_splats, status, AGS_CHECK_BACKWARD_VALUE)) {
+      s_m[tid] = 0u;
+      s_e[tid] = 0u;
+    } else if (tid < nb) {
       const uint32_t e = __ldg(vals + start + bbeg + tid);
       const float4* rec = splat + (size_t)e * 3;
       Staged st;
@@ -427,6 +433,7 @@ extern "C" ags_status ags_rasterize_backward(const ags_gaussians* g, const ags_c
   if (s != AGS_OK) return s;
   s = build_params(params, &dp);
   if (s != AGS_OK) return s;
+  if (g->n * (int64_t)views > (int64_t)UINT32_MAX) return AGS_ERR_INVALID_ARG;   // pair values are 32-bit
   if (g->n == 0) return AGS_OK;
   if (!ws || ws_bytes < ags_backward_workspace_bytes(g->n, views) || ((uintptr_t)ws & 3u)) return AGS_ERR_INVALID_ARG;
   if (!proj->splat || !proj->flags || !sorted_vals || ((uintptr_t)proj->splat & 15u)) return AGS_ERR_INVALID_ARG;
@@ -438,7 +445,8 @@ extern "C" ags_status ags_rasterize_backward(const ags_gaussians* g, const ags_c
   BlendConst bc = make_blend_const(dp);
   raster_backward_kernel<<<(unsigned)(tiles_per_view * views), 128, 0, st>>>(
       reinterpret_cast<const float4*>(proj->splat), sorted_vals, reinterpret_cast<const uint2*>(ranges), cb.c[0].W,
-      cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, final_T, n_contrib, dL_dimage, gs);
+      cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, final_T, n_contrib, dL_dimage, gs, (uint32_t)(g->n * views),
+      d_status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return AGS_ERR_CUDA;
   GradOut go{g_mean, g_log_scale, g_quat, g_opacity_logit, g_sh};

@@ -93,15 +93,20 @@ emit_kernel(const uint2* __restrict__ rect, const float* __restrict__ depth, con
     uint32_t c = 0;
     if (s < total) {
       uint32_t e = order ? __ldg(order + s) : (uint32_t)s;
-      uint2 r = __ldg(rect + e);
-      uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
-      uint32_t w = x1 - x0;
-      c = ell.splat ? __ldg(ell.touched + e) : w * (y1 - y0);
-      uint32_t view = e / n;
-      s_base[li] = view * tiles_per_view + y0 * gx + x0;
-      s_w[li] = w;
-      if (sizeof(K) == 8) s_dbits[li] = c ? __float_as_uint(__ldg(depth + e)) : 0u;
-      s_idx[li] = e;
+      if (AGS_DCHECK(e < (uint64_t)total_bound, status, AGS_CHECK_EMIT_ORDER)) {
+        uint2 r = __ldg(rect + e);
+        uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
+        uint32_t w = x1 - x0;
+        c = ell.splat ? __ldg(ell.touched + e) : w * (y1 - y0);
+        uint32_t view = e / n;
+        s_base[li] = view * tiles_per_view + y0 * gx + x0;
+        s_w[li] = w;
+        if (sizeof(K) == 8) s_dbits[li] = c ? __float_as_uint(__ldg(depth + e)) : 0u;
+        s_idx[li] = e;
+      } else {     // (debug builds) an order entry out of range: no pairs, an empty record
+        s_base[li] = s_w[li] = s_idx[li] = 0u;
+        if (sizeof(K) == 8) s_dbits[li] = 0u;
+      }
     }
     s_off[li] = c;
   }

@@ -175,6 +175,21 @@ __device__ __forceinline__ void blend_step_state(float q, const BlendConst& bc, 
   }
 }
 
+// The pair value at `v` and its 48-byte splat record.  A debug build checks
+// the value against the record count first; a value out of range becomes an
+// empty record of Gaussian-view 0 (opacity 0: it reaches no pixel).
+__device__ __forceinline__ void gather_record(const float4* __restrict__ splat, const uint32_t* v, uint32_t n_splats,
+                                              int64_t* status, uint32_t& e, float4& r0, float4& r1, float4& r2) {
+  e = __ldg(v);
+  if (AGS_DCHECK(e < n_splats, status, AGS_CHECK_BLEND_VALUE)) {
+    const float4* rec = splat + (size_t)e * 3;
+    r0 = __ldg(rec); r1 = __ldg(rec + 1); r2 = __ldg(rec + 2);
+  } else {
+    e = 0u;
+    r0 = r1 = r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
 // kStats: count evaluations and blends; kMaxT: calibration output; kState:
 // each pixel's final T and last blended position (for the backward).  The
 // shape: kRows rows per lane (4: 8x16-pixel warp blocks, two warps a tile;
@@ -186,7 +201,7 @@ __global__ void __launch_bounds__(256 / kRows)
 raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
               int W, int H, int gx, int tiles_per_view, BlendConst bc, float* __restrict__ image,
               float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ max_T_bits,
-              unsigned long long* stats) {
+              unsigned long long* stats, uint32_t n_splats, int64_t* status) {
   constexpr bool kRec = kStats || kMaxT || kState;
   constexpr int kWarps = 8 / kRows;
   constexpr int kBH = 4 * kRows;                 // warp block: 8 columns x kBH rows
@@ -216,7 +231,8 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
     stop_at[k] = 0u;
   }
   const uint2 rg = __ldg(ranges + tile);
-  const uint32_t start = rg.x, end = rg.y;
+  const uint32_t start = rg.x;
+  const uint32_t end = AGS_DCHECK(rg.x <= rg.y, status, AGS_CHECK_BLEND_RANGE) ? rg.y : rg.x;
   float4* sa = s_a[warp];
   float4* sb = s_b[warp];
   float* sc = s_c[warp];
@@ -230,11 +246,8 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
   for (int i = 0; i < kBatch; i++) {
     n0[i] = n1[i] = n2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     ne[i] = 0u;
-    if (start + 32 * i + lane < end) {
-      ne[i] = __ldg(vals + start + 32 * i + lane);
-      const float4* rec = splat + (size_t)ne[i] * 3;
-      n0[i] = __ldg(rec); n1[i] = __ldg(rec + 1); n2[i] = __ldg(rec + 2);
-    }
+    if (start + 32 * i + lane < end)
+      gather_record(splat, vals + start + 32 * i + lane, n_splats, status, ne[i], n0[i], n1[i], n2[i]);
   }
   for (uint32_t bb = start; bb < end; bb += kStage) {
     bool alive = false;
@@ -260,11 +273,8 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
     }
 #pragma unroll
     for (int i = 0; i < kBatch; i++) {   // the next batch, in flight while this one is blended
-      if (bb + kStage + 32 * i + lane < end) {
-        ne[i] = __ldg(vals + bb + kStage + 32 * i + lane);
-        const float4* rec = splat + (size_t)ne[i] * 3;
-        n0[i] = __ldg(rec); n1[i] = __ldg(rec + 1); n2[i] = __ldg(rec + 2);
-      }
+      if (bb + kStage + 32 * i + lane < end)
+        gather_record(splat, vals + bb + kStage + 32 * i + lane, n_splats, status, ne[i], n0[i], n1[i], n2[i]);
     }
     __syncwarp();
     int walked = 0;
@@ -378,7 +388,7 @@ raster_kernel(const float4* __restrict__ splat, const uint32_t* __restrict__ val
 }
 
 typedef void (*RasterFn)(const float4*, const uint32_t*, const uint2*, int, int, int, int, BlendConst, float*, float*,
-                         uint32_t*, uint32_t*, unsigned long long*);
+                         uint32_t*, uint32_t*, unsigned long long*, uint32_t, int64_t*);
 
 template <int kRows, int kBatch>
 RasterFn pick_raster(bool st, bool mt, bool state) {
@@ -428,6 +438,7 @@ extern "C" ags_status ags_rasterize(const ags_projected* proj, int64_t n, const 
   if (s != AGS_OK) return s;
   if (n > 0 && (!proj->splat || !sorted_vals)) return AGS_ERR_INVALID_ARG;
   if ((uintptr_t)proj->splat & 15u) return AGS_ERR_INVALID_ARG;
+  if (n * (int64_t)views > (int64_t)UINT32_MAX) return AGS_ERR_INVALID_ARG;   // pair values are 32-bit
   const int tiles_per_view = cb.c[0].gx * cb.c[0].gy;
   BlendConst bc = make_blend_const(dp);
   const bool st = stats != nullptr, mt = max_T != nullptr, state = n_contrib != nullptr;
@@ -442,7 +453,8 @@ extern "C" ags_status ags_rasterize(const ags_projected* proj, int64_t n, const 
   kern<<<(unsigned)(tiles_per_view * views), threads, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const float4*>(proj->splat), sorted_vals, reinterpret_cast<const uint2*>(ranges),
       cb.c[0].W, cb.c[0].H, cb.c[0].gx, tiles_per_view, bc, image, final_T, n_contrib,
-      reinterpret_cast<uint32_t*>(max_T), reinterpret_cast<unsigned long long*>(stats));
+      reinterpret_cast<uint32_t*>(max_T), reinterpret_cast<unsigned long long*>(stats), (uint32_t)(n * views),
+      d_status);
   return launch_status(cudaGetLastError());
 }
 

@@ -51,6 +51,7 @@ def test_struct_layouts_match_header(lib):
 def test_status_strings_and_version(lib):
     assert B.ags_status_string(0) == "ok"
     assert "capacity" in B.ags_status_string(2)
+    assert B.ags_status_string(B.AGS_ERR_BOUNDS) == B.STATUS_NAMES[B.AGS_ERR_BOUNDS]
     assert "sm_103a" in B.ags_version()
 
 
@@ -189,3 +190,16 @@ def test_invalid_arguments_rejected_on_host(lib):
                              ctypes.c_void_p(4096), ctypes.c_void_p(8192), None) == 1
     assert L.ags_render_skip(ctypes.byref(full), 10, sv, rg, cam1, 1, ctypes.byref(par), 0, None, 0.5,
                              None, ctypes.c_void_p(8192), None) == 1
+
+
+def test_debug_library_builds_and_exports_every_symbol():
+    """libags_debug.so (-DAGS_DEBUG): the same C ABI, and a version string that says so."""
+    from paper_2604_18980_gb300 import build as cuda_build
+    path = cuda_build.build(debug=True, quiet=True)
+    assert path != cuda_build.LIB
+    L = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    L.ags_version.restype = ctypes.c_char_p
+    assert b"AGS_DEBUG" in L.ags_version()
+    assert "AGS_DEBUG" not in B.ags_version()
