@@ -52,6 +52,8 @@
  *  - Arrays are structure-of-arrays fp32 unless stated; `n` Gaussians, `views`
  *    cameras of one common width and height rendered in one launch per stage.
  *  - Tiles are 16x16 pixels; pixel centres sit at integer coordinates.
+ *  - Tile ranges are uint32[tiles][2] = (start, end) pairs, 8-byte aligned
+ *    (every kernel reads or writes a pair in one 8-byte access).
  *  - Gaussian-tile pair counts are limited to AGS_MAX_PAIRS per sort call.
  */
 #ifndef AGS_H

@@ -425,6 +425,7 @@ extern "C" ags_status ags_rasterize_backward(const ags_gaussians* g, const ags_c
                                              void* ws, size_t ws_bytes, void* stream) {
   using namespace ags;
   if (!g || !proj || !ranges || !final_T || !n_contrib || !dL_dimage || !d_status) return AGS_ERR_INVALID_ARG;
+  if ((uintptr_t)ranges & 7u) return AGS_ERR_INVALID_ARG;       // read as 8-byte (start, end) pairs
   if (!g_mean || !g_log_scale || !g_quat || !g_opacity_logit || !g_sh) return AGS_ERR_INVALID_ARG;
   if (g->n < 0 || g->n > (int64_t)1 << 31) return AGS_ERR_INVALID_ARG;
   CamBatch cb;

@@ -254,6 +254,7 @@ static ags_status diag_prepare(const ags_projected* proj, int64_t n, const uint3
                                const uint32_t* ranges, const ags_camera* cams, int32_t views,
                                const ags_params* params, CamBatch* cb, DevParams* dp) {
   if (!proj || !ranges || n < 0) return AGS_ERR_INVALID_ARG;
+  if ((uintptr_t)ranges & 7u) return AGS_ERR_INVALID_ARG;       // read as 8-byte (start, end) pairs
   ags_status s = build_cams(cams, views, cb);
   if (s != AGS_OK) return s;
   s = build_params(params, dp);

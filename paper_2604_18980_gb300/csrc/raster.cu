@@ -430,6 +430,7 @@ extern "C" ags_status ags_rasterize(const ags_projected* proj, int64_t n, const 
                                     float* max_T, uint64_t* stats, int64_t* d_status, void* stream) {
   using namespace ags;
   if (!proj || !ranges || !image || !d_status || n < 0) return AGS_ERR_INVALID_ARG;
+  if ((uintptr_t)ranges & 7u) return AGS_ERR_INVALID_ARG;       // read as 8-byte (start, end) pairs
   CamBatch cb;
   DevParams dp;
   ags_status s = build_cams(cams, views, &cb);

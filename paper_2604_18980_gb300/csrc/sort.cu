@@ -361,6 +361,14 @@ onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* 
   }
 }
 
+// Every range to (0xffffffff, 0) before the last pass narrows them (one
+// 8-byte store per range; a 2D memset of 4-byte rows at an 8-byte pitch ran
+// far slower over 10^5..10^6 ranges).
+__global__ void ranges_init_kernel(uint2* ranges, int64_t num_ranges) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < num_ranges; t += (int64_t)gridDim.x * blockDim.x)
+    ranges[t] = make_uint2(0xffffffffu, 0u);
+}
+
 // Ranges no key reached still hold the (0xffffffff, 0) of the initialisation.
 __global__ void ranges_fixup_kernel(uint2* ranges, int64_t num_ranges) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < num_ranges; t += (int64_t)gridDim.x * blockDim.x) {
@@ -694,6 +702,7 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
   const int passes = (end_bit - begin_bit + digit_bits - 1) / digit_bits;
   if (passes > kMaxPasses) return AGS_ERR_INVALID_ARG;
   if (ranges && (num_ranges <= 0 || num_ranges > ((int64_t)1 << 32) - 1)) return AGS_ERR_INVALID_ARG;
+  if ((uintptr_t)ranges & 7u) return AGS_ERR_INVALID_ARG;       // (start, end) pairs are 8-byte stores
   if (capacity > 0 && (!keys || !vals || (passes > 0 && (!keys_alt || !vals_alt)))) return AGS_ERR_INVALID_ARG;
   if (capacity > 0 && passes > 0 && ((uintptr_t)keys & 15u)) return AGS_ERR_INVALID_ARG;   // 16-byte key loads
   if (!ws || ws_bytes < ags_sort_workspace_bytes(capacity) || ((uintptr_t)ws & 15u)) return AGS_ERR_INVALID_ARG;
@@ -718,9 +727,8 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
     hist_kernel<K><<<hb, 256, 0, st>>>(keys, d_num_pairs, capacity, begin_bit, end_bit, digit_bits, passes, radix,
                                        ghist);
     if (ranges) {   // start = 0xffffffff, end = 0: the last pass narrows them with atomics
-      e = cudaMemset2DAsync(ranges, 8, 0xff, 4, (size_t)num_ranges, st);
-      if (e == cudaSuccess) e = cudaMemset2DAsync(ranges + 1, 8, 0, 4, (size_t)num_ranges, st);
-      if (e != cudaSuccess) return AGS_ERR_CUDA;
+      const int blocks = (int)std::min<int64_t>((num_ranges + 255) / 256, 4096);
+      ranges_init_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), num_ranges);
     }
     auto launch = radix == 512   ? launch_passes<512, K>
                   : radix == 256 ? launch_passes<256, K>

@@ -118,6 +118,12 @@ def test_invalid_arguments_rejected_on_host(lib):
                         None) == 1
     assert L.ags_sort32(ctypes.c_void_p(20), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
                         10, 0, 32, 8, 0, None, 0, ctypes.byref(alt), st, ctypes.c_void_p(256), 1 << 20, None) == 1
+    # ranges not 8-byte aligned
+    assert L.ags_sort32(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
+                        10, 0, 32, 8, 0, ctypes.c_void_p(260), 4, ctypes.byref(alt), st, ctypes.c_void_p(256),
+                        1 << 20, None) == 1
+    assert L.ags_rasterize(ctypes.byref(pr), 0, None, ctypes.c_void_p(260), cam, 1, ctypes.byref(par),
+                           ctypes.c_void_p(512), None, None, None, None, st, None) == 1
     # 64-bit sort: unaligned keys
     assert L.ags_sort(ctypes.c_void_p(24), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
                       10, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st, ctypes.c_void_p(256), 1 << 20, None) == 1
