@@ -87,7 +87,7 @@ class Renderer:
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
                  presort: bool = True, pair_rank_or: bool = True, emit_two_pass: bool = True,
                  keep_state: bool = True, tile_test: int = B.AGS_TILE_SQUARE, view_major: bool | None = None,
-                 blend_flags: int = 0, sort_wide: bool = False):
+                 blend_flags: int = 0, sort_wide: bool = False, depth_rank_or: bool = True):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -102,6 +102,9 @@ class Renderer:
         self.tile_test = tile_test
         self.blend_flags = int(blend_flags)      # AGS_BLEND_*: launch shape of the blend
         self.sort_flags = B.AGS_SORT_WIDE_BLOCK if sort_wide else 0
+        # depth keys: the low digits of the float bits are close to uniform, so a
+        # warp's keys mostly carry distinct digits -- the case of the atomic-OR ranking
+        self.depth_rank_flags = B.AGS_SORT_RANK_OR if depth_rank_or else 0
         self.emit_flags = B.AGS_EMIT_ELLIPSE if tile_test == B.AGS_TILE_ELLIPSE else 0
         self.tile_bits = max(1, (self.T - 1).bit_length())
         if view_major is None:
@@ -214,7 +217,7 @@ class Renderer:
             passes, db = digit_plan(self.dsort_end, self.digit_bits)
             alt = B.ags_sort32(self.dkey, self.order, self.dkey_alt, self.order_alt, self.n_visible,
                                self.V * self.n, 0, self.dsort_end, db, None, 0, self.status, self.ws_dsort,
-                               flags=B.AGS_SORT_DISCARD_KEYS | self.sort_flags)
+                               flags=B.AGS_SORT_DISCARD_KEYS | self.depth_rank_flags | self.sort_flags)
             self.emit_order = self.order_alt if alt else self.order
             if self.view_major:
                 # then stably by view: the views one after the other, each in

@@ -533,7 +533,7 @@ def test_autotuner_candidates_render_identically():
 def test_launch_shapes_give_identical_outputs(digit_bits):
     """The block shapes the autotuner sweeps -- the blend's 8x16 or 8x8 warp
     blocks and 32- or 64-splat batches, the 32-bit sort passes on 256 x 16 or
-    512 x 8 partitions -- change no output: image, final T, last blended
+    512 x 8 partitions -- and the depth pre-sort's ranking method change no output: image, final T, last blended
     position, calibration max T, the evaluation and blend counts, and the
     sorted pair lists, bit for bit.  A ragged frame (tiles cut at the right and
     bottom edges), two views, and tiles long enough for several batches."""
@@ -541,7 +541,7 @@ def test_launch_shapes_give_identical_outputs(digit_bits):
     scene, cams = _c1(n=12000, W=200, H=150, views=2)
     sc = R.scene_to_device(scene)
     ref = None
-    for sh in autotune.SHAPES:
+    for sh in autotune.SHAPES + [dict(depth_rank_or=False)]:
         r = R.Renderer(sc, cams, 1, 0.3, want_stats=True, digit_bits=digit_bits, **sh)
         max_T = torch.zeros(r.V * r.n, dtype=torch.float32, device="cuda")
         img = r.forward(max_T=max_T).clone()
