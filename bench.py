@@ -708,10 +708,12 @@ def stage_bytes(stage, r, passes):
         dp = digit_plan(r.dsort_end, r.digit_bits)[0] if r.presort else 0
         if not dp:
             return 0, "onesweep_kernel (depth keys)"
-        # compaction: flags (1 B) and depth (4 B) of every Gaussian-view read, key and
-        # index (8 B) of the visible ones written; the sort of the visible ones:
-        # histogram 4 B, each pass 16 B, minus the keys the last pass does not write
-        return G * 5 + live * 8 + live * 4 + dp * live * 16 - live * 4, "visible_kernel + onesweep_kernel (depth keys)"
+        # compaction: the flag (1 B) of every Gaussian-view read, the depth (4 B) of
+        # the visible ones read and their key and index (8 B) written; the sort of the
+        # visible ones: histogram 4 B, each pass 16 B, minus the keys the last pass
+        # does not write
+        return G * 1 + live * 12 + live * 4 + dp * live * 16 - live * 4, \
+            "visible_count/scan/write_kernel + lean_kernel (depth keys)"
     if stage == "emit":
         if r.presort:
             # order (4 B) and rectangle (8 B) per visible Gaussian-view; 8 B per pair (tile key, value)

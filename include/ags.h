@@ -268,8 +268,9 @@ size_t ags_compact_workspace_bytes(int64_t n, int32_t views);
  * reach a tile list (Sec. 2.1 frustum cull, Sec. 3.3 Th > opacity cull), so the
  * depth pre-sort (ags_sort32 of keys with ids as values, count d_count) needs
  * only these.  Reads proj->flags and proj->depth (both 16-byte aligned);
- * keys and ids hold up to views*n entries.  Single pass with a decoupled
- * look-back (bounded spin). */
+ * keys and ids hold up to views*n entries.  Three launches -- per-partition
+ * counts, one block scanning them, the writes -- with no device-side wait;
+ * d_status is not written. */
 ags_status ags_compact_visible(const ags_projected* proj, int64_t n, int32_t views, uint32_t* keys,
                                uint32_t* ids, int64_t* d_count, int64_t* d_status, void* ws,
                                size_t ws_bytes, void* stream);

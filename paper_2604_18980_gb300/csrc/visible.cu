@@ -5,12 +5,15 @@
 //
 // A culled Gaussian-view (no pairs in its view, Sec. 2.1 frustum cull and
 // Sec. 3.3 Th > opacity cull) never reaches a tile list, so the depth
-// pre-sort needs only the others.  One pass: each 256-thread block takes 4096
-// consecutive entries e (16 per thread, read as 16-byte vectors), counts the
-// visible ones, scans the counts, finds its output offset with a decoupled
-// look-back over the preceding blocks (bounded spin), and writes
-// (float_bits(depth[e]), e) for its visible entries in increasing e -- so each
-// view's entries keep increasing Gaussian index, the tie order of the sort.
+// pre-sort needs only the others.  Reduce, then scan, then write -- three
+// launches and no block ever waits for another: (1) each 256-thread block
+// counts the visible entries of one 4096-entry partition from the flags (16
+// per thread, read as 16-byte vectors); (2) one block scans the partition
+// counts into offsets and writes the total; (3) each block re-reads its
+// partition's flags, ranks its visible entries with a block scan, reads their
+// depths, stages (float_bits(depth[e]), e) in shared memory and writes them
+// out coalesced at its offset -- so the entries keep increasing e and each
+// view's entries increasing Gaussian index, the tie order of the sort.
 #include <algorithm>
 
 #include "ags_internal.cuh"
@@ -20,54 +23,95 @@ namespace ags {
 constexpr int kVisThreads = 256;
 constexpr int kVisItems = 16;
 constexpr int kVisPart = kVisThreads * kVisItems;     // 4096 entries per partition
-constexpr uint64_t kVisAgg = 1ull << 62;
-constexpr uint64_t kVisInc = 2ull << 62;
-constexpr uint64_t kVisMask = (1ull << 62) - 1;
+constexpr int kVisScanThreads = 1024;
 
-__global__ void __launch_bounds__(kVisThreads)
-visible_kernel(const uint8_t* __restrict__ flags, const float* __restrict__ depth, uint32_t total,
-               uint32_t* __restrict__ keys, uint32_t* __restrict__ ids, int64_t* d_count, int64_t* status,
-               uint64_t* part_status, uint32_t* counter, uint32_t num_parts) {
-  __shared__ uint32_t s_warp[kVisThreads / 32];
-  __shared__ uint32_t s_part;
-  __shared__ uint64_t s_prefix;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_part = atomicAdd(counter, 1u);
-  __syncthreads();
-  const uint32_t part = s_part;
-  const uint32_t i0 = part * kVisPart + (uint32_t)tid * kVisItems;
-
-  // this thread's 16 entries: visibility mask and depth bits
+// Visibility bits of this thread's 16 entries i0 .. i0+15 (bit k: entry i0+k).
+__device__ __forceinline__ uint32_t visible_bits(const uint8_t* __restrict__ flags, uint32_t i0, uint32_t total) {
   uint32_t vis = 0u;
-  uint32_t dbits[kVisItems];
   if (i0 + kVisItems <= total) {
-    const uint4 f = __ldcs(reinterpret_cast<const uint4*>(flags + i0));
+    const uint4 f = __ldg(reinterpret_cast<const uint4*>(flags + i0));
     const uint32_t fw[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
     for (int k = 0; k < kVisItems; k++)
       if (!((fw[k >> 2] >> (8 * (k & 3))) & kFlagCulled)) vis |= 1u << k;
-    const float4* d4 = reinterpret_cast<const float4*>(depth + i0);
-#pragma unroll
-    for (int q = 0; q < kVisItems / 4; q++) {
-      const float4 d = __ldcs(d4 + q);
-      dbits[4 * q] = __float_as_uint(d.x);
-      dbits[4 * q + 1] = __float_as_uint(d.y);
-      dbits[4 * q + 2] = __float_as_uint(d.z);
-      dbits[4 * q + 3] = __float_as_uint(d.w);
-    }
   } else {
-#pragma unroll
-    for (int k = 0; k < kVisItems; k++) {
-      dbits[k] = 0u;
-      if (i0 + k < total && !(flags[i0 + k] & kFlagCulled)) {
-        vis |= 1u << k;
-        dbits[k] = __float_as_uint(depth[i0 + k]);
-      }
-    }
+    for (int k = 0; k < kVisItems; k++)
+      if (i0 + k < total && !(flags[i0 + k] & kFlagCulled)) vis |= 1u << k;
   }
-  const uint32_t cnt = (uint32_t)__popc(vis);
+  return vis;
+}
 
-  // block scan of the counts
+// (1) visible entries per partition
+__global__ void __launch_bounds__(kVisThreads)
+visible_count_kernel(const uint8_t* __restrict__ flags, uint32_t total, uint32_t* __restrict__ part_count) {
+  __shared__ uint32_t s_warp[kVisThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t i0 = blockIdx.x * (uint32_t)kVisPart + (uint32_t)tid * kVisItems;
+  const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(visible_bits(flags, i0, total)));
+  if (lane == 0) s_warp[warp] = c;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kVisThreads / 32; w++) t += s_warp[w];
+    part_count[blockIdx.x] = t;
+  }
+}
+
+// (2) exclusive scan of the partition counts in place (one block, chunks of
+// 1024 x 16 partitions with a running carry); the total goes to *d_count
+__global__ void __launch_bounds__(kVisScanThreads)
+visible_scan_kernel(uint32_t* __restrict__ part, uint32_t parts, int64_t* d_count) {
+  __shared__ uint32_t s_warp[kVisScanThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t carry = 0;
+  for (uint32_t base = 0; base < parts; base += kVisScanThreads * 16u) {
+    const uint32_t j0 = base + (uint32_t)tid * 16u;
+    uint32_t v[16], t = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      v[k] = j0 + k < parts ? part[j0 + k] : 0u;
+      t += v[k];
+    }
+    uint32_t incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0, agg = 0;
+#pragma unroll 4
+    for (int w = 0; w < kVisScanThreads / 32; w++) {
+      const uint32_t x = s_warp[w];
+      if (w < warp) wpre += x;
+      agg += x;
+    }
+    uint64_t run = carry + wpre + incl - t;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      if (j0 + k < parts) part[j0 + k] = (uint32_t)run;
+      run += v[k];
+    }
+    carry += agg;
+    __syncthreads();     // s_warp is reused by the next chunk
+  }
+  if (tid == 0) *d_count = (int64_t)carry;
+}
+
+// (3) the visible entries of one partition, written at its offset
+__global__ void __launch_bounds__(kVisThreads)
+visible_write_kernel(const uint8_t* __restrict__ flags, const float* __restrict__ depth, uint32_t total,
+                     const uint32_t* __restrict__ part_off, uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
+  __shared__ uint32_t s_key[kVisPart];
+  __shared__ uint32_t s_id[kVisPart];
+  __shared__ uint32_t s_warp[kVisThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t p0 = blockIdx.x * (uint32_t)kVisPart;
+  const uint32_t i0 = p0 + (uint32_t)tid * kVisItems;
+  const uint32_t vis = visible_bits(flags, i0, total);
+  const uint32_t cnt = (uint32_t)__popc(vis);
   uint32_t incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -75,63 +119,37 @@ visible_kernel(const uint8_t* __restrict__ flags, const float* __restrict__ dept
     if (lane >= o) incl += y;
   }
   if (lane == 31) s_warp[warp] = incl;
+  // this thread's depths (only where an entry is visible) while the scan settles
+  uint32_t o = incl - cnt;
+  uint32_t m = vis;
+  uint32_t dk[kVisItems];
+#pragma unroll
+  for (int k = 0; k < kVisItems; k++) dk[k] = (m >> k) & 1u ? __float_as_uint(__ldg(depth + i0 + k)) : 0u;
   __syncthreads();
   uint32_t wpre = 0, agg = 0;
 #pragma unroll
   for (int w = 0; w < kVisThreads / 32; w++) {
-    const uint32_t v = s_warp[w];
-    if (w < warp) wpre += v;
-    agg += v;
+    const uint32_t x = s_warp[w];
+    if (w < warp) wpre += x;
+    agg += x;
   }
-
-  // decoupled look-back (warp 0): 32 predecessors per poll
-  if (warp == 0) {
-    uint64_t excl = 0;
-    if (part == 0) {
-      if (lane == 0) st_relaxed_u64(part_status, kVisInc | (uint64_t)agg);
-    } else {
-      if (lane == 0) st_relaxed_u64(part_status + part, kVisAgg | (uint64_t)agg);
-      int64_t top = (int64_t)part - 1;
-      const uint64_t t0 = globaltimer_ns();
-      bool timed_out = false;
-      while (true) {
-        const int64_t q = top - lane;
-        const uint64_t sv = q >= 0 ? ld_relaxed_u64(part_status + q) : kVisInc;
-        const uint32_t flag = (uint32_t)(sv >> 62);
-        const unsigned inc_mask = __ballot_sync(0xffffffffu, flag == 2u);
-        const unsigned none_mask = __ballot_sync(0xffffffffu, flag == 0u);
-        const int first_inc = inc_mask ? __ffs(inc_mask) - 1 : 32;
-        const unsigned upto = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
-        if ((none_mask & upto) && !timed_out) {
-          if (globaltimer_ns() - t0 > kWaitLimitNs) {
-            timed_out = true;
-            if (lane == 0) set_status(status, AGS_ERR_TIMEOUT, kStageVisible);
-          }
-          continue;
-        }
-        excl += warp_sum((lane <= first_inc && flag != 0u) ? (sv & kVisMask) : 0ull);
-        if (first_inc < 32 || timed_out) break;
-        top -= 32;
-      }
-      if (lane == 0) st_relaxed_u64(part_status + part, kVisInc | ((excl + agg) & kVisMask));
+  o += wpre;
+#pragma unroll
+  for (int k = 0; k < kVisItems; k++) {
+    if ((m >> k) & 1u) {
+      s_key[o] = dk[k];
+      s_id[o] = i0 + (uint32_t)k;
+      o++;
     }
-    if (lane == 0) s_prefix = excl;
   }
   __syncthreads();
-
-  // write this thread's visible entries in index order
-  uint32_t o = (uint32_t)s_prefix + wpre + incl - cnt;
-  uint32_t m = vis;
-  while (m) {
-    const int k = __ffs(m) - 1;
-    m &= m - 1;
-    if (o < total) {
-      keys[o] = dbits[k];
-      ids[o] = i0 + (uint32_t)k;
+  const uint32_t base = __ldg(part_off + blockIdx.x);
+  for (uint32_t k = (uint32_t)tid; k < agg; k += kVisThreads) {
+    if (base + k < total) {
+      keys[base + k] = s_key[k];
+      ids[base + k] = s_id[k];
     }
-    o++;
   }
-  if (part == num_parts - 1 && tid == 0) *d_count = (int64_t)(s_prefix + agg);
 }
 
 static size_t vis_parts(int64_t total) { return (size_t)((total + kVisPart - 1) / kVisPart); }
@@ -156,13 +174,11 @@ extern "C" ags_status ags_compact_visible(const ags_projected* proj, int64_t n, 
   if (((uintptr_t)proj->flags & 15u) || ((uintptr_t)proj->depth & 15u)) return AGS_ERR_INVALID_ARG;
   if (!ws || ws_bytes < ags_compact_workspace_bytes(n, views) || ((uintptr_t)ws & 7u)) return AGS_ERR_INVALID_ARG;
   const size_t parts = vis_parts(total);
-  cudaError_t e = cudaMemsetAsync(ws, 0, 256 + 8 * parts, st);
-  if (e != cudaSuccess) return AGS_ERR_CUDA;
-  uint32_t* counter = reinterpret_cast<uint32_t*>(ws);
-  uint64_t* part_status = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + 256);
-  visible_kernel<<<(unsigned)parts, kVisThreads, 0, st>>>(proj->flags, proj->depth, (uint32_t)total, keys, ids,
-                                                          d_count, d_status, part_status, counter,
-                                                          (uint32_t)parts);
+  uint32_t* part = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + 256);
+  visible_count_kernel<<<(unsigned)parts, kVisThreads, 0, st>>>(proj->flags, (uint32_t)total, part);
+  visible_scan_kernel<<<1, kVisScanThreads, 0, st>>>(part, (uint32_t)parts, d_count);
+  visible_write_kernel<<<(unsigned)parts, kVisThreads, 0, st>>>(proj->flags, proj->depth, (uint32_t)total, part, keys,
+                                                                ids);
   return launch_status(cudaGetLastError());
 }
 

@@ -467,8 +467,10 @@ def test_emit_tile_pairs_balanced_blocks():
 
 def test_compact_visible_edges():
     """Compaction of ragged counts (not a multiple of the partition), all-culled
-    and none-culled inputs, against numpy."""
-    for total, p_cull in ((1, 0.0), (4095, 0.5), (4097, 0.3), (3 * 4096 + 17, 1.0), (70001, 0.0), (70001, 0.9)):
+    and none-culled inputs, and more partitions than one chunk of the offset
+    scan (16384), against numpy."""
+    for total, p_cull in ((1, 0.0), (4095, 0.5), (4097, 0.3), (3 * 4096 + 17, 1.0), (70001, 0.0), (70001, 0.9),
+                          ((1 << 26) + 3 * 4096 + 5, 0.85)):
         rng = np.random.default_rng(total + int(10 * p_cull))
         flags = np.where(rng.random(total) < p_cull, 0x80, rng.integers(0, 0x20, total)).astype(np.uint8)
         depth = rng.uniform(0.2, 50.0, total).astype(np.float32)
