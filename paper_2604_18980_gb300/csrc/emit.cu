@@ -387,6 +387,158 @@ __device__ __forceinline__ void warp_emit_ellipse(const uint4* rec, int m, uint3
   __syncwarp();
 }
 
+// Pass 1 of the two-pass tile-key emission: the record {first pair, splat
+// index, first tile key, width} of every visited entry, the entry holding the
+// first pair of every kTileChunk-pair block, and the pair total.  Partitions
+// of 4096 entries per 256-thread block (a quarter of the look-backs of
+// 1024-entry partitions): striped loads of the order (coalesced) with the 16
+// rectangle gathers of a thread in flight together, the counts transposed
+// through shared memory for a blocked scan, a decoupled look-back for the
+// partition's offset, and the records written striped (coalesced 16-byte
+// stores).  Same records, block starts and total as the fused kernel's
+// record path.
+constexpr int kScanItems = 16;
+constexpr int kScanPart = kEmitThreads * kScanItems;      // 4096 entries per partition
+
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }   // conflict-free blocked reads
+
+__global__ void __launch_bounds__(kEmitThreads)
+tile_scan_kernel(const uint2* __restrict__ rect, const uint32_t* __restrict__ order, int64_t total_bound,
+                 const int64_t* d_total, uint32_t n, uint32_t tiles_per_view, uint32_t gx, int64_t capacity,
+                 int64_t* d_num_pairs, int64_t* status, uint64_t* part_status, uint32_t* counter,
+                 uint4* __restrict__ recs, uint32_t* __restrict__ chunk_start, EllipseSrc ell, WaitHook hook) {
+  __shared__ uint32_t s_c[kScanPart + kScanPart / 32];   // counts, then exclusive offsets in the partition
+  __shared__ uint32_t s_warp[kEmitThreads / 32];
+  __shared__ uint32_t s_part;
+  __shared__ unsigned long long s_prefix;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_part = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t part = s_part;
+  int64_t total = total_bound;
+  if (d_total) {
+    const int64_t t = *d_total;
+    total = t < 0 ? 0 : (t > total_bound ? total_bound : t);
+  }
+  const uint32_t nparts = (uint32_t)((total + kScanPart - 1) / kScanPart);
+  if (part >= nparts) {                       // beyond the entries: no pairs, nobody waits on it
+    if (part == 0 && tid == 0) *d_num_pairs = 0;
+    return;
+  }
+  const int64_t base = (int64_t)part * kScanPart;
+
+  // 1. striped entries li = k * 256 + tid: order, rectangle, count
+  uint32_t e[kScanItems];
+  uint2 r[kScanItems];
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    const int64_t s = base + k * kEmitThreads + tid;
+    e[k] = 0u;
+    if (s < total) {
+      const uint32_t v = order ? __ldg(order + s) : (uint32_t)s;
+      e[k] = AGS_DCHECK(v < (uint64_t)total_bound, status, AGS_CHECK_EMIT_ORDER) ? v : 0xffffffffu;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++)
+    r[k] = e[k] != 0xffffffffu && base + k * kEmitThreads + tid < total ? __ldg(rect + e[k]) : make_uint2(0u, 0u);
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    const uint32_t w = (r[k].y & 0xffffu) - (r[k].x & 0xffffu), h = (r[k].y >> 16) - (r[k].x >> 16);
+    uint32_t c = w * h;
+    if (ell.splat) c = (c && e[k] != 0xffffffffu) ? __ldg(ell.touched + e[k]) : 0u;
+    s_c[scan_pad(k * kEmitThreads + tid)] = c;
+  }
+  __syncthreads();
+
+  // 2. blocked scan: thread t owns entries 16t .. 16t+15
+  uint32_t cb[kScanItems], tsum = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    cb[j] = s_c[scan_pad(tid * kScanItems + j)];
+    tsum += cb[j];
+  }
+  uint32_t incl = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  uint32_t wpre = 0, agg = 0;
+#pragma unroll
+  for (int w = 0; w < kEmitThreads / 32; w++) {
+    const uint32_t v = s_warp[w];
+    if (w < warp) wpre += v;
+    agg += v;
+  }
+  uint32_t run = wpre + incl - tsum;
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    s_c[scan_pad(tid * kScanItems + j)] = run;
+    run += cb[j];
+  }
+
+  // 3. decoupled look-back (warp 0) for the partition's global offset
+  if (warp == 0) {
+    uint64_t excl = 0;
+    const bool publish = part != hook.withhold;
+    if (part == 0) {
+      if (lane == 0 && publish) st_relaxed_u64(part_status, kInc | (uint64_t)agg);
+    } else {
+      if (lane == 0 && publish) st_relaxed_u64(part_status + part, kAgg | (uint64_t)agg);
+      int64_t top = (int64_t)part - 1;
+      const uint64_t t0 = globaltimer_ns();
+      bool timed_out = false;
+      while (true) {
+        const int64_t qidx = top - lane;
+        const uint64_t sv = qidx >= 0 ? ld_relaxed_u64(part_status + qidx) : kInc;
+        const uint32_t flag = (uint32_t)(sv >> 62);
+        const unsigned inc_mask = __ballot_sync(0xffffffffu, flag == 2u);
+        const unsigned inv_mask = __ballot_sync(0xffffffffu, flag == 0u);
+        const int first_inc = inc_mask ? __ffs(inc_mask) - 1 : 32;
+        const unsigned upto = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
+        if ((inv_mask & upto) && !timed_out) {
+          if (globaltimer_ns() - t0 > hook.limit_ns) {
+            timed_out = true;
+            if (lane == 0) set_status(status, AGS_ERR_TIMEOUT, kStageEmit);
+          }
+          continue;
+        }
+        excl += warp_sum((lane <= first_inc) ? (sv & kValMask) : 0ull);
+        if (first_inc < 32 || timed_out) break;
+        top -= 32;
+      }
+      if (lane == 0 && publish) st_relaxed_u64(part_status + part, kInc | ((excl + agg) & kValMask));
+    }
+    if (lane == 0) s_prefix = excl;
+  }
+  __syncthreads();
+  const uint64_t prefix = s_prefix;
+
+  // 4. striped records and the pair blocks that start inside each entry
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    const int li = k * kEmitThreads + tid;
+    if (base + li < total) {
+      const uint32_t x0 = r[k].x & 0xffffu, y0 = r[k].x >> 16, w = (r[k].y & 0xffffu) - x0;
+      const uint32_t c = (li + 1 < kScanPart ? s_c[scan_pad(li + 1)] : agg) - s_c[scan_pad(li)];
+      const uint64_t off = prefix + s_c[scan_pad(li)], end = off + c;
+      const uint32_t ev = e[k] == 0xffffffffu ? 0u : e[k];
+      recs[base + li] = make_uint4((uint32_t)off, ev, (ev / n) * tiles_per_view + y0 * gx + x0, w);
+      const uint64_t lim = end < (uint64_t)capacity ? end : (uint64_t)capacity;
+      for (uint64_t q = (off + kTileChunk - 1) / kTileChunk * kTileChunk; q < lim; q += kTileChunk)
+        chunk_start[q / kTileChunk] = (uint32_t)(base + li);
+    }
+  }
+  if (part == nparts - 1 && tid == 0) {
+    const int64_t tot = (int64_t)(prefix + agg);
+    *d_num_pairs = tot;
+    if (tot > capacity) set_status(status, AGS_ERR_CAPACITY, tot);
+  }
+}
+
 struct TileEmitSmem {
   uint4 rec[kTileChunk + 2];
   uint32_t k_run[kEmitThreads / 32][32];
@@ -594,10 +746,10 @@ extern "C" ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, 
     return launch_status(cudaGetLastError());
   }
   // phase 1: per-entry records and the pair count
-  emit_kernel<uint32_t><<<(unsigned)parts, kEmitThreads, 0, st>>>(
-      reinterpret_cast<const uint2*>(proj->rect), proj->depth, order, total, d_entries, (uint32_t)n, tiles_per_view,
-      (uint32_t)cb.c[0].gx, keys, vals, capacity, d_num_pairs, d_status, part_status, counter, recs, chunk_start,
-      ell, wait_hook(flags & AGS_EMIT_TEST_STALL));
+  tile_scan_kernel<<<(unsigned)((total + kScanPart - 1) / kScanPart), kEmitThreads, 0, st>>>(
+      reinterpret_cast<const uint2*>(proj->rect), order, total, d_entries, (uint32_t)n, tiles_per_view,
+      (uint32_t)cb.c[0].gx, capacity, d_num_pairs, d_status, part_status, counter, recs, chunk_start, ell,
+      wait_hook(flags & AGS_EMIT_TEST_STALL));
   e = cudaGetLastError();
   if (e != cudaSuccess || capacity == 0) return launch_status(e);
   // phase 2: the pairs, in blocks of kTileChunk (grid-stride over the device count)
