@@ -545,6 +545,7 @@ struct TileEmitSmem {
   uint32_t key[kEmitThreads / 32][32 * kEmitStride];
   uint32_t val[kEmitThreads / 32][32 * kEmitStride];
   uint32_t k0;
+  uint32_t k1;       // first window of a block: one past the sentinel record it needs
 };
 
 __global__ void __launch_bounds__(kEmitThreads)
@@ -566,8 +567,14 @@ tile_emit_kernel(const uint4* __restrict__ recs, const uint32_t* __restrict__ ch
     uint32_t cs = c0;
     bool first = true;
     while (cs < cend) {
+      const bool win_first = first;
       if (first) {
-        if (tid == 0) S.k0 = min(__ldg(chunk_start + b), nent - 1u);
+        // the block's records run from the one holding its first pair to the one
+        // holding the next block's first pair (whose successor is the sentinel)
+        if (tid == 0) {
+          S.k0 = min(__ldg(chunk_start + b), nent - 1u);
+          S.k1 = cend < total ? min(__ldg(chunk_start + b + 1) + 2u, nent + 1u) : nent + 1u;
+        }
       } else if (warp == 0) {   // the last record whose first pair is <= cs
         uint32_t lo = 0, hi = nent;                // answer in [lo, hi); record 0 starts at pair 0
         while (hi - lo > 32) {
@@ -584,7 +591,7 @@ tile_emit_kernel(const uint4* __restrict__ recs, const uint32_t* __restrict__ ch
       first = false;
       __syncthreads();
       const uint32_t k0 = S.k0;
-      const uint32_t m = min((uint32_t)kTileChunk + 1u, nent - k0);
+      const uint32_t m = min(min((uint32_t)kTileChunk + 1u, nent - k0), win_first ? S.k1 - 1u - k0 : 0xffffffffu);
       for (uint32_t q = tid; q <= m; q += kEmitThreads)
         S.rec[q] = (k0 + q < nent) ? __ldg(&recs[k0 + q]) : make_uint4(total, 0u, 0u, 1u);
       __syncthreads();
