@@ -140,6 +140,8 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(PreIn in, in
   const bool ok = active && finite;
   Frame F;                    // scales, rotation, R S and opacity: once for all views
   make_frame(ls, q, logit, F);
+  const float smax = fmaxf(F.s[0], fmaxf(F.s[1], F.s[2]));
+  const float smax2 = smax * smax;
   float4* qj = s_job[warp];
   uint32_t* qt = s_tag[warp];
   int qn = 0;                 // queued survivors (warp-uniform)
@@ -152,7 +154,8 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(PreIn in, in
     uint32_t tag = 0u;
     if (ok) {
       Proj pj;
-      bool live = project_view(C, m, F, pj);
+      // off-screen footprints leave before the covariance (same outputs: no tile)
+      bool live = project_mean(C, m, pj) && footprint_may_reach(pj, smax2, C.W, C.H) && project_cov(F, pj);
       // footprint radius: plain 3-sigma, or AdaGScale (Eq. 10, Sec. 3.3)
       float th = P.tau, rf = 0.f;
       if (live) {

@@ -153,7 +153,35 @@ struct Proj {
 
 // Projection of Gaussian (m, F) for camera C.  Returns false when the
 // Gaussian is culled (near plane or degenerate).
+// The view-space mean, the frustum clamp, T = J W and the 2D mean: the first
+// half of project_view (false behind the near plane).
+__device__ __forceinline__ bool project_mean(const DevCam& C, const float m[3], Proj& P);
+// The second half: V, the dilated 2D covariance, its conic and largest
+// eigenvalue (false when the determinant is not positive).
+__device__ __forceinline__ bool project_cov(const Frame& F, Proj& P);
+
 __device__ __forceinline__ bool project_view(const DevCam& C, const float m[3], const Frame& F, Proj& P) {
+  return project_mean(C, m, P) && project_cov(F, P);
+}
+
+// Can the footprint of a Gaussian whose mean passed project_mean touch a
+// pixel of the W x H image?  A bound taken before the covariance: the radius
+// of either scale mode is at most ceil(3 sqrt(lam1)); lam1 <= tr + 0.3163 for
+// the dilated covariance (trace tr, the eigenvalue's max(0.1, .) floor
+// included); tr = |T Rq S|_F^2 + 0.6 <= |T|_F^2 s_max^2 + 0.6.  With relative
+// slack far above fp32 rounding and a pixel of absolute slack, a false answer
+// means the full projection would find no tile (tile_span of u +- rf, v +- rf
+// is empty), so skipping it changes no output.  NaN bounds answer true.
+__device__ __forceinline__ bool footprint_may_reach(const Proj& P, float smax2, int W, int H) {
+  float tn2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; k++) tn2 = fmaf(P.Tm[k], P.Tm[k], tn2);
+  const float lam = fmaf(tn2 * smax2, 1.001f, 0.92f);
+  const float R = 3.003f * sqrtf(lam) + 2.f;
+  return !(P.u + R < 0.f || P.u - R > (float)(W - 1) || P.v + R < 0.f || P.v - R > (float)(H - 1));
+}
+
+__device__ __forceinline__ bool project_mean(const DevCam& C, const float m[3], Proj& P) {
   // view transform t = R m + t_cam (compensated: depth keys and the near-plane
   // test see the correctly rounded value up to an ulp)
 #pragma unroll
@@ -177,6 +205,12 @@ __device__ __forceinline__ bool project_view(const DevCam& C, const float m[3], 
     P.Tm[k] = jx * fmaf(-P.ctx, C.R[6 + k], C.R[k]);
     P.Tm[3 + k] = jy * fmaf(-P.cty, C.R[6 + k], C.R[3 + k]);
   }
+  P.u = fmaf(C.fx, P.t[0] * P.iz, C.cx);
+  P.v = fmaf(C.fy, P.t[1] * P.iz, C.cy);
+  return true;
+}
+
+__device__ __forceinline__ bool project_cov(const Frame& F, Proj& P) {
   // V = T (Rq S)
 #pragma unroll
   for (int r = 0; r < 2; r++)
@@ -201,8 +235,6 @@ __device__ __forceinline__ bool project_view(const DevCam& C, const float m[3], 
   P.C = ad * id;
   const float half = 0.5f * (ad - cd);
   P.lam1 = 0.5f * (ad + cd) + sqrtf(fmaxf(0.1f, half * half + P.b * P.b));
-  P.u = fmaf(C.fx, P.t[0] * P.iz, C.cx);
-  P.v = fmaf(C.fy, P.t[1] * P.iz, C.cy);
   return true;
 }
 
