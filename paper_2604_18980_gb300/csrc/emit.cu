@@ -394,9 +394,11 @@ __device__ __forceinline__ void warp_emit_ellipse(const uint4* rec, int m, uint3
 // 1024-entry partitions): striped loads of the order (coalesced) with the 16
 // rectangle gathers of a thread in flight together, the counts transposed
 // through shared memory for a blocked scan, a decoupled look-back for the
-// partition's offset, and the records written striped (coalesced 16-byte
-// stores).  Same records, block starts and total as the fused kernel's
-// record path.
+// partition's offset.  The records go out striped (coalesced 16-byte stores)
+// as soon as an entry's rectangle is known, with the count in the first-pair
+// field, which the last step overwrites (still in L2), so no entry state stays
+// in registers across the scan.  Same records, block starts and total as the
+// fused kernel's record path.
 constexpr int kScanItems = 16;
 constexpr int kScanPart = kEmitThreads * kScanItems;      // 4096 entries per partition
 
@@ -427,37 +429,37 @@ tile_scan_kernel(const uint2* __restrict__ rect, const uint32_t* __restrict__ or
   }
   const int64_t base = (int64_t)part * kScanPart;
 
-  // 1. striped entries li = k * 256 + tid: order, rectangle, count
+  // 1. striped entries li = k * 256 + tid: order, rectangle, count; the record
+  //    is written now with the count in place of the first pair (step 4 fixes it)
   uint32_t e[kScanItems];
-  uint2 r[kScanItems];
 #pragma unroll
   for (int k = 0; k < kScanItems; k++) {
     const int64_t s = base + k * kEmitThreads + tid;
-    e[k] = 0u;
+    e[k] = 0xffffffffu;
     if (s < total) {
       const uint32_t v = order ? __ldg(order + s) : (uint32_t)s;
       e[k] = AGS_DCHECK(v < (uint64_t)total_bound, status, AGS_CHECK_EMIT_ORDER) ? v : 0xffffffffu;
     }
   }
 #pragma unroll
-  for (int k = 0; k < kScanItems; k++)
-    r[k] = e[k] != 0xffffffffu && base + k * kEmitThreads + tid < total ? __ldg(rect + e[k]) : make_uint2(0u, 0u);
-#pragma unroll
   for (int k = 0; k < kScanItems; k++) {
-    const uint32_t w = (r[k].y & 0xffffu) - (r[k].x & 0xffffu), h = (r[k].y >> 16) - (r[k].x >> 16);
+    const int li = k * kEmitThreads + tid;
+    const uint2 r = e[k] != 0xffffffffu ? __ldg(rect + e[k]) : make_uint2(0u, 0u);
+    const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, w = (r.y & 0xffffu) - x0, h = (r.y >> 16) - y0;
     uint32_t c = w * h;
-    if (ell.splat) c = (c && e[k] != 0xffffffffu) ? __ldg(ell.touched + e[k]) : 0u;
-    s_c[scan_pad(k * kEmitThreads + tid)] = c;
+    if (ell.splat) c = c ? __ldg(ell.touched + e[k]) : 0u;
+    s_c[scan_pad(li)] = c;
+    if (base + li < total) {
+      const uint32_t ev = e[k] == 0xffffffffu ? 0u : e[k];
+      recs[base + li] = make_uint4(c, ev, (ev / n) * tiles_per_view + y0 * gx + x0, w);
+    }
   }
   __syncthreads();
 
   // 2. blocked scan: thread t owns entries 16t .. 16t+15
-  uint32_t cb[kScanItems], tsum = 0;
+  uint32_t tsum = 0;
 #pragma unroll
-  for (int j = 0; j < kScanItems; j++) {
-    cb[j] = s_c[scan_pad(tid * kScanItems + j)];
-    tsum += cb[j];
-  }
+  for (int j = 0; j < kScanItems; j++) tsum += s_c[scan_pad(tid * kScanItems + j)];
   uint32_t incl = tsum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -476,8 +478,9 @@ tile_scan_kernel(const uint2* __restrict__ rect, const uint32_t* __restrict__ or
   uint32_t run = wpre + incl - tsum;
 #pragma unroll
   for (int j = 0; j < kScanItems; j++) {
+    const uint32_t c = s_c[scan_pad(tid * kScanItems + j)];
     s_c[scan_pad(tid * kScanItems + j)] = run;
-    run += cb[j];
+    run += c;
   }
 
   // 3. decoupled look-back (warp 0) for the partition's global offset
@@ -517,16 +520,15 @@ tile_scan_kernel(const uint2* __restrict__ rect, const uint32_t* __restrict__ or
   __syncthreads();
   const uint64_t prefix = s_prefix;
 
-  // 4. striped records and the pair blocks that start inside each entry
-#pragma unroll
+  // 4. each record's first pair, and the pair blocks that start inside it
+#pragma unroll 4
   for (int k = 0; k < kScanItems; k++) {
     const int li = k * kEmitThreads + tid;
     if (base + li < total) {
-      const uint32_t x0 = r[k].x & 0xffffu, y0 = r[k].x >> 16, w = (r[k].y & 0xffffu) - x0;
-      const uint32_t c = (li + 1 < kScanPart ? s_c[scan_pad(li + 1)] : agg) - s_c[scan_pad(li)];
-      const uint64_t off = prefix + s_c[scan_pad(li)], end = off + c;
-      const uint32_t ev = e[k] == 0xffffffffu ? 0u : e[k];
-      recs[base + li] = make_uint4((uint32_t)off, ev, (ev / n) * tiles_per_view + y0 * gx + x0, w);
+      const uint32_t o = s_c[scan_pad(li)];
+      const uint32_t c = (li + 1 < kScanPart ? s_c[scan_pad(li + 1)] : agg) - o;
+      const uint64_t off = prefix + o, end = off + c;
+      recs[base + li].x = (uint32_t)off;
       const uint64_t lim = end < (uint64_t)capacity ? end : (uint64_t)capacity;
       for (uint64_t q = (off + kTileChunk - 1) / kTileChunk * kTileChunk; q < lim; q += kTileChunk)
         chunk_start[q / kTileChunk] = (uint32_t)(base + li);
