@@ -465,6 +465,41 @@ def test_emit_tile_pairs_balanced_blocks():
         assert torch.all(k32[P:] == -1)
 
 
+def test_emit_tile_pairs_long_runs_of_empty_entries():
+    """An order with a run of thousands of entries without pairs in its middle:
+    the pair block that straddles the run spans more records than one staged
+    window, so the second pass must look the next window up.  Identical to the
+    64-bit emission's tile words and values."""
+    scene, cams = _c1(n=6000, W=640, H=480, views=2)
+    scene["mean"][:, 1000:5000] = np.nan            # 4000 Gaussians culled in both views
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, 0, 0.0, presort=True)
+    r.preprocess()
+    touched = r.proj["tiles_touched"]
+    e_all = torch.arange(r.V * r.n, device="cuda")
+    vis, empty = e_all[touched > 0], e_all[touched == 0]
+    assert len(empty) > 3 * 2049
+    half = len(vis) // 2
+    order = torch.cat([vis[:half], empty, vis[half:]]).to(torch.int32)
+    cap = r.capacity
+    for flags in (0, B.AGS_EMIT_SINGLE_PASS):
+        k64 = torch.empty(cap, dtype=torch.int64, device="cuda")
+        v64 = torch.empty(cap, dtype=torch.int32, device="cuda")
+        k32 = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+        v32 = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+        n64 = torch.zeros(1, dtype=torch.int64, device="cuda")
+        n32 = torch.zeros(1, dtype=torch.int64, device="cuda")
+        B.ags_emit_pairs(r.proj, r.n, cams, k64, v64, cap, n64, r.status, r.ws_emit, order=order)
+        B.ags_emit_tile_pairs(r.proj, r.n, cams, k32, v32, cap, n32, r.status, r.ws_emit, order=order, flags=flags)
+        r.check()
+        P = int(n64.item())
+        assert P == int(n32.item()) and P > 2 * 2048
+        hi = (k64[:P].cpu().numpy().view(np.uint64) >> np.uint64(32)).astype(np.uint32)
+        np.testing.assert_array_equal(k32[:P].cpu().numpy().view(np.uint32), hi)
+        assert torch.equal(v32[:P], v64[:P])
+        assert torch.all(k32[P:] == -1)
+
+
 def test_compact_visible_edges():
     """Compaction of ragged counts (not a multiple of the partition), all-culled
     and none-culled inputs, and more partitions than one chunk of the offset
