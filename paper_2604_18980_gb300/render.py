@@ -196,12 +196,21 @@ class Renderer:
         return max(1, -(-self.end_bit // self.digit_bits)), self.digit_bits
 
     def launches_per_forward(self) -> int:
-        # preprocess, emit, (histogram, digit scan, passes, ranges fix-up), blend
-        n = 1 + 1 + (2 + self.sort_plan()[0] + 1) + 1
-        if self.presort:       # compaction, then (histogram, digit scan, passes)
-            n += 1 + 2 + digit_plan(self.dsort_end, self.digit_bits)[0]
+        """libags kernel launches of one forward (memsets are not kernels)."""
+        ellipse = self.tile_test == B.AGS_TILE_ELLIPSE
+        # preprocess (+ the ellipse test's tile count), blend
+        n = 1 + (1 if ellipse else 0) + 1
+        # pair sort: histogram, digit scan, passes, ranges initialisation and fix-up
+        n += 2 + self.sort_plan()[0] + 2
+        if self.presort:
+            # emission: two passes (scan, pairs) or one fused pass
+            n += 2 if self.emit_two_pass else 1
+            # compaction (count, scan, write), then (histogram, digit scan, passes)
+            n += 3 + 2 + digit_plan(self.dsort_end, self.digit_bits)[0]
             if self.view_major:   # view keys, then (histogram, digit scan, one pass)
                 n += 1 + 3
+        else:
+            n += 1
         return n
 
     # -- stages ---------------------------------------------------------------

@@ -621,3 +621,25 @@ def test_blend_counters_match_oracle(mode, K):
     assert abs(bl - bl_o) <= int(px_len[flagged].sum()), (bl, bl_o)
     if not flagged.any():
         assert (ev, bl) == (ev_o, bl_o)
+
+
+@pytest.mark.parametrize("knobs", [dict(), dict(emit_two_pass=False), dict(presort=False),
+                                   dict(tile_test=B.AGS_TILE_ELLIPSE), dict(view_major=False)])
+def test_launches_per_forward_counts_the_kernels(knobs):
+    """Renderer.launches_per_forward(), the bench line's gpu_launches per step,
+    equals the kernels one forward launches (counted by the profiler; memsets
+    are not kernels)."""
+    from torch.profiler import ProfilerActivity, profile
+    scene, cams = _c1(n=6000, W=160, H=120, views=2)
+    sc = R.scene_to_device(scene)
+    r = R.Renderer(sc, cams, 1, 0.3, keep_state=False, **knobs)
+    r.forward()
+    r.check()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        r.forward()
+        torch.cuda.synchronize()
+    names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+    kernels = [nm for nm in names if not nm.lower().startswith(("memset", "memcpy"))]
+    if not kernels:
+        pytest.skip("the profiler recorded no kernels on this box")
+    assert len(kernels) == r.launches_per_forward(), kernels
