@@ -95,6 +95,36 @@ def test_batched_views_match_single_views():
     _full_check(scene, cams, 1, 0.3)
 
 
+def test_maximum_views_in_one_batch():
+    """AGS_MAX_VIEWS views in one launch per stage (the most view bits in the
+    keys) render each view exactly as it renders alone, with the default
+    knobs and with 64-bit keys."""
+    scene, cams = _c1(n=3000, W=72, H=40, views=B.AGS_MAX_VIEWS)
+    for knobs in (dict(), dict(presort=False)):
+        rb = gpu_render(scene, cams, 1, 0.3, **knobs)
+        assert rb.V == B.AGS_MAX_VIEWS
+        for v in (0, 1, 17, B.AGS_MAX_VIEWS - 1):
+            r1 = gpu_render(scene, [cams[v]], 1, 0.3, **knobs)
+            np.testing.assert_array_equal(rb.image[v].cpu().numpy(), r1.image[0].cpu().numpy())
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 40), (37, 1), (16, 16), (17, 17)])
+def test_tiny_and_single_tile_images(W, H):
+    """Images of one pixel, one column, one row, exactly one tile and one tile
+    plus one pixel each way, against the oracle: features, pair lists and
+    image exact outside the edge classes.  The ceilings on the edge classes'
+    share are lifted: with a handful of pixels and live Gaussians a fraction
+    says nothing."""
+    scene, cams = _c1(n=2000, W=W, H=H, views=2)
+    r = gpu_render(scene, cams, 1, 0.3)
+    outs = [oracle.render(scene, cam, oracle_params(cam, 1, 0.3)) for cam in cams]
+    for v, oo in enumerate(outs):
+        compare_features(r, oo, v, max_edge=1.0)
+    _, edge_tiles = compare_lists(r, outs, max_edge_tiles=1.0)
+    for v, oo in enumerate(outs):
+        compare_image(r.image[v].cpu().numpy(), oo, edge_tiles=edge_tiles[v], max_flagged=1.0)
+
+
 def test_empty_and_all_culled():
     scene, cams = _c1(n=0, W=64, H=48)
     r = gpu_render(scene, cams, 0, 0.0, bg=(0.2, 0.4, 0.6), capacity=1024)
