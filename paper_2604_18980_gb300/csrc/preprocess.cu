@@ -52,13 +52,15 @@ __device__ __forceinline__ void tile_span(float lo, float hi, int len, int& t0, 
 
 constexpr int kPreThreads = 256;
 constexpr int kPreWarps = kPreThreads / 32;
+constexpr int kShFloats = 48;                       // SH coefficients x channels of one Gaussian, degree 3
+constexpr size_t kPreShBytes = (size_t)kPreWarps * kShFloats * 32 * sizeof(float);
 
 // Colour of one queued survivor (SH at the world-space direction from the
 // camera centre, + 0.5, clamped at 0) and the rest of its splat record.  The
 // Gaussian's mean and opacity arrive from its lane by shuffles (all lanes call
 // this; only `go` lanes write).
 __device__ __forceinline__ void colour_job(bool go, float4 jb, uint32_t tg, int64_t iw, int64_t n, const float m[3],
-                                           float opac, const CamBatch& cams, const DevParams& P, const PreIn& in,
+                                           float opac, const CamBatch& cams, const DevParams& P, const float* wsh,
                                            const PreOut& out, int64_t* status) {
   const int gl = (int)(tg & 31u), gv = (int)((tg >> 8) & 0xffu);
   const float mx = __shfl_sync(0xffffffffu, m[0], gl), my = __shfl_sync(0xffffffffu, m[1], gl),
@@ -76,7 +78,7 @@ __device__ __forceinline__ void colour_job(bool go, float4 jb, uint32_t tg, int6
   for (int c = 0; c < 16; c++) {
     if (c < nc) {
 #pragma unroll
-      for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(__ldg(in.sh + (int64_t)(c * 3 + ch) * n + gi), Y[c], rgb[ch]);
+      for (int ch = 0; ch < 3; ch++) rgb[ch] = fmaf(wsh[(c * 3 + ch) * 32 + gl], Y[c], rgb[ch]);
     }
   }
   uint8_t flags = (uint8_t)(tg >> 16);
@@ -138,6 +140,26 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(PreIn in, in
     for (int view = 0; view < views; view++) write_culled(out, (int64_t)view * n + i);
   }
   const bool ok = active && finite;
+  // the SH planes of the warp's 32 Gaussians, copied to shared memory while
+  // the views are projected; waited for before the first colour batch
+  extern __shared__ float s_sh[];                       // [kPreWarps][48][32]
+  float* wsh = s_sh + warp * kShFloats * 32;
+  if (active) {
+    const int planes = (P.sh_degree + 1) * (P.sh_degree + 1) * 3;
+    for (int c = 0; c < planes; c++) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(wsh + c * 32 + lane);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(in.sh + (int64_t)c * n + i) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  bool sh_ready = false;
+  auto sh_wait = [&]() {      // warp-uniform: every lane reaches it together
+    if (!sh_ready) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncwarp();
+      sh_ready = true;
+    }
+  };
   Frame F;                    // scales, rotation, R S and opacity: once for all views
   make_frame(ls, q, logit, F);
   const float smax = fmaxf(F.s[0], fmaxf(F.s[1], F.s[2]));
@@ -204,7 +226,8 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(PreIn in, in
     qn += __popc(bal);
     __syncwarp();
     if (qn >= 32) {           // a full batch: one colour per lane
-      colour_job(true, qj[lane], qt[lane], iw, n, m, F.opac, cams, P, in, out, status);
+      sh_wait();
+      colour_job(true, qj[lane], qt[lane], iw, n, m, F.opac, cams, P, wsh, out, status);
       __syncwarp();
       if (lane < qn - 32) {
         qj[lane] = qj[lane + 32];
@@ -216,9 +239,12 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(PreIn in, in
   }
   if (qn > 0) {
     const bool go = lane < qn;
+    sh_wait();
     colour_job(go, go ? qj[lane] : make_float4(0.f, 0.f, 0.f, 0.f), go ? qt[lane] : 0u, iw, n, m, F.opac, cams, P,
-               in, out, status);
+               wsh, out, status);
   }
+  // no copy into this block's shared memory may still be in flight when it exits
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Ellipse tile test (tile_test AGS_TILE_ELLIPSE): the kept tiles of every
@@ -276,8 +302,11 @@ extern "C" ags_status ags_preprocess(const ags_gaussians* g, const ags_camera* c
   if (dp.tile_test == AGS_TILE_ELLIPSE && !out->tiles_touched) return AGS_ERR_INVALID_ARG;
   PreIn in{g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
   PreOut po{out->splat, out->depth, out->rect, out->tiles_touched, out->flags, out->depth_key};
-  preprocess_kernel<<<(unsigned)((g->n + kPreThreads - 1) / kPreThreads), kPreThreads, 0, (cudaStream_t)stream>>>(
-      in, g->n, views, cb, dp, po, d_status);
+  cudaError_t ea = cudaFuncSetAttribute(preprocess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kPreShBytes);
+  if (ea != cudaSuccess) return launch_status(ea);
+  preprocess_kernel<<<(unsigned)((g->n + kPreThreads - 1) / kPreThreads), kPreThreads, kPreShBytes,
+                      (cudaStream_t)stream>>>(in, g->n, views, cb, dp, po, d_status);
   if (dp.tile_test == AGS_TILE_ELLIPSE) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return launch_status(e);
