@@ -140,19 +140,27 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(PreIn in, in
     for (int view = 0; view < views; view++) write_culled(out, (int64_t)view * n + i);
   }
   const bool ok = active && finite;
-  // the SH planes of the warp's 32 Gaussians, copied to shared memory while
-  // the views are projected; waited for before the first colour batch
+  // the SH planes of the warp's 32 Gaussians, copied to shared memory at the
+  // first view in which one of them survives, while further views are
+  // projected; waited for before the first colour batch (a warp none of whose
+  // Gaussians survives anywhere reads no SH)
   extern __shared__ float s_sh[];                       // [kPreWarps][48][32]
   float* wsh = s_sh + warp * kShFloats * 32;
-  if (active) {
-    const int planes = (P.sh_degree + 1) * (P.sh_degree + 1) * 3;
-    for (int c = 0; c < planes; c++) {
-      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(wsh + c * 32 + lane);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(in.sh + (int64_t)c * n + i) : "memory");
+  bool sh_issued = false, sh_ready = false;
+  auto sh_issue = [&]() {     // warp-uniform
+    if (!sh_issued) {
+      if (active) {
+        const int planes = (P.sh_degree + 1) * (P.sh_degree + 1) * 3;
+        for (int c = 0; c < planes; c++) {
+          const uint32_t dst = (uint32_t)__cvta_generic_to_shared(wsh + c * 32 + lane);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(in.sh + (int64_t)c * n + i)
+                       : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      sh_issued = true;
     }
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  bool sh_ready = false;
+  };
   auto sh_wait = [&]() {      // warp-uniform: every lane reaches it together
     if (!sh_ready) {
       asm volatile("cp.async.wait_all;" ::: "memory");
@@ -218,6 +226,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(PreIn in, in
     }
     // enqueue this view's survivors behind the waiting ones
     const unsigned bal = __ballot_sync(0xffffffffu, surv);
+    if (bal) sh_issue();
     if (surv) {
       const int slot = qn + __popc(bal & lanemask_lt());
       qj[slot] = job;
