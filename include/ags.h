@@ -331,6 +331,12 @@ size_t ags_sort_workspace_bytes(int64_t capacity);
                                         instead of 256 threads of 16 keys (4096 keys either way);
                                         same result.  64-bit keys and 9-bit digits always take the
                                         512-thread pass. */
+#define AGS_SORT_PERSISTENT 16       /* sort flag: the 256-thread digit passes launch only as many
+                                        blocks as are resident at once, each taking partitions of
+                                        the count on the device until none is left, instead of one
+                                        block per partition of the capacity; same result, faster
+                                        when the count is far below the capacity (the depth
+                                        pre-sort of the visible Gaussian-views) */
 
 /* Stable LSD radix sort of (keys, vals) by key bits [begin_bit, end_bit)
  * (Sec. 2.1 sorting stage): one global-histogram pass, then one single-pass
@@ -340,8 +346,8 @@ size_t ags_sort_workspace_bytes(int64_t capacity);
  * Keys already stably ordered by their bits below begin_bit stay so ordered
  * within equal [begin_bit, end_bit) fields: pairs emitted in depth order
  * need only the tile digits, with the same result as a sort of all bits.
- * flags: AGS_SORT_IDENTITY_VALUES, AGS_SORT_DISCARD_KEYS, AGS_SORT_RANK_OR, AGS_SORT_WIDE_BLOCK
- * (any other bit but AGS_SORT_TEST_STALL is invalid).  `keys` must be
+ * flags: AGS_SORT_IDENTITY_VALUES, AGS_SORT_DISCARD_KEYS, AGS_SORT_RANK_OR, AGS_SORT_WIDE_BLOCK,
+ * AGS_SORT_PERSISTENT (any other bit but AGS_SORT_TEST_STALL is invalid).  `keys` must be
  * 16-byte aligned when a digit pass runs (read 16 bytes at a time).
  * The sorted result lands in (keys, vals) when the number of digit passes is
  * even and in (keys_alt, vals_alt) when it is odd; *result_in_alt (host)

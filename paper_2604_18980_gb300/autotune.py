@@ -10,8 +10,10 @@ two passes balanced by pairs.  The block shapes come second, on the best of
 those: the blend's warp block (8x16 pixels, two warps a tile and four rows a
 lane, or 8x8, four warps and two rows), its tile batch (32 or 64 splats
 staged per warp and round) and the partition shape of the 32-bit sort passes
-(256 threads of 16 keys or 512 of 8).  The stages do not interact, so the two
-rounds find the best combination with 26 timings instead of 144.  Every
+(256 threads of 16 keys or 512 of 8).  A third round picks the depth
+pre-sort's grid: resident blocks taking partitions of the visible count, or
+one block per partition of every Gaussian-view.  The stages do not interact,
+so the rounds find the best combination with 28 timings instead of 288.  Every
 candidate renders the same frames through the same kernels -- results are
 identical -- and the fastest one (CUDA-event time of a whole forward, after
 warm-up) is kept.  Results are cached in a JSON file keyed by GPU name and
@@ -33,8 +35,9 @@ CANDIDATES = ([dict(digit_bits=d, presort=True, pair_rank_or=o, emit_two_pass=t)
               + [dict(digit_bits=d, presort=False, pair_rank_or=o) for o in (True, False) for d in (9, 8, 7)])
 SHAPES = [dict(blend_flags=f, sort_wide=w) for w in (False, True)
           for f in (0, B.AGS_BLEND_ROWS2, B.AGS_BLEND_BATCH64, B.AGS_BLEND_ROWS2 | B.AGS_BLEND_BATCH64)]
-KNOBS = ("digit_bits", "presort", "pair_rank_or", "emit_two_pass", "blend_flags", "sort_wide")
-DEFAULTS = dict(emit_two_pass=True, blend_flags=0, sort_wide=False)
+DEPTH_PASSES = [dict(depth_persistent=p) for p in (True, False)]
+KNOBS = ("digit_bits", "presort", "pair_rank_or", "emit_two_pass", "blend_flags", "sort_wide", "depth_persistent")
+DEFAULTS = dict(emit_two_pass=True, blend_flags=0, sort_wide=False, depth_persistent=True)
 
 
 def workload_key(scene: dict, cams: list, scale_mode: int) -> str:
@@ -60,7 +63,8 @@ def _time_forward(r: R.Renderer, warmup: int, reps: int) -> float:
 def tune(scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_ADAGSCALE, K: float = 0.0, lut=None,
          warmup: int = 2, reps: int = 5, use_cache: bool = True, candidates=None, shapes=None) -> dict:
     """Fastest configuration for this workload: the KNOBS, "ms" and "table"
-    (every timed candidate with its ms, the stage knobs first, then the shapes)."""
+    (every timed candidate with its ms: the stage knobs, then the shapes, then
+    the depth pre-sort's grid)."""
     key = workload_key(scene, cams, scale_mode)
     cache = {}
     if use_cache and os.path.exists(CACHE):
@@ -85,6 +89,8 @@ def tune(scene: dict, cams: list, scale_mode: int = B.AGS_SCALE_ADAGSCALE, K: fl
     best = min((dict(DEFAULTS, **c) for c in (candidates or CANDIDATES)), key=timed)
     stage = {k: best[k] for k in KNOBS if k not in ("blend_flags", "sort_wide")}
     best = min((dict(stage, **sh) for sh in (shapes if shapes is not None else SHAPES)), key=timed)
+    if best["presort"]:       # the depth pre-sort's grid: resident blocks or one per partition
+        best = min((dict(best, **dp) for dp in DEPTH_PASSES), key=timed)
     ms = min(t["ms"] for t in table if all(t.get(k, DEFAULTS.get(k)) == best[k] for k in KNOBS))
     out = dict({k: best[k] for k in KNOBS}, ms=ms, table=table)
     if use_cache:

@@ -301,6 +301,7 @@ AGS_SORT_IDENTITY_VALUES = 1
 AGS_SORT_DISCARD_KEYS = 2
 AGS_SORT_RANK_OR = 4
 AGS_SORT_WIDE_BLOCK = 8       # 32-bit key passes on 512 x 8 partitions instead of 256 x 16
+AGS_SORT_PERSISTENT = 16      # resident blocks take partitions of the device count by ticket
 AGS_SORT_TEST_STALL = 256     # tests only: a look-back partition that never publishes
 
 

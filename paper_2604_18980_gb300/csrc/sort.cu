@@ -424,7 +424,7 @@ __device__ __forceinline__ uint32_t bfe32(uint32_t k, int shift, int bits) {
   return d;
 }
 
-template <int RADIX, bool kOr>
+template <int RADIX, bool kOr, bool kPersist>
 __global__ void __launch_bounds__(kLT, 4)
 lean_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
             uint32_t* __restrict__ vout, const int64_t* count_ptr, int64_t capacity, int identity, int shift,
@@ -434,6 +434,14 @@ lean_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sm& S = *reinterpret_cast<Sm*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool dthread = tid < RADIX;
+  const uint32_t gp = dthread ? __ldg(gprefix + tid) : 0u;
+  const uint32_t count = clamped_count(count_ptr, capacity);
+  const uint32_t nparts = (count + kSortPart - 1) / kSortPart;
+  // one partition per block, or (persistent) partitions in ticket order until
+  // none is left -- every lower ticket belongs to a block that is running or
+  // done, so the look-back always makes progress
+  for (;;) {
   if (tid == 0) S.part = atomicAdd(counter, 1u);
   {
     uint32_t* wz = reinterpret_cast<uint32_t*>(&S.u.r.wh[0][0]);
@@ -443,12 +451,9 @@ lean_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, 
       for (int i = tid; i < kLW * (RADIX + 1); i += kLT) bz[i] = 0u;
     }
   }
-  const bool dthread = tid < RADIX;
-  const uint32_t gp = dthread ? __ldg(gprefix + tid) : 0u;
   __syncthreads();
   const uint32_t part = S.part;
-  const uint32_t count = clamped_count(count_ptr, capacity);
-  if (part >= (count + kSortPart - 1) / kSortPart) return;
+  if (part >= nparts) return;
   const uint32_t base = part * kSortPart;
   const uint32_t ibase = base + (uint32_t)warp * (32u * kLI) + (uint32_t)lane;   // item i at ibase + 32 i
   const bool full = base + kSortPart <= count;
@@ -596,29 +601,42 @@ lean_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, 
       }
     }
   }
+  if (!kPersist) return;
+  __syncthreads();     // the staged keys are read above; the next partition overwrites them
+  }
 }
 
 template <int RADIX>
 static cudaError_t launch_lean(bool rank_or, dim3 grid, cudaStream_t st, const uint32_t* kin, const uint32_t* vin,
                                uint32_t* kout, uint32_t* vout, const int64_t* count_ptr, int64_t capacity, int identity,
                                int shift, int bits, const uint32_t* gprefix, uint32_t* lookback, uint32_t* counter,
-                               int64_t* status, uint32_t* ranges, uint32_t num_ranges, RangeMap rmap, WaitHook hook) {
+                               int64_t* status, uint32_t* ranges, uint32_t num_ranges, RangeMap rmap, WaitHook hook,
+                               bool persistent) {
   cudaError_t e;
-  if (rank_or) {
-    auto kern = lean_kernel<RADIX, true>;
-    const int smem = (int)sizeof(LeanSmem<RADIX, true>);
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // persistent: as many blocks as are resident at once (they take the
+  // partitions of the count on the device by ticket), never more than the
+  // partitions of the capacity; otherwise one block per partition of the capacity
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto resident = [&](auto kern, int smem) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLT, smem) != cudaSuccess || occ < 1) occ = 1;
+    return persistent ? dim3(std::min<unsigned>(grid.x, (unsigned)(sms * occ))) : grid;
+  };
+  auto go = [&](auto kern, int smem) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kLT, smem, st>>>(kin, vin, kout, vout, count_ptr, capacity, identity, shift, bits, gprefix, lookback,
-                                  counter, status, ranges, num_ranges, rmap, hook);
-  } else {
-    auto kern = lean_kernel<RADIX, false>;
-    const int smem = (int)sizeof(LeanSmem<RADIX, false>);
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, kLT, smem, st>>>(kin, vin, kout, vout, count_ptr, capacity, identity, shift, bits, gprefix, lookback,
-                                  counter, status, ranges, num_ranges, rmap, hook);
-  }
+    kern<<<resident(kern, smem), kLT, smem, st>>>(kin, vin, kout, vout, count_ptr, capacity, identity, shift, bits,
+                                                  gprefix, lookback, counter, status, ranges, num_ranges, rmap, hook);
+    return cudaSuccess;
+  };
+  const int smem_or = (int)sizeof(LeanSmem<RADIX, true>), smem_m = (int)sizeof(LeanSmem<RADIX, false>);
+  if (rank_or)
+    e = persistent ? go(lean_kernel<RADIX, true, true>, smem_or) : go(lean_kernel<RADIX, true, false>, smem_or);
+  else
+    e = persistent ? go(lean_kernel<RADIX, false, true>, smem_m) : go(lean_kernel<RADIX, false, false>, smem_m);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -654,7 +672,8 @@ static cudaError_t launch_passes(K*& kin, uint32_t*& vin, K* kout, uint32_t* vou
                                                   reinterpret_cast<uint32_t*>(ko), vout, d_num_pairs, capacity,
                                                   identity, sh, __builtin_popcount(mask), ghist + p * RADIX,
                                                   lookback, counters + p, d_status, last ? ranges : nullptr,
-                                                  (uint32_t)num_ranges, rmap, wait_hook(flags & AGS_SORT_TEST_STALL));
+                                                  (uint32_t)num_ranges, rmap, wait_hook(flags & AGS_SORT_TEST_STALL),
+                                                  (flags & AGS_SORT_PERSISTENT) != 0);
       if (e != cudaSuccess) return e;
       std::swap(kin, kout);
       std::swap(vin, vout);
@@ -697,7 +716,7 @@ static ags_status sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
   if (begin_bit < 0 || end_bit > kKeyBits || begin_bit > end_bit || digit_bits < 4 || digit_bits > 9)
     return AGS_ERR_INVALID_ARG;
   if (flags & ~(AGS_SORT_IDENTITY_VALUES | AGS_SORT_DISCARD_KEYS | AGS_SORT_RANK_OR | AGS_SORT_WIDE_BLOCK |
-                AGS_SORT_TEST_STALL))
+                AGS_SORT_PERSISTENT | AGS_SORT_TEST_STALL))
     return AGS_ERR_INVALID_ARG;
   const int passes = (end_bit - begin_bit + digit_bits - 1) / digit_bits;
   if (passes > kMaxPasses) return AGS_ERR_INVALID_ARG;

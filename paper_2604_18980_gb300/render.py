@@ -87,7 +87,8 @@ class Renderer:
                  headroom: float = 1.25, want_backward: bool = False, want_stats: bool = False,
                  presort: bool = True, pair_rank_or: bool = True, emit_two_pass: bool = True,
                  keep_state: bool = True, tile_test: int = B.AGS_TILE_SQUARE, view_major: bool | None = None,
-                 blend_flags: int = 0, sort_wide: bool = False, depth_rank_or: bool = True):
+                 blend_flags: int = 0, sort_wide: bool = False, depth_rank_or: bool = True,
+                 depth_persistent: bool = True):
         self.scene = scene
         self.cams = list(cams)
         self.V = len(self.cams)
@@ -105,6 +106,11 @@ class Renderer:
         # depth keys: the low digits of the float bits are close to uniform, so a
         # warp's keys mostly carry distinct digits -- the case of the atomic-OR ranking
         self.depth_rank_flags = B.AGS_SORT_RANK_OR if depth_rank_or else 0
+        # the depth keys' capacity is every Gaussian-view, the count only the
+        # visible ones (a few to a few tens of percent): resident blocks can take
+        # the partitions of the count instead of one block per partition of the capacity
+        self.depth_pass_flags = B.AGS_SORT_PERSISTENT if depth_persistent else 0
+        self.depth_rank_flags |= self.depth_pass_flags
         self.emit_flags = B.AGS_EMIT_ELLIPSE if tile_test == B.AGS_TILE_ELLIPSE else 0
         self.tile_bits = max(1, (self.T - 1).bit_length())
         if view_major is None:
@@ -236,7 +242,7 @@ class Renderer:
                 B.ags_view_keys(self.emit_order, self.n_visible, self.V * self.n, self.n, self.dkey)
                 alt2 = B.ags_sort32(self.dkey, self.emit_order, self.dkey_alt, other, self.n_visible, self.V * self.n,
                                     0, vb, min(9, max(4, vb)), None, 0, self.status, self.ws_dsort,
-                                    flags=B.AGS_SORT_DISCARD_KEYS | self.sort_flags)
+                                    flags=B.AGS_SORT_DISCARD_KEYS | self.depth_pass_flags | self.sort_flags)
                 self.emit_order = other if alt2 else self.emit_order
 
     def emit(self):

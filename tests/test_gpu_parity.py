@@ -363,20 +363,24 @@ def test_sort_tiles_view_shifted_keys(count, views, tiles, digit, flags):
     assert np.all(got[views * nn - 3:] == -1)
 
 
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("rank_or", [False, True])
 @pytest.mark.parametrize("count,bits,digit,flags", [(1, 12, 8, 0), (4095, 13, 8, 2), (4097, 17, 9, 0),
                                                     (100003, 17, 9, 2), (250000, 20, 7, 1), (77777, 16, 5, 3),
                                                     (300001, 32, 8, 3), (65536, 32, 9, 0)])
-def test_sort32_random_keys_stable(count, bits, digit, flags, rank_or):
+def test_sort32_random_keys_stable(count, bits, digit, flags, rank_or, persistent):
     """32-bit keys: the stable order, the ranges of the whole key, the identity
-    values flag, the discarded-keys flag and both ranking methods."""
+    values flag, the discarded-keys flag, both ranking methods and the
+    persistent passes (with a capacity six times the count, their use)."""
     if rank_or:
         flags |= B.AGS_SORT_RANK_OR
+    if persistent:
+        flags |= B.AGS_SORT_PERSISTENT
     rng = np.random.default_rng(count + bits)
     keys = rng.integers(0, 1 << bits, count, dtype=np.uint64).astype(np.uint32)
     keys[rng.random(count) < 0.3] = keys[0]          # long runs of equal keys: stability matters
     vals = rng.permutation(count).astype(np.uint32)
-    cap = count + 77
+    cap = count * (6 if persistent else 1) + 77
     k = torch.zeros(cap, dtype=torch.int32, device="cuda")
     v = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
     k[:count] = torch.from_numpy(keys.view(np.int32)).cuda()
@@ -592,7 +596,8 @@ def test_autotuner_candidates_render_identically():
         np.testing.assert_array_equal(v, lists[0][1])
     best = autotune.tune(sc, cams, 1, 0.3, use_cache=False, warmup=1, reps=2)
     assert best["digit_bits"] in (7, 8, 9)
-    assert len(best["table"]) == len(autotune.CANDIDATES) + len(autotune.SHAPES)
+    assert len(best["table"]) == (len(autotune.CANDIDATES) + len(autotune.SHAPES)
+                                  + (len(autotune.DEPTH_PASSES) if best["presort"] else 0))
     assert all(k in best for k in autotune.KNOBS)
 
 
@@ -608,7 +613,7 @@ def test_launch_shapes_give_identical_outputs(digit_bits):
     scene, cams = _c1(n=12000, W=200, H=150, views=2)
     sc = R.scene_to_device(scene)
     ref = None
-    for sh in autotune.SHAPES + [dict(depth_rank_or=False)]:
+    for sh in autotune.SHAPES + [dict(depth_rank_or=False), dict(depth_persistent=False)]:
         r = R.Renderer(sc, cams, 1, 0.3, want_stats=True, digit_bits=digit_bits, **sh)
         max_T = torch.zeros(r.V * r.n, dtype=torch.float32, device="cuda")
         img = r.forward(max_T=max_T).clone()

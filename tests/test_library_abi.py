@@ -109,12 +109,12 @@ def test_invalid_arguments_rejected_on_host(lib):
                       None, 0, None) == 1
     assert L.ags_sort(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
                       10, 0, 40, 8, 0, None, 0, ctypes.byref(alt), st, None, 0, None) == 1
-    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 8, 16, None, 0, ctypes.byref(alt), st, None, 0,
+    assert L.ags_sort(None, None, None, None, npairs, 10, 0, 40, 8, 32, None, 0, ctypes.byref(alt), st, None, 0,
                       None) == 1
     # 32-bit sort: end bit beyond the key, unknown flag, unaligned keys
     assert L.ags_sort32(None, None, None, None, npairs, 10, 0, 33, 8, 0, None, 0, ctypes.byref(alt), st, None, 0,
                         None) == 1
-    assert L.ags_sort32(None, None, None, None, npairs, 10, 0, 32, 8, 16, None, 0, ctypes.byref(alt), st, None, 0,
+    assert L.ags_sort32(None, None, None, None, npairs, 10, 0, 32, 8, 32, None, 0, ctypes.byref(alt), st, None, 0,
                         None) == 1
     assert L.ags_sort32(ctypes.c_void_p(20), ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), npairs,
                         10, 0, 32, 8, 0, None, 0, ctypes.byref(alt), st, ctypes.c_void_p(256), 1 << 20, None) == 1
