@@ -242,7 +242,7 @@ class Renderer:
                 B.ags_view_keys(self.emit_order, self.n_visible, self.V * self.n, self.n, self.dkey)
                 alt2 = B.ags_sort32(self.dkey, self.emit_order, self.dkey_alt, other, self.n_visible, self.V * self.n,
                                     0, vb, min(9, max(4, vb)), None, 0, self.status, self.ws_dsort,
-                                    flags=B.AGS_SORT_DISCARD_KEYS | self.depth_pass_flags | self.sort_flags)
+                                    flags=B.AGS_SORT_DISCARD_KEYS | self.depth_rank_flags | self.sort_flags)
                 self.emit_order = other if alt2 else self.emit_order
 
     def emit(self):
