@@ -721,9 +721,10 @@ def stage_bytes(stage, r, passes):
         return G * 8 + live * 4 + P * 12, "emit_kernel"
     # preprocess: 44 B geometry per Gaussian and 192 B SH per Gaussian that survives
     # in some view, read once per batch; per view, survivors write 48 B splat + 4 depth
-    # + 8 rect + 4 count + 1 flag + 4 depth key = 69 B, culled Gaussians 17 B
+    # + 8 rect + 4 count + 1 flag = 65 B, culled Gaussian-views 8 rect + 4 count + 1 flag
+    # = 13 B (the renderer requests no separate depth keys)
     any_live = int(((r.proj["flags"].view(V, n) & 0x80) == 0).any(0).sum().item())
-    return n * 44 + any_live * 192 + live * 69 + (G - live) * 17, "preprocess_kernel"
+    return n * 44 + any_live * 192 + live * 65 + (G - live) * 13, "preprocess_kernel"
 
 
 def roofline(stage, ms, r, evals, pk, pk_src, passes, clk, workload=WORKLOAD, slots=None):
