@@ -53,9 +53,13 @@ def test_emission_look_back_gives_up_and_reports():
     assert int(npairs.item()) == r.pairs()
 
 
-def test_sort_look_back_gives_up_and_reports():
+@pytest.mark.parametrize("extra,count", [(0, 50000), (B.AGS_SORT_PERSISTENT, 50000),
+                                         (B.AGS_SORT_PERSISTENT, 4000000)])
+def test_sort_look_back_gives_up_and_reports(extra, count):
+    """13 partitions of 4096 keys, and (persistent passes) about 980, more than
+    the blocks resident at once, so that blocks go on to further partitions
+    after the one that gave up."""
     rng = np.random.default_rng(2)
-    count = 50000                    # 13 partitions of 4096 keys
     keys = rng.integers(0, 1 << 20, count).astype(np.uint32)
     k = torch.zeros(count + GUARD, dtype=torch.int32, device="cuda")
     k[:count] = torch.from_numpy(keys.view(np.int32))
@@ -66,7 +70,7 @@ def test_sort_look_back_gives_up_and_reports():
     st = torch.zeros(4, dtype=torch.int64, device="cuda")
     ws = torch.empty(B.ags_sort_workspace_bytes(count), dtype=torch.uint8, device="cuda")
     alt = B.ags_sort32(k, v, ka, va, n, count, 0, 20, 7, None, 0, st, ws,
-                       flags=B.AGS_SORT_TEST_STALL)
+                       flags=B.AGS_SORT_TEST_STALL | extra)
     code, detail = B.ags_check(st, raise_on_error=False)
     assert code == B.AGS_ERR_TIMEOUT and detail == STAGE_SORT
     assert torch.all(ka[count:] == -7) and torch.all(va[count:] == -7)
@@ -76,7 +80,7 @@ def test_sort_look_back_gives_up_and_reports():
     k[:count] = torch.from_numpy(keys.view(np.int32))
     v[:count] = torch.arange(count, dtype=torch.int32, device="cuda")
     st.zero_()
-    alt = B.ags_sort32(k, v, ka, va, n, count, 0, 20, 7, None, 0, st, ws)
+    alt = B.ags_sort32(k, v, ka, va, n, count, 0, 20, 7, None, 0, st, ws, flags=extra)
     B.ags_check(st)
     out = (va if alt else v)[:count].cpu().numpy()
     np.testing.assert_array_equal(out, np.argsort(keys, kind="stable"))
