@@ -525,7 +525,10 @@ def run_ours(args, world, rank, local):
         tgt_r = R.Renderer(pert, cams[:1], B.AGS_SCALE_PLAIN)
         target = tgt_r.forward().clone()
         del tgt_r, pert
-        fb = R.Renderer(sc, cams[:1], B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_backward=True)
+        # launch parameters tuned for this one-view workload (untimed set-up)
+        tuned1 = autotune.tune(sc, cams[:1], B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"])
+        knobs1 = {k: tuned1[k] for k in autotune.KNOBS}
+        fb = R.Renderer(sc, cams[:1], B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"], want_backward=True, **knobs1)
         grads = {k: torch.empty_like(v) for k, v in sc.items()}
         inv = 2.0 / target.numel()
 
@@ -563,6 +566,7 @@ def run_ours(args, world, rank, local):
         fb.check()
         extras["fwd_bwd_ms"] = max_over_ranks(a.elapsed_time(b)) / args.steps
         extras["fwd_bwd_ms_eager"] = fb_eager_ms
+        extras["fwd_bwd_tuned"] = knobs1
         del fb, grads, target, g_fb
 
         # data-parallel training step over the workload's views: each rank renders
@@ -576,7 +580,7 @@ def run_ours(args, world, rank, local):
             targets = tgt_r.forward().clone()
             del tgt_r, pert
             tr = R.Renderer(sc, [cams[v] for v in mine], B.AGS_SCALE_ADAGSCALE, wp["K"], wp["lut"],
-                            want_backward=True)
+                            want_backward=True, **knobs)
             fn = MV.renderer_grads(tr, targets, 1.0 / (V * 3 * ada.H * ada.W))
             for _ in range(max(2, args.warmup)):
                 MV.train_step(mine, fn)
