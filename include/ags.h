@@ -259,7 +259,8 @@ ags_status ags_emit_tile_pairs(const ags_projected* proj, int64_t n, int32_t vie
                                int64_t capacity, int64_t* d_num_pairs, int64_t* d_status,
                                int32_t flags, void* ws, size_t ws_bytes, void* stream);
 
-/* Scratch bytes needed by ags_compact_visible for views*n Gaussian-views. */
+/* Scratch bytes needed by ags_compact_visible for views*n Gaussian-views
+ * (per 4096-entry partition: its count and offset, and 512 B of visibility bits). */
 size_t ags_compact_workspace_bytes(int64_t n, int32_t views);
 
 /* The Gaussian-views with pairs (flags bit 7 clear), in increasing index

@@ -41,13 +41,16 @@ __device__ __forceinline__ uint32_t visible_bits(const uint8_t* __restrict__ fla
   return vis;
 }
 
-// (1) visible entries per partition
+// (1) visible entries per partition, and each thread's visibility bits for (3)
 __global__ void __launch_bounds__(kVisThreads)
-visible_count_kernel(const uint8_t* __restrict__ flags, uint32_t total, uint32_t* __restrict__ part_count) {
+visible_count_kernel(const uint8_t* __restrict__ flags, uint32_t total, uint32_t* __restrict__ part_count,
+                     uint16_t* __restrict__ masks) {
   __shared__ uint32_t s_warp[kVisThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t i0 = blockIdx.x * (uint32_t)kVisPart + (uint32_t)tid * kVisItems;
-  const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(visible_bits(flags, i0, total)));
+  const uint32_t vis = visible_bits(flags, i0, total);
+  masks[(size_t)blockIdx.x * kVisThreads + tid] = (uint16_t)vis;
+  const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(vis));
   if (lane == 0) s_warp[warp] = c;
   __syncthreads();
   if (tid == 0) {
@@ -102,7 +105,7 @@ visible_scan_kernel(uint32_t* __restrict__ part, uint32_t parts, int64_t* d_coun
 
 // (3) the visible entries of one partition, written at its offset
 __global__ void __launch_bounds__(kVisThreads)
-visible_write_kernel(const uint8_t* __restrict__ flags, const float* __restrict__ depth, uint32_t total,
+visible_write_kernel(const uint16_t* __restrict__ masks, const float* __restrict__ depth,
                      const uint32_t* __restrict__ part_off, uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
   __shared__ uint32_t s_key[kVisPart];
   __shared__ uint32_t s_id[kVisPart];
@@ -110,7 +113,7 @@ visible_write_kernel(const uint8_t* __restrict__ flags, const float* __restrict_
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t p0 = blockIdx.x * (uint32_t)kVisPart;
   const uint32_t i0 = p0 + (uint32_t)tid * kVisItems;
-  const uint32_t vis = visible_bits(flags, i0, total);
+  const uint32_t vis = __ldg(masks + (size_t)blockIdx.x * kVisThreads + tid);
   const uint32_t cnt = (uint32_t)__popc(vis);
   uint32_t incl = cnt;
 #pragma unroll
@@ -144,11 +147,9 @@ visible_write_kernel(const uint8_t* __restrict__ flags, const float* __restrict_
   }
   __syncthreads();
   const uint32_t base = __ldg(part_off + blockIdx.x);
-  for (uint32_t k = (uint32_t)tid; k < agg; k += kVisThreads) {
-    if (base + k < total) {
-      keys[base + k] = s_key[k];
-      ids[base + k] = s_id[k];
-    }
+  for (uint32_t k = (uint32_t)tid; k < agg; k += kVisThreads) {   // base + agg <= the entries
+    keys[base + k] = s_key[k];
+    ids[base + k] = s_id[k];
   }
 }
 
@@ -158,7 +159,8 @@ static size_t vis_parts(int64_t total) { return (size_t)((total + kVisPart - 1) 
 
 extern "C" size_t ags_compact_workspace_bytes(int64_t n, int32_t views) {
   if (n < 0 || views < 1) return 0;
-  return 256 + 8 * ags::vis_parts(n * (int64_t)views);
+  const size_t parts = ags::vis_parts(n * (int64_t)views);
+  return 256 + 8 * parts + sizeof(uint16_t) * ags::kVisThreads * parts;   // header, counts, visibility masks
 }
 
 extern "C" ags_status ags_compact_visible(const ags_projected* proj, int64_t n, int32_t views, uint32_t* keys,
@@ -175,10 +177,10 @@ extern "C" ags_status ags_compact_visible(const ags_projected* proj, int64_t n, 
   if (!ws || ws_bytes < ags_compact_workspace_bytes(n, views) || ((uintptr_t)ws & 7u)) return AGS_ERR_INVALID_ARG;
   const size_t parts = vis_parts(total);
   uint32_t* part = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + 256);
-  visible_count_kernel<<<(unsigned)parts, kVisThreads, 0, st>>>(proj->flags, (uint32_t)total, part);
+  uint16_t* masks = reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(ws) + 256 + 8 * parts);
+  visible_count_kernel<<<(unsigned)parts, kVisThreads, 0, st>>>(proj->flags, (uint32_t)total, part, masks);
   visible_scan_kernel<<<1, kVisScanThreads, 0, st>>>(part, (uint32_t)parts, d_count);
-  visible_write_kernel<<<(unsigned)parts, kVisThreads, 0, st>>>(proj->flags, proj->depth, (uint32_t)total, part, keys,
-                                                                ids);
+  visible_write_kernel<<<(unsigned)parts, kVisThreads, 0, st>>>(masks, proj->depth, part, keys, ids);
   return launch_status(cudaGetLastError());
 }
 

@@ -62,11 +62,11 @@ def test_workspace_sizes(lib):
     assert B.ags_sort_workspace_bytes(4096) == 256 + 16 * 512 * 4 + 1 * 512 * 4
     assert B.ags_sort_workspace_bytes(4097) == 256 + 16 * 512 * 4 + 2 * 512 * 4
     assert B.ags_backward_workspace_bytes(10, 2) == 10 * 2 * 9 * 4
-    assert B.ags_compact_workspace_bytes(4096, 1) == 256 + 8
+    assert B.ags_compact_workspace_bytes(4096, 1) == 256 + (8 + 2 * 256) * 1       # header, count, masks per partition
     chunks = 4 * ((B.AGS_MAX_PAIRS + 2047) // 2048 + 1)
     assert B.ags_emit_tile_workspace_bytes(1024, 1) == 256 + 16 + 16 * 1024 + chunks
     assert B.ags_emit_tile_workspace_bytes(1025, 2) == 256 + 32 + 16 * 2050 + chunks
-    assert B.ags_compact_workspace_bytes(4097, 2) == 256 + 8 * 3
+    assert B.ags_compact_workspace_bytes(4097, 2) == 256 + (8 + 2 * 256) * 3
 
 
 def test_invalid_arguments_rejected_on_host(lib):
